@@ -1,0 +1,155 @@
+/* esmp2.h -- C ABI of the GB300 (sm_103a) ESMP2-TOP(1) library.
+ *
+ * ESMP2 (excited-state-specific second-order perturbation theory) corrects an
+ * excited-state mean-field (ESMF) reference Psi0 = sum_ia C_ia (a+_a a_i + a+_a a_i)|Phi>
+ * (singlet, closed-shell coefficient zero; Sec. II.A, Eq. psi0).  The library
+ * works in the transition-orbital-pair (TOP) basis of Sec. II.A (SVD C = U Lambda V^+,
+ * Eqs. 2-4) and solves the first-order equation
+ *        (H0 - E0) |Psi1> = -Q H |Psi0>                     (Sec. II.C-D)
+ * with the modified zeroth-order Hamiltonian of Eq. qfq_replacement: the Fock
+ * operator F acts fully on the doubles (D) and on the L-triples (triples holding
+ * the large transition-orbital pair t -> t', TOP(1)), and only through its diagonal
+ * on the S- and N-triples, which are therefore inverted directly.  E2 = <Psi0|H|Psi1>.
+ *
+ * Conventions shared by every call
+ *  - No exceptions cross the ABI; every call returns an esmp2_status and leaves a
+ *    message for esmp2_last_error().
+ *  - Orbital order: No occupied then Nv virtual orbitals; virtual a is orbital No+a.
+ *  - Two-electron integrals are real chemist-notation (pq|rs) with 8-fold symmetry.
+ *  - All arrays are row-major float64 unless stated otherwise.
+ *  - The iterative vector ("block vector") is five full-storage blocks
+ *    [5][No][No][Nv][Nv] (T, S, X, Y, Z) in the TOP basis; the element meaning,
+ *    masks and inner-product weights are returned by esmp2_layout().  Block k
+ *    element (i,j,a,b) is the coefficient of the operator string
+ *      T: a+_{a up} a+_{b up} a_{j up} a_{i up}|Phi>            (shared with down-down)
+ *      S: a+_{a up} a+_{b dn} a_{j dn} a_{i up}|Phi>
+ *      X: a+_{t' up} a+_{a up} a+_{b up} a_{j up} a_{i up} a_{t up}|Phi>   (shared, all down)
+ *      Y: a+_{t' up} a+_{a dn} a+_{b dn} a_{j dn} a_{i dn} a_{t up}|Phi>   (shared, spin flip)
+ *      Z: a+_{a up} a+_{t' dn} a+_{b dn} a_{j dn} a_{t dn} a_{i up}|Phi>   (shared, spin flip)
+ *    with t = occupied 0 (largest singular value) and t' = virtual 0 (Eq. psi1).
+ *  - Device pointers passed to the library stay owned by the caller; the library
+ *    never frees them.  Buffers owned by a handle are released by esmp2_destroy().
+ *  - Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef ESMP2_H
+#define ESMP2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ESMP2_OK = 0,
+  ESMP2_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, non-finite input */
+  ESMP2_ERR_UNSUPPORTED = 2,   /* e.g. triplet spin, Nv < No, layout not supported */
+  ESMP2_ERR_OOM = 3,           /* device allocation failed */
+  ESMP2_ERR_NOT_CONVERGED = 4, /* maxit reached before the residual tolerance */
+  ESMP2_ERR_INDEFINITE = 5,    /* CG met p.Ap <= 0: (H0 - E0) is not positive definite */
+  ESMP2_ERR_CUDA = 6,          /* a CUDA runtime error (message in esmp2_last_error) */
+  ESMP2_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  ESMP2_ERR_STATE = 8          /* call order violated (e.g. energy before solve) */
+} esmp2_status;
+
+typedef enum {
+  ESMP2_FP64 = 0,        /* every contraction in float64 */
+  ESMP2_MIXED_BF16 = 1,  /* sigma contractions bf16 x bf16 -> fp32 (tcgen05) inside fp64 refinement */
+  ESMP2_MIXED_TF32 = 2   /* reserved: tf32 inner contractions (returns ESMP2_ERR_UNSUPPORTED) */
+} esmp2_precision;
+
+typedef struct esmp2_handle esmp2_handle;
+
+/* Problem statement (Sec. II.A, II.C): Fock matrix F built from Psi0's one-body
+ * density, the integral blocks the right-hand side Q H Psi0 needs, and C. */
+typedef struct {
+  int No, Nv;               /* occupied / virtual spatial orbitals; 1 <= No <= 64, No <= Nv */
+  const double *F;          /* (No+Nv)^2, symmetric, ESMF orbital basis */
+  const double *ovov;       /* (ia|jb)  [No][Nv][No][Nv] */
+  const double *ooov;       /* (ij|ka)  [No][No][No][Nv] */
+  const double *ovvv;       /* (ia|bc)  [No][Nv][Nv][Nv] */
+  const double *C;          /* No x Nv singles coefficients (any normalisation; rescaled so 2|C|^2 = 1) */
+  int spin;                 /* +1 singlet (supported); -1 triplet -> ESMP2_ERR_UNSUPPORTED */
+  int inputs_on_device;     /* 0: host pointers, 1: device pointers (read during create only) */
+} esmp2_desc;
+
+typedef struct {
+  int No, Nv;
+  int64_t block_elems;      /* No*No*Nv*Nv */
+  int64_t n_elems;          /* 5 * block_elems: length of a block vector */
+  double weights[5];        /* determinant inner product = sum_k weights[k] * sum(u_k * v_k) */
+  double omega;             /* E0 - E_Phi[F] = sum_u 2 lam_u^2 (F_u'u' - F_uu) */
+  double E0;                /* <Psi0|F|Psi0> */
+} esmp2_layout_info;
+
+typedef struct {
+  int iterations;           /* total CG iterations (inner iterations for mixed precision) */
+  int outer;                /* fp64 refinement steps (1 for ESMP2_FP64) */
+  int sigma_fp64;           /* number of float64 sigma applications */
+  int sigma_lowp;           /* number of low-precision sigma applications */
+  double rel_residual;      /* true ||b + A x|| / ||b|| at exit (determinant norm) */
+  double seconds;           /* wall time of the solve (host clock) */
+} esmp2_solve_info;
+
+typedef struct {
+  double E2, E2_D, E2_L, E2_S;   /* E2 = E2_D + E2_L + E2_S (Eh) */
+} esmp2_energy_parts;
+
+/* Create a handle: normalises C, builds the TOP basis on the device (one-sided Jacobi
+ * SVD of C, Householder completion of the virtual space; Sec. II.A), transforms F and
+ * the integrals, builds the right-hand side b = Q H Psi0 on D+L and the diagonal.
+ * Inputs are copied; the caller keeps ownership.  Stream: the default stream until
+ * esmp2_set_stream().  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+esmp2_status esmp2_create(esmp2_handle **h, const esmp2_desc *d);
+void esmp2_destroy(esmp2_handle *h);
+const char *esmp2_last_error(const esmp2_handle *h);
+
+/* Launch every later kernel of this handle on `stream` (a cudaStream_t, e.g. torch's
+ * current stream).  NULL selects the legacy default stream. */
+esmp2_status esmp2_set_stream(esmp2_handle *h, void *stream);
+
+esmp2_status esmp2_layout(const esmp2_handle *h, esmp2_layout_info *out);
+
+/* TOP basis as built on the device, copied to host arrays (any may be NULL):
+ * U No x No, lam No, Wv Nv x Nv (first No columns = TOP virtuals), F_top (No+Nv)^2. */
+esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv, double *F_top);
+
+/* y = (H0 - E0) x on D+L (the "sigma build"): Eq. qfq_replacement restricted to the
+ * doubles and L-triples, minus E0.  x, y: caller-owned DEVICE buffers of n_elems
+ * float64 in the block layout; x must be zero on masked elements and antisymmetric
+ * where the layout says so; y is written on every element (zero on masked ones).
+ * p = ESMP2_FP64 computes in float64; ESMP2_MIXED_BF16 rounds x and F to bf16 for
+ * the N_o^2 N_v^3 virtual-index contractions (fp32 accumulation), keeps the rest
+ * in fp32/fp64.  x and y must not overlap. */
+esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
+
+/* Right-hand side b = Q H Psi0 on D+L (Slater-Condon, Sec. II.B), copied into a
+ * caller-owned DEVICE buffer of n_elems float64. */
+esmp2_status esmp2_rhs(esmp2_handle *h, double *b);
+
+/* Solve (H0 - E0) x = -b on D+L by Jacobi-preconditioned conjugate gradients
+ * (Sec. III.A uses CG).  ESMP2_FP64: plain fp64 PCG.  ESMP2_MIXED_BF16: fp64
+ * iterative refinement, each step solving the correction with bf16/fp32 inner
+ * PCG.  Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
+ * Errors: NOT_CONVERGED (maxit CG iterations in total), INDEFINITE, CUDA.
+ * The solution stays on the device (esmp2_get_solution); a later solve warm-starts
+ * from it. */
+esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision p, esmp2_solve_info *info);
+
+/* Copy the current solution x (DEVICE buffer, n_elems float64) out / set a guess in. */
+esmp2_status esmp2_get_solution(esmp2_handle *h, double *x);
+esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x);
+
+/* E2 = E2_D + E2_L + E2_S.  E2_D, E2_L: Hylleraas functional 2 b.x + x.Ax of the
+ * current solution (error quadratic in the residual); E2_S = -sum_S b_I^2 / D_I over
+ * the S-triples with the diagonal Fock denominator (Sec. II.D), evaluated on the fly.
+ * All reductions in float64.  Requires a previous esmp2_solve (else ERR_STATE). */
+esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
+
+/* Number of CUDA kernels this handle has launched since creation (for accounting). */
+int64_t esmp2_kernel_launches(const esmp2_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,191 @@
+// C ABI entry points of the ESMP2 library (declared in include/esmp2.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace esmp2 {
+esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, double *ovvv_in, double *scratch);
+}
+
+using namespace esmp2;
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+bool finite_host(const double *p, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+void free_handle(esmp2_handle *h) {
+  void *ptrs[] = {h->C, h->U, h->lam, h->Wv, h->W, h->F, h->f0vo, h->scal, h->ovov, h->ooov, h->ovvt, h->b,
+                  h->s64.x, h->s64.r, h->s64.p, h->s64.q, h->s64.w, h->cp.VX, h->cp.OX, h->cp.WZ, h->cp.OZ,
+                  h->cp.G, h->cp.H, h->cp.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
+                  h->q32, h->x32};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (h->hred) cudaFreeHost(h->hred);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *esmp2_last_error(const esmp2_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int64_t esmp2_kernel_launches(const esmp2_handle *h) { return h ? h->launches : 0; }
+
+esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) {
+  if (!out || !d) return ESMP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  esmp2_handle *h = new (std::nothrow) esmp2_handle();
+  if (!h) return ESMP2_ERR_OOM;
+  *out = h;
+  const int No = d->No, Nv = d->Nv;
+  if (No < 1 || No > 64 || Nv < No || Nv > 4096) {
+    h->err = "require 1 <= No <= 64 and No <= Nv <= 4096";
+    return No >= 1 && Nv >= 1 && Nv < No ? ESMP2_ERR_UNSUPPORTED : ESMP2_ERR_INVALID_ARG;
+  }
+  if (d->spin != 1) { h->err = "only singlet states (spin = +1) are supported"; return ESMP2_ERR_UNSUPPORTED; }
+  if (!d->F || !d->ovov || !d->ooov || !d->ovvv || !d->C) { h->err = "NULL input array"; return ESMP2_ERR_INVALID_ARG; }
+  const int N = No + Nv;
+  h->d.No = No; h->d.Nv = Nv; h->d.N = N;
+  h->d.B = (int64_t)No * No * Nv * Nv;
+  h->d.n = 5 * h->d.B;
+  const size_t nF = (size_t)N * N, nC = (size_t)No * Nv;
+  const size_t nOVOV = (size_t)h->d.B, nOOOV = (size_t)No * No * No * Nv, nOVVV = (size_t)No * Nv * Nv * Nv;
+  const size_t nOVVT = (size_t)No * Nv * Nv * No;
+  if (!d->inputs_on_device) {
+    if (!finite_host(d->F, nF) || !finite_host(d->C, nC)) { h->err = "non-finite F or C"; return ESMP2_ERR_INVALID_ARG; }
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < p; ++q)
+        if (std::fabs(d->F[(size_t)p * N + q] - d->F[(size_t)q * N + p]) > 1e-12 * (1.0 + std::fabs(d->F[(size_t)p * N + q]))) {
+          h->err = "F is not symmetric";
+          return ESMP2_ERR_INVALID_ARG;
+        }
+  }
+  cudaError_t ce = cudaSuccess;
+#define ALLOC(ptr, cnt) if ((ce = dalloc(&(ptr), (cnt))) != cudaSuccess) { esmp2_status s = check_cuda(h, ce, "alloc " #ptr); return s; }
+  ALLOC(h->C, nC); ALLOC(h->U, (size_t)No * No); ALLOC(h->lam, (size_t)No); ALLOC(h->Wv, (size_t)Nv * Nv);
+  ALLOC(h->W, nF); ALLOC(h->F, nF); ALLOC(h->f0vo, nC); ALLOC(h->scal, (size_t)8);
+  ALLOC(h->ovov, nOVOV); ALLOC(h->ooov, nOOOV); ALLOC(h->ovvt, nOVVT);
+  ALLOC(h->b, (size_t)h->d.n);
+  ALLOC(h->s64.x, (size_t)h->d.n); ALLOC(h->s64.r, (size_t)h->d.n); ALLOC(h->s64.p, (size_t)h->d.n);
+  ALLOC(h->s64.q, (size_t)h->d.n);
+  ALLOC(h->cp.VX, (size_t)No * No * Nv); ALLOC(h->cp.OX, (size_t)No * Nv * Nv); ALLOC(h->cp.WZ, (size_t)No * No * Nv);
+  ALLOC(h->cp.OZ, (size_t)No * Nv * Nv); ALLOC(h->cp.G, nC); ALLOC(h->cp.H, nC); ALLOC(h->cp.CYZ, nC);
+  {
+    const size_t nred = std::max<size_t>((size_t)16 * 1216, (size_t)No * No * No);
+    ALLOC(h->red, nred);
+  }
+  ALLOC(h->red_out, (size_t)32);
+  if ((ce = cudaMallocHost(reinterpret_cast<void **>(&h->hred), sizeof(double) * 32)) != cudaSuccess)
+    return check_cuda(h, ce, "pinned alloc");
+  // inputs -> device
+  const cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double *ovov_in = nullptr, *ooov_in = nullptr, *ovvv_in = nullptr, *scratch = nullptr;
+  const size_t nscr = std::max(nOVOV, std::max(nOOOV, nOVVT));
+  if ((ce = dalloc(&ovov_in, nOVOV)) != cudaSuccess || (ce = dalloc(&ooov_in, nOOOV)) != cudaSuccess ||
+      (ce = dalloc(&ovvv_in, std::max(nOVVV, nOVVT))) != cudaSuccess || (ce = dalloc(&scratch, nscr)) != cudaSuccess) {
+    cudaFree(ovov_in); cudaFree(ooov_in); cudaFree(ovvv_in); cudaFree(scratch);
+    return check_cuda(h, ce, "input staging");
+  }
+  cudaMemcpy(h->F, d->F, sizeof(double) * nF, kind);
+  cudaMemcpy(h->C, d->C, sizeof(double) * nC, kind);
+  cudaMemcpy(ovov_in, d->ovov, sizeof(double) * nOVOV, kind);
+  cudaMemcpy(ooov_in, d->ooov, sizeof(double) * nOOOV, kind);
+  cudaMemcpy(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind);
+  ce = cudaGetLastError();
+  esmp2_status s = check_cuda(h, ce, "input copy");
+  if (!s) s = setup_top_basis(h);
+  if (!s) s = setup_rhs_from(h, ovov_in, ooov_in, ovvv_in, scratch);
+  if (!s) {
+    cudaMemsetAsync(h->s64.x, 0, sizeof(double) * h->d.n, h->stream);
+    s = check_cuda(h, cudaStreamSynchronize(h->stream), "create");
+  }
+  cudaFree(ovov_in); cudaFree(ooov_in); cudaFree(ovvv_in); cudaFree(scratch);
+  if (!s && !std::isfinite(h->omega)) { h->err = "non-finite Fock matrix in the TOP basis"; s = ESMP2_ERR_INVALID_ARG; }
+  return s;
+#undef ALLOC
+}
+
+void esmp2_destroy(esmp2_handle *h) {
+  if (!h) return;
+  free_handle(h);
+  delete h;
+}
+
+esmp2_status esmp2_set_stream(esmp2_handle *h, void *stream) {
+  if (!h) return ESMP2_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return ESMP2_OK;
+}
+
+esmp2_status esmp2_layout(const esmp2_handle *h, esmp2_layout_info *o) {
+  if (!h || !o) return ESMP2_ERR_INVALID_ARG;
+  o->No = h->d.No; o->Nv = h->d.Nv;
+  o->block_elems = h->d.B; o->n_elems = h->d.n;
+  for (int k = 0; k < 5; ++k) o->weights[k] = kWeights[k];
+  o->omega = h->omega; o->E0 = h->E0;
+  return ESMP2_OK;
+}
+
+esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv, double *F_top) {
+  if (!h) return ESMP2_ERR_INVALID_ARG;
+  const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
+  cudaStreamSynchronize(h->stream);
+  if (U) cudaMemcpy(U, h->U, sizeof(double) * No * No, cudaMemcpyDeviceToHost);
+  if (lam) cudaMemcpy(lam, h->lam, sizeof(double) * No, cudaMemcpyDeviceToHost);
+  if (Wv) cudaMemcpy(Wv, h->Wv, sizeof(double) * Nv * Nv, cudaMemcpyDeviceToHost);
+  if (F_top) cudaMemcpy(F_top, h->F, sizeof(double) * N * N, cudaMemcpyDeviceToHost);
+  return check_cuda(h, cudaGetLastError(), "top_basis");
+}
+
+esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p) {
+  if (!h || !x || !y || x == y) return ESMP2_ERR_INVALID_ARG;
+  if (p == ESMP2_FP64) return sigma64(h, x, y);
+  if (p == ESMP2_MIXED_BF16) return sigma_mixed(h, x, y);
+  h->err = "precision not supported";
+  return ESMP2_ERR_UNSUPPORTED;
+}
+
+esmp2_status esmp2_rhs(esmp2_handle *h, double *b) {
+  if (!h || !b) return ESMP2_ERR_INVALID_ARG;
+  cudaMemcpyAsync(b, h->b, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  return check_cuda(h, cudaGetLastError(), "rhs");
+}
+
+esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision p, esmp2_solve_info *info) {
+  if (!h || !(tol > 0) || maxit < 1) return ESMP2_ERR_INVALID_ARG;
+  if (p == ESMP2_FP64) return solve64(h, tol, maxit, info);
+  if (p == ESMP2_MIXED_BF16) return solve_mixed(h, tol, maxit, info);
+  h->err = "precision not supported";
+  return ESMP2_ERR_UNSUPPORTED;
+}
+
+esmp2_status esmp2_get_solution(esmp2_handle *h, double *x) {
+  if (!h || !x) return ESMP2_ERR_INVALID_ARG;
+  cudaMemcpyAsync(x, h->s64.x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  return check_cuda(h, cudaGetLastError(), "get_solution");
+}
+
+esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
+  if (!h || !x) return ESMP2_ERR_INVALID_ARG;
+  cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  return check_cuda(h, cudaGetLastError(), "set_solution");
+}
+
+esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts) {
+  if (!h || !parts) return ESMP2_ERR_INVALID_ARG;
+  return energy(h, parts);
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations of the ESMP2 GB300 library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/esmp2.h"
+
+namespace esmp2 {
+
+constexpr int kBlocks = 5;  // T, S, X, Y, Z
+enum Block { BT = 0, BS = 1, BX = 2, BY = 3, BZ = 4 };
+
+// Determinant inner-product weights of the full-storage blocks: T, X, Y hold every
+// unique amplitude four times and stand for two determinants (spin flip); S elements
+// are unique determinants; Z elements stand for a determinant and its spin flip.
+constexpr double kWeights[kBlocks] = {0.5, 1.0, 0.5, 0.5, 2.0};
+
+struct Dims {
+  int No, Nv, N;
+  int64_t B;   // block elements No*No*Nv*Nv
+  int64_t n;   // 5*B
+};
+
+// Strided batched float64 GEMM: C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+struct Gemm64 {
+  int M, N, K, batch;
+  double alpha, beta;
+  const double *A; int64_t sAm, sAk, sAb;
+  const double *B; int64_t sBk, sBn, sBb;
+  double *C; int64_t sCm, sCn, sCb;
+};
+void gemm64(const Gemm64 &g, cudaStream_t st);
+
+// Mode product of a 4-index tensor: out[..k'..] = sum_k in[..k..] R[k][k'] on axis `mode`;
+// R is Kin x Kout with row stride ldR.
+void mode_product(const double *in, double *out, const int dims[4], int mode, const double *R,
+                  int Kout, int64_t ldR, cudaStream_t st);
+
+// Device intermediates of the N^4 coupling terms of sigma.
+struct Couplings {
+  double *VX;  // [No][No][Nv]  sum_c Fov[0][c] X[i][j][c][b]
+  double *OX;  // [No][Nv][Nv]  sum_k Fov[k][0] X[k][j][a][b]
+  double *WZ;  // [No][No][Nv]  sum_c Fov[0][c] Z[i][j][a][c]
+  double *OZ;  // [No][Nv][Nv]  sum_k Fov[k][0] Z[i][k][a][b]
+  double *G;   // [No][Nv]      sum_kc Fov[k][c] (X+Z)[k][j][c][b]
+  double *H;   // [No][Nv]      sum_kc Fov[k][c] (Y+Z)[i][k][a][c]
+  double *CYZ; // [No][Nv]      sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
+};
+
+struct Solver64 {
+  double *x, *r, *p, *q, *w;  // fp64 vectors (n)
+};
+
+}  // namespace esmp2
+
+struct esmp2_handle {
+  esmp2::Dims d;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  // TOP basis and transformed one-electron quantities
+  double *C = nullptr;      // No x Nv normalised
+  double *U = nullptr;      // No x No
+  double *lam = nullptr;    // No
+  double *Wv = nullptr;     // Nv x Nv
+  double *W = nullptr;      // N x N block-diagonal rotation
+  double *F = nullptr;      // N x N  F in the TOP basis
+  double *f0vo = nullptr;   // Nv x No  Fock matrix of Phi, virtual-occupied block
+  double *scal = nullptr;   // device scalars: [0] omega, [1] E0
+  double omega = 0, E0 = 0;
+  // transformed integrals
+  double *ovov = nullptr;   // (ia|jb)  No Nv No Nv
+  double *ooov = nullptr;   // (ij|ka)  No No No Nv
+  double *ovvt = nullptr;   // (ia|bu') No Nv Nv No
+  // vectors
+  double *b = nullptr;      // right-hand side (n)
+  esmp2::Solver64 s64{};
+  esmp2::Couplings cp{};
+  double *red = nullptr;    // reduction partials
+  double *red_out = nullptr;// reduction results (device)
+  double *hred = nullptr;   // pinned host copy of reduction results
+  bool solved = false;
+  bool e2s_done = false;
+  double e2s = 0;
+  // low-precision sigma workspace (mixed path)
+  void *xlp = nullptr;      // bf16 copy of the sigma input (n)
+  void *Fvlp = nullptr;     // bf16 Fvv (Nv x Nv, padded)
+  float *ylp = nullptr;     // fp32 sigma output (n)
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr;  // inner PCG vectors
+};
+
+namespace esmp2 {
+// kernels.cu
+esmp2_status setup_top_basis(esmp2_handle *h);
+esmp2_status setup_rhs(esmp2_handle *h);
+esmp2_status sigma64(esmp2_handle *h, const double *x, double *y);
+esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
+esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
+esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
+esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+}  // namespace esmp2

@@ -1,0 +1,377 @@
+// Krylov solve of the first-order equation (H0 - E0) x = -b on D+L and the E2 reductions.
+//
+// Preconditioned conjugate gradients (the paper's solver is CG, Sec. III.A) with the
+// Jacobi preconditioner diag(A) = F_aa + F_bb - F_ii - F_jj - omega (+ F_t't' - F_tt on
+// the L blocks).  Inner products are the determinant-space ones (block weights).  All
+// vector updates are fused streaming kernels; every reduction is a deterministic
+// two-level float64 sum (per-CTA partials, then one CTA in fixed order).
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace esmp2 {
+
+constexpr int kRedBlocks = 1216;  // 152 SMs x 8
+constexpr int kRedThreads = 256;
+
+namespace {
+
+struct VCtx {
+  int No, Nv, N;
+  int64_t B;
+  const double *F;
+  double omega;
+  __device__ __forceinline__ double dinv(int64_t e) const {
+    int64_t f = e;
+    const int b = (int)(f % Nv); f /= Nv;
+    const int a = (int)(f % Nv); f /= Nv;
+    const int j = (int)(f % No); f /= No;
+    const int i = (int)(f % No); f /= No;
+    const int blk = (int)f;
+    if ((blk == BT || blk == BX || blk == BY) && (i == j || a == b)) return 0.0;
+    if (blk == BX && (i == 0 || j == 0 || a == 0 || b == 0)) return 0.0;
+    if (blk == BZ && (j == 0 || b == 0 || (i == 0 && a == 0))) return 0.0;
+    double d = F[(int64_t)(No + a) * N + No + a] + F[(int64_t)(No + b) * N + No + b] - F[(int64_t)i * N + i] -
+               F[(int64_t)j * N + j] - omega;
+    if (blk >= BX) d += F[(int64_t)No * N + No] - F[0];
+    return 1.0 / d;
+  }
+  __device__ __forceinline__ double w(int64_t e) const {
+    const int blk = (int)(e / B);
+    return blk == 1 ? 1.0 : (blk == 4 ? 2.0 : 0.5);
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce NQ values and store them as partials red[q * gridDim.x + blockIdx.x].
+template <int NQ>
+__device__ __forceinline__ void block_partials(double (&v)[NQ], double *red) {
+  __shared__ double sh[NQ][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) red[(int64_t)q * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// Sum the partials of nq quantities in fixed order; mode selects the scalar bookkeeping.
+// slots: 0 rz, 1 rr, 2 bb, 3 pq, 4 alpha, 5 beta, 8.. generic results
+__global__ void k_finalize(const double *red, int nparts, int nq, double *slots, int mode) {
+  __shared__ double sh[32];
+  for (int q = 0; q < nq; ++q) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += red[(int64_t)q * nparts + k];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      if (mode == 0) {            // init: rz, rr, bb
+        slots[q] = t;
+      } else if (mode == 1) {     // pq -> alpha
+        slots[3] = t;
+        slots[4] = slots[0] / t;
+      } else if (mode == 2) {     // rz_new, rr -> beta
+        if (q == 0) { slots[5] = t / slots[0]; slots[0] = t; }
+        else slots[1] = t;
+      } else {                    // generic
+        slots[8 + q] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// r = -b - q; p = M^-1 r; partials <r,M^-1 r>, <r,r>, <b,b>
+__global__ void k_pcg_init(VCtx c, const double *b, const double *q, double *r, double *p, double *red) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = -b[e] - q[e], z = c.dinv(e) * ri, w = c.w(e);
+    r[e] = ri;
+    p[e] = z;
+    v[0] += w * ri * z;
+    v[1] += w * ri * ri;
+    v[2] += w * b[e] * b[e];
+  }
+  block_partials<3>(v, red);
+}
+
+__global__ void k_dot_w(VCtx c, const double *u, const double *v_, double *red) {
+  double v[1] = {0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    v[0] += c.w(e) * u[e] * v_[e];
+  block_partials<1>(v, red);
+}
+
+// x += alpha p; r -= alpha q; partials <r,M^-1 r>, <r,r>
+__global__ void k_pcg_update(VCtx c, const double *slots, double *x, double *r, const double *p, const double *q,
+                             double *red) {
+  const double alpha = slots[4];
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    x[e] += alpha * p[e];
+    const double ri = r[e] - alpha * q[e];
+    r[e] = ri;
+    const double w = c.w(e);
+    v[0] += w * ri * c.dinv(e) * ri;
+    v[1] += w * ri * ri;
+  }
+  block_partials<2>(v, red);
+}
+
+// p = M^-1 r + beta p
+__global__ void k_pcg_p(VCtx c, const double *slots, const double *r, double *p) {
+  const double beta = slots[5];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = c.dinv(e) * r[e] + beta * p[e];
+}
+
+// per-block <b,x> and <x,Ax> for the Hylleraas functional (10 partial sums)
+__global__ void k_hylleraas(VCtx c, const double *b, const double *x, const double *q, double *red) {
+  double v[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) v[k] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const int blk = (int)(e / c.B);
+    const double xb = x[e] * b[e], xq = x[e] * q[e];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k == blk) { v[2 * k] += xb; v[2 * k + 1] += xq; }
+  }
+  block_partials<10>(v, red);
+}
+
+// ---- S-space energy: E2_S = -sum_{I in S} b_I^2 / D_I, both spin sectors (factor 2).
+struct SCtx {
+  int No, Nv, N;
+  const double *F, *lam, *ovov;
+  double omega;
+  __device__ __forceinline__ double Fo(int k) const { return F[(int64_t)k * N + k]; }
+  __device__ __forceinline__ double Fv(int a) const { return F[(int64_t)(No + a) * N + No + a]; }
+  __device__ __forceinline__ double g(int i, int a, int j, int b) const {  // (ia|jb)
+    return ovov[(((int64_t)i * Nv + a) * No + j) * Nv + b];
+  }
+  // b of a triple: P(k/ij)P(c/ab) [<ab||ij> s_kc] with s_kc = lam_k when c is k's TOP partner.
+  __device__ double b3(const int *ho, const int *hs, const int *po, const int *ps) const {
+    const int PERM[3][3] = {{0, 1, 2}, {2, 1, 0}, {0, 2, 1}};
+    const int PS[3] = {1, -1, -1};
+    double v = 0.0;
+    for (int t = 0; t < 3; ++t)
+      for (int r = 0; r < 3; ++r) {
+        const int h3 = PERM[t][2], p3 = PERM[r][2];
+        if (hs[h3] != ps[p3] || ho[h3] != po[p3]) continue;
+        const int H0 = PERM[t][0], H1 = PERM[t][1], P0 = PERM[r][0], P1 = PERM[r][1];
+        double a = 0.0;
+        if (ps[P0] == hs[H0] && ps[P1] == hs[H1]) a += g(ho[H0], po[P0], ho[H1], po[P1]);
+        if (ps[P0] == hs[H1] && ps[P1] == hs[H0]) a -= g(ho[H1], po[P0], ho[H0], po[P1]);
+        v += PS[t] * PS[r] * lam[ho[h3]] * a;
+      }
+    return v;
+  }
+  __device__ double term(const int *ho, const int *hs, const int *po, const int *ps) const {
+    const double bI = b3(ho, hs, po, ps);
+    const double D = Fv(po[0]) + Fv(po[1]) + Fv(po[2]) - Fo(ho[0]) - Fo(ho[1]) - Fo(ho[2]) - omega;
+    return -2.0 * bI * bI / D;
+  }
+};
+
+// sector A: up-up-up, lowest pair u >= 1; block = (u, j, k), threads over b, loop c > b
+__global__ void k_e2s_a(SCtx s, double *red) {
+  const int No = s.No, Nv = s.Nv;
+  const int64_t blk = blockIdx.x;
+  const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
+  double v[1] = {0.0};
+  if (u >= 1 && j < k && j != u && k != u) {
+    for (int b = threadIdx.x; b < Nv; b += blockDim.x) {
+      if (b == u) continue;
+      for (int c = b + 1; c < Nv; ++c) {
+        if (c == u) continue;
+        const bool pj = (b == j || c == j), pk = (b == k || c == k);
+        if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
+        if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
+        const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
+        v[0] += s.term(ho, hs, po, ps);
+      }
+    }
+  }
+  block_partials<1>(v, red);
+}
+
+// sector B: up-down-down with the up pair u -> u' (u >= 1), any down-down double
+__global__ void k_e2s_b(SCtx s, double *red) {
+  const int No = s.No, Nv = s.Nv;
+  const int64_t blk = blockIdx.x;
+  const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
+  double v[1] = {0.0};
+  if (u >= 1 && j < k) {
+    for (int b = threadIdx.x; b < Nv; b += blockDim.x)
+      for (int c = b + 1; c < Nv; ++c) {
+        if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
+        const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
+        v[0] += s.term(ho, hs, po, ps);
+      }
+  }
+  block_partials<1>(v, red);
+}
+
+// sector C: up-down-down without an up pair; lowest down pair u >= 1; block = (u, i, k)
+__global__ void k_e2s_c(SCtx s, double *red) {
+  const int No = s.No, Nv = s.Nv;
+  const int64_t blk = blockIdx.x;
+  const int u = (int)(blk / ((int64_t)No * No)), i = (int)((blk / No) % No), k = (int)(blk % No);
+  double v[1] = {0.0};
+  if (u >= 1 && k != u) {
+    for (int a = threadIdx.x; a < Nv; a += blockDim.x) {
+      if (a == i) continue;
+      for (int c = 0; c < Nv; ++c) {
+        if (c == u) continue;
+        if (c == k && (k < u || k == 0)) continue;
+        const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, c}, ps[3] = {0, 1, 1};
+        v[0] += s.term(ho, hs, po, ps);
+      }
+    }
+  }
+  block_partials<1>(v, red);
+}
+
+}  // namespace
+
+void launch_pcg_init(esmp2_handle *h, const double *b, const double *q, double *r, double *p);
+
+static VCtx vctx(const esmp2_handle *h) {
+  VCtx c;
+  c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = h->F; c.omega = h->omega;
+  return c;
+}
+
+static esmp2_status read_slots(esmp2_handle *h, double *out, int n) {
+  cudaMemcpyAsync(h->hred, h->red_out, sizeof(double) * 32, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "sync");
+  for (int k = 0; k < n; ++k) out[k] = h->hred[k];
+  return ESMP2_OK;
+}
+
+double dot_w(esmp2_handle *h, const double *u, const double *v) {
+  k_dot_w<<<kRedBlocks, kRedThreads, 0, h->stream>>>(vctx(h), u, v, h->red);
+  k_finalize<<<1, 256, 0, h->stream>>>(h->red, kRedBlocks, 1, h->red_out, 3);
+  h->launches += 2;
+  double s[32];
+  read_slots(h, s, 32);
+  return s[8];
+}
+
+esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const VCtx c = vctx(h);
+  double *x = h->s64.x, *r = h->s64.r, *p = h->s64.p, *q = h->s64.q;
+  cudaStream_t st = h->stream;
+  esmp2_status s = sigma64(h, x, q);
+  if (s) return s;
+  int nsig = 1;
+  k_pcg_init<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->b, q, r, p, h->red);
+  k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 3, h->red_out, 0);
+  h->launches += 2;
+  double sl[32];
+  if ((s = read_slots(h, sl, 32))) return s;
+  const double bnorm = std::sqrt(sl[2]);
+  double rr = sl[1];
+  int it = 0;
+  esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
+  double relres = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
+  if (bnorm == 0.0) result = ESMP2_OK;
+  while (result != ESMP2_OK && it < maxit) {
+    if (std::sqrt(rr) <= tol * bnorm) {  // confirm with the true residual
+      if ((s = sigma64(h, x, q))) return s;
+      ++nsig;
+      k_pcg_init<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->b, q, r, p, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 3, h->red_out, 0);
+      h->launches += 2;
+      if ((s = read_slots(h, sl, 32))) return s;
+      rr = sl[1];
+      relres = std::sqrt(rr) / bnorm;
+      if (relres <= tol) { result = ESMP2_OK; break; }
+    }
+    if ((s = sigma64(h, p, q))) return s;
+    ++nsig;
+    k_dot_w<<<kRedBlocks, kRedThreads, 0, st>>>(c, p, q, h->red);
+    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
+    k_pcg_update<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->red_out, x, r, p, q, h->red);
+    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
+    k_pcg_p<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->red_out, r, p);
+    h->launches += 5;
+    if ((s = read_slots(h, sl, 32))) return s;
+    ++it;
+    if (!(sl[3] > 0.0)) { h->err = "CG: p.Ap <= 0 (operator not positive definite)"; result = ESMP2_ERR_INDEFINITE; break; }
+    rr = sl[1];
+    relres = std::sqrt(rr) / bnorm;
+  }
+  if (result == ESMP2_ERR_NOT_CONVERGED) h->err = "CG did not reach the tolerance within maxit iterations";
+  if (info) {
+    info->iterations = it;
+    info->outer = 1;
+    info->sigma_fp64 = nsig;
+    info->sigma_lowp = 0;
+    info->rel_residual = relres;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  h->solved = (result == ESMP2_OK || result == ESMP2_ERR_NOT_CONVERGED);
+  return result;
+}
+
+esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
+  if (!h->solved) { h->err = "esmp2_energy needs a previous esmp2_solve"; return ESMP2_ERR_STATE; }
+  cudaStream_t st = h->stream;
+  esmp2_status s = sigma64(h, h->s64.x, h->s64.q);
+  if (s) return s;
+  k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h), h->b, h->s64.x, h->s64.q, h->red);
+  k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 10, h->red_out, 3);
+  h->launches += 2;
+  double sl[32];
+  if ((s = read_slots(h, sl, 32))) return s;
+  double e_blk[5];
+  for (int k = 0; k < 5; ++k) e_blk[k] = kWeights[k] * (2.0 * sl[8 + 2 * k] + sl[9 + 2 * k]);
+  if (!h->e2s_done) {
+    const int No = h->d.No;
+    SCtx sc;
+    sc.No = No; sc.Nv = h->d.Nv; sc.N = h->d.N; sc.F = h->F; sc.lam = h->lam; sc.ovov = h->ovov; sc.omega = h->omega;
+    const int nb = No * No * No;
+    double tot = 0.0;
+    for (int sector = 0; sector < 3; ++sector) {
+      if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, h->red);
+      else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, h->red);
+      else k_e2s_c<<<nb, 128, 0, st>>>(sc, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, nb, 1, h->red_out, 3);
+      h->launches += 2;
+      if ((s = read_slots(h, sl, 32))) return s;
+      tot += sl[8];
+    }
+    h->e2s = tot;
+    h->e2s_done = true;
+  }
+  parts->E2_D = e_blk[0] + e_blk[1];
+  parts->E2_L = e_blk[2] + e_blk[3] + e_blk[4];
+  parts->E2_S = h->e2s;
+  parts->E2 = parts->E2_D + parts->E2_L + parts->E2_S;
+  return check_cuda(h, cudaGetLastError(), "energy");
+}
+
+}  // namespace esmp2

@@ -1,0 +1,452 @@
+// One-time setup on the device: TOP basis (Sec. II.A, Eqs. 2-4), orbital transforms,
+// the closed-shell Fock block f0_vo and the right-hand side b = Q H Psi0 on D+L.
+//
+// Conventions (shared by construction with every consumer of the TOP basis):
+//  * 2 ||C||^2 = 1;
+//  * SVD by one-sided (Hestenes) Jacobi on the rows of C, singular values sorted in
+//    descending order, column k of V signed so its largest-magnitude component is
+//    positive, u_k = C v_k / lambda_k;
+//  * AVOs = columns No.. of the product of the Householder reflectors that
+//    triangularise V (H = I - 2 w w^T / w^T w, w = x - alpha e_0, alpha = -sign(x_0)|x|).
+#include <cmath>
+
+#include "internal.h"
+
+namespace esmp2 {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// 2 |C|^2 = 1 (each spin-adapted CSF of Eq. psi0 has norm^2 2).
+__global__ void k_normalise(const double *Cin, double *C, int n) {
+  __shared__ double part[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s += Cin[k] * Cin[k];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[0] = v;
+  }
+  __syncthreads();
+  const double scale = 1.0 / sqrt(2.0 * part[0]);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) C[k] = Cin[k] * scale;
+}
+
+// One-sided Jacobi SVD of C (No x Nv, No <= 64): rotate the rows of B = C with an
+// orthogonal J until they are mutually orthogonal; then C = J diag(|B_k|) (B_k/|B_k|).
+// One warp per row pair, pairs of a round disjoint (round-robin ordering).
+// Outputs: U (No x No), lam (No), V into columns 0..No-1 of Wv (Nv x Nv).
+__global__ void __launch_bounds__(1024) k_jacobi_svd(const double *C, double *B, double *J, double *U,
+                                                     double *lam, double *Wv, int No, int Nv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ int rotated;
+  __shared__ int perm[64];
+  __shared__ double nrm[64];
+  for (int k = threadIdx.x; k < No * Nv; k += blockDim.x) B[k] = C[k];
+  for (int k = threadIdx.x; k < No * No; k += blockDim.x) J[k] = (k / No == k % No) ? 1.0 : 0.0;
+  __syncthreads();
+  const int n = (No & 1) ? No + 1 : No;  // padded with a dummy row when No is odd
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int pi = warp; pi < n / 2; pi += nw) {
+        int p, q;
+        if (pi == 0) { p = 0; q = 1 + (r % (n - 1)); }
+        else { p = 1 + ((pi + r) % (n - 1)); q = 1 + ((n - 1 - pi + r) % (n - 1)); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= No) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int a = lane; a < Nv; a += 32) {
+          const double x = B[p * Nv + a], y = B[q * Nv + a];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (al <= 1e-300 || be <= 1e-300) continue;
+        if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int a = lane; a < Nv; a += 32) {
+          const double x = B[p * Nv + a], y = B[q * Nv + a];
+          B[p * Nv + a] = c * x - s * y;
+          B[q * Nv + a] = s * x + c * y;
+        }
+        for (int i = lane; i < No; i += 32) {
+          const double x = J[i * No + p], y = J[i * No + q];
+          J[i * No + p] = c * x - s * y;
+          J[i * No + q] = s * x + c * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  // row norms and descending order
+  for (int k = warp; k < No; k += nw) {
+    double s = 0.0;
+    for (int a = lane; a < Nv; a += 32) s += B[k * Nv + a] * B[k * Nv + a];
+    s = warp_sum(s);
+    if (lane == 0) nrm[k] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < No; ++k) perm[k] = k;
+    for (int k = 0; k < No; ++k) {
+      int best = k;
+      for (int l = k + 1; l < No; ++l)
+        if (nrm[perm[l]] > nrm[perm[best]]) best = l;
+      const int t = perm[k]; perm[k] = perm[best]; perm[best] = t;
+    }
+  }
+  __syncthreads();
+  const double lmax = nrm[perm[0]];
+  // V columns, sign convention, u_k = C v_k / lambda_k.  Done by warp 0 in order so that
+  // columns with a vanishing singular value can be completed against earlier ones.
+  if (warp == 0) {
+    for (int kk = 0; kk < No; ++kk) {
+      const int o = perm[kk];
+      const double l = nrm[o];
+      const bool live = l > 1e-12 * lmax && l > 1e-300;
+      if (live) {
+        for (int a = lane; a < Nv; a += 32) Wv[a * Nv + kk] = B[o * Nv + a] / l;
+      } else {  // Gram-Schmidt completion with the first unit vector that survives
+        for (int m = 0; m < Nv; ++m) {
+          double nn = 0.0;
+          for (int a = lane; a < Nv; a += 32) {
+            double v = (a == m) ? 1.0 : 0.0;
+            for (int prev = 0; prev < kk; ++prev) v -= Wv[m * Nv + prev] * Wv[a * Nv + prev];
+            Wv[a * Nv + kk] = v;
+            nn += v * v;
+          }
+          nn = warp_sum(nn);
+          if (nn > 0.25) {
+            const double inv = 1.0 / sqrt(nn);
+            for (int a = lane; a < Nv; a += 32) Wv[a * Nv + kk] *= inv;
+            break;
+          }
+        }
+      }
+      __syncwarp();
+      // argmax |v| (first occurrence)
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int a = lane; a < Nv; a += 32) {
+        const double v = fabs(Wv[a * Nv + kk]);
+        if (v > best) { best = v; bi = a; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      const double sg = Wv[bi * Nv + kk] < 0 ? -1.0 : 1.0;
+      for (int a = lane; a < Nv; a += 32) Wv[a * Nv + kk] *= sg;
+      __syncwarp();
+      for (int i = lane; i < No; i += 32) {
+        double u;
+        if (live) {
+          u = 0.0;
+          for (int a = 0; a < Nv; ++a) u += C[i * Nv + a] * Wv[a * Nv + kk];
+          u /= l;
+        } else {
+          u = sg * J[i * No + o];
+        }
+        U[i * No + kk] = u;
+      }
+      if (lane == 0) lam[kk] = live ? l : 0.0;
+      __syncwarp();
+    }
+  }
+}
+
+// Householder reflectors triangularising V (columns 0..No-1 of Wv).  A: Nv x No work copy,
+// R: Nv x No reflector vectors (column k holds w_k on rows k..Nv-1), ww: No norms^2.
+__global__ void __launch_bounds__(1024) k_householder(const double *Wv, double *A, double *R, double *ww,
+                                                      int No, int Nv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ double sh_ww;
+  for (int e = threadIdx.x; e < Nv * No; e += blockDim.x) {
+    A[e] = Wv[(e / No) * Nv + (e % No)];
+    R[e] = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < No; ++k) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int r = k + lane; r < Nv; r += 32) s += A[r * No + k] * A[r * No + k];
+      s = warp_sum(s);
+      const double x0 = A[k * No + k];
+      const double alpha = -(x0 >= 0 ? 1.0 : -1.0) * sqrt(s);
+      double w2 = 0.0;
+      for (int r = k + lane; r < Nv; r += 32) {
+        const double w = A[r * No + k] - (r == k ? alpha : 0.0);
+        R[r * No + k] = w;
+        w2 += w * w;
+      }
+      w2 = warp_sum(w2);
+      if (lane == 0) { sh_ww = w2; ww[k] = w2; }
+    }
+    __syncthreads();
+    const double w2 = sh_ww;
+    if (w2 > 0.0) {
+      for (int col = k + warp; col < No; col += nw) {
+        double d = 0.0;
+        for (int r = k + lane; r < Nv; r += 32) d += R[r * No + k] * A[r * No + col];
+        d = warp_sum(d) * (2.0 / w2);
+        for (int r = k + lane; r < Nv; r += 32) A[r * No + col] -= d * R[r * No + k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// AVO column j = H_0 H_1 ... H_{No-1} e_{No+j}, written to Wv[:, No+j].  One warp per column;
+// E is Nv-1-No rows of scratch, row j contiguous.
+__global__ void k_avo(const double *R, const double *ww, double *E, double *Wv, int No, int Nv) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int navo = Nv - No;
+  if (warp >= navo) return;
+  double *e = E + (int64_t)warp * Nv;
+  for (int r = lane; r < Nv; r += 32) e[r] = (r == No + warp) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k = No - 1; k >= 0; --k) {
+    const double w2 = ww[k];
+    if (w2 <= 0.0) continue;
+    double d = 0.0;
+    for (int r = k + lane; r < Nv; r += 32) d += R[r * No + k] * e[r];
+    d = warp_sum(d) * (2.0 / w2);
+    for (int r = k + lane; r < Nv; r += 32) e[r] -= d * R[r * No + k];
+    __syncwarp();
+  }
+  for (int r = lane; r < Nv; r += 32) Wv[(int64_t)r * Nv + No + warp] = e[r];
+}
+
+__global__ void k_assemble_W(const double *U, const double *Wv, double *W, int No, int Nv) {
+  const int N = No + Nv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / N), q = (int)(e % N);
+    double v = 0.0;
+    if (p < No && q < No) v = U[p * No + q];
+    else if (p >= No && q >= No) v = Wv[(int64_t)(p - No) * Nv + (q - No)];
+    W[e] = v;
+  }
+}
+
+// omega = sum_u 2 lam_u^2 (F_u'u' - F_uu);  E0 = E_Phi[F] + omega = 2 sum_i F_ii + omega.
+__global__ void k_scalars(const double *F, const double *lam, double *scal, int No, int Nv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int N = No + Nv;
+  double om = 0.0, eph = 0.0;
+  for (int u = 0; u < No; ++u) {
+    om += 2.0 * lam[u] * lam[u] * (F[(int64_t)(No + u) * N + No + u] - F[(int64_t)u * N + u]);
+    eph += 2.0 * F[(int64_t)u * N + u];
+  }
+  scal[0] = om;
+  scal[1] = eph + om;
+}
+
+// f0_aj: the Fock matrix of the closed-shell determinant Phi, F - G[gamma - gamma_Phi],
+// with gamma - gamma_Phi = -2 lam_u^2 on occupied u and +2 lam_u^2 on TOP virtual u'.
+__global__ void k_f0vo(const double *F, const double *lam, const double *ooov, const double *ovvt,
+                       double *f0, int No, int Nv) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Nv * No) return;
+  const int a = e / No, j = e % No, N = No + Nv;
+  double v = F[(int64_t)j * N + No + a];
+  for (int u = 0; u < No; ++u) {
+    const double w = 2.0 * lam[u] * lam[u];
+    const double aj_uu = ooov[(((int64_t)u * No + u) * No + j) * Nv + a];
+    const double au_uj = ooov[(((int64_t)u * No + j) * No + u) * Nv + a];
+    const double aj_pp = ovvt[(((int64_t)j * Nv + a) * Nv + u) * No + u];
+    const double ap_pj = ovvt[(((int64_t)j * Nv + u) * Nv + a) * No + u];
+    v += w * (aj_uu - 0.5 * au_uj) - w * (aj_pp - 0.5 * ap_pj);
+  }
+  f0[e] = v;
+}
+
+__device__ __forceinline__ bool valid_elem(int blk, int i, int j, int a, int b) {
+  if ((blk == BT || blk == BX || blk == BY) && (i == j || a == b)) return false;
+  if (blk == BX && (i == 0 || j == 0 || a == 0 || b == 0)) return false;
+  if (blk == BZ && (j == 0 || b == 0 || (i == 0 && a == 0))) return false;
+  return true;
+}
+
+// b = Q H Psi0 on the stored blocks (Slater-Condon rules with Psi0 = sum_u lam_u (u -> u')):
+//  doubles: P(ij)P(ab)[s_ia f0_bj] + P(ij) sum_c <ab||cj> s_ic - P(ab) sum_k <kb||ij> s_ka
+//  triples: P(k/ij)P(c/ab)[<ab||ij> s_kc]  (disconnected product of the double and the single)
+__global__ void k_rhs(const double *lam, const double *f0, const double *ovov, const double *ooov,
+                      const double *ovvt, double *out, int No, int Nv) {
+  const int64_t B = (int64_t)No * No * Nv * Nv;
+  const int64_t n = 5 * B;
+  const int64_t sNv = Nv;
+#define OVOV(i, a, j, b) ovov[(((int64_t)(i) * sNv + (a)) * No + (j)) * sNv + (b)]
+#define OOOV(i, j, k, a) ooov[(((int64_t)(i) * No + (j)) * No + (k)) * sNv + (a)]
+#define OVVT(i, a, b, u) ovvt[(((int64_t)(i) * sNv + (a)) * sNv + (b)) * No + (u)]
+#define F0(a, j) f0[(int64_t)(a) * No + (j)]
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t f = e;
+    const int b = (int)(f % Nv); f /= Nv;
+    const int a = (int)(f % Nv); f /= Nv;
+    const int j = (int)(f % No); f /= No;
+    const int i = (int)(f % No); f /= No;
+    const int blk = (int)f;
+    double v = 0.0;
+    if (valid_elem(blk, i, j, a, b)) {
+      const double l0 = lam[0];
+      if (blk == BT) {
+        if (a == i) v += lam[i] * F0(b, j);
+        if (a == j) v -= lam[j] * F0(b, i);
+        if (b == i) v -= lam[i] * F0(a, j);
+        if (b == j) v += lam[j] * F0(a, i);
+        v += lam[i] * (OVVT(j, b, a, i) - OVVT(j, a, b, i)) - lam[j] * (OVVT(i, b, a, j) - OVVT(i, a, b, j));
+        if (a < No) v -= lam[a] * (OOOV(a, i, j, b) - OOOV(a, j, i, b));
+        if (b < No) v += lam[b] * (OOOV(b, i, j, a) - OOOV(b, j, i, a));
+      } else if (blk == BS) {
+        if (a == i) v += lam[i] * F0(b, j);
+        if (b == j) v += lam[j] * F0(a, i);
+        v += lam[i] * OVVT(j, b, a, i) + lam[j] * OVVT(i, a, b, j);
+        if (a < No) v -= lam[a] * OOOV(a, i, j, b);
+        if (b < No) v -= lam[b] * OOOV(b, j, i, a);
+      } else if (blk == BX || blk == BY) {
+        // t j k -> t' b c  (here j,k,b,c = i,j,a,b):  lam_t <bc||jk> + P(jk)P(bc)[lam_k d_ck q(j,b)]
+        v = l0 * (OVOV(i, a, j, b) - OVOV(j, a, i, b));
+        // X: q(j,b) = <t'b||tj> = (t't|bj) - (t'j|bt);  Y: q(j,b) = (t't|bj) (opposite spins)
+        auto q = [&](int jj, int bb) {
+          double r = OVOV(0, 0, jj, bb);
+          if (blk == BX) r -= OVOV(jj, 0, 0, bb);
+          return r;
+        };
+        if (b == j) v += lam[j] * q(i, a);
+        if (b == i) v -= lam[i] * q(j, a);
+        if (a == j) v -= lam[j] * q(i, b);
+        if (a == i) v += lam[i] * q(j, b);
+      } else {  // BZ: i t k -> a t' c  (here k,c = j,b)
+        v = l0 * OVOV(i, a, j, b);
+        if (b == j) v += lam[j] * OVOV(i, a, 0, 0);
+        if (a == i) v += lam[i] * (OVOV(j, b, 0, 0) - OVOV(0, b, j, 0));
+      }
+    }
+    out[e] = v;
+  }
+#undef OVOV
+#undef OOOV
+#undef OVVT
+#undef F0
+}
+
+}  // namespace
+
+esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return ESMP2_OK;
+  h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? ESMP2_ERR_OOM : ESMP2_ERR_CUDA;
+}
+
+esmp2_status setup_top_basis(esmp2_handle *h) {
+  const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
+  cudaStream_t st = h->stream;
+  double *work = nullptr, *Jm = nullptr, *A = nullptr, *R = nullptr, *ww = nullptr, *E = nullptr, *T1 = nullptr;
+  const size_t wbytes = sizeof(double) * (size_t)No * Nv;
+  cudaError_t ce = cudaSuccess;
+  if ((ce = cudaMalloc(&work, wbytes)) != cudaSuccess) return check_cuda(h, ce, "setup alloc");
+  cudaMalloc(&Jm, sizeof(double) * No * No);
+  cudaMalloc(&A, wbytes);
+  cudaMalloc(&R, wbytes);
+  cudaMalloc(&ww, sizeof(double) * No);
+  cudaMalloc(&E, sizeof(double) * (size_t)(Nv - No + 1) * Nv);
+  cudaMalloc(&T1, sizeof(double) * (size_t)N * N);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return check_cuda(h, ce, "setup alloc");
+
+  k_normalise<<<1, 1024, 0, st>>>(h->C, h->C, No * Nv);
+  k_jacobi_svd<<<1, 1024, 0, st>>>(h->C, work, Jm, h->U, h->lam, h->Wv, No, Nv);
+  k_householder<<<1, 1024, 0, st>>>(h->Wv, A, R, ww, No, Nv);
+  const int navo = Nv - No;
+  if (navo > 0) k_avo<<<(unsigned)cdiv((int64_t)navo * 32, 256), 256, 0, st>>>(R, ww, E, h->Wv, No, Nv);
+  k_assemble_W<<<256, 256, 0, st>>>(h->U, h->Wv, h->W, No, Nv);
+  h->launches += 4 + (navo > 0);
+  // F_TOP = W^T F W
+  Gemm64 g{};
+  g.alpha = 1.0; g.beta = 0.0; g.batch = 1;
+  g.M = N; g.N = N; g.K = N;
+  g.A = h->F; g.sAm = N; g.sAk = 1;   // h->F holds the input F here
+  g.B = h->W; g.sBk = N; g.sBn = 1;
+  g.C = T1; g.sCm = N; g.sCn = 1;
+  gemm64(g, st);
+  g.A = h->W; g.sAm = 1; g.sAk = N;
+  g.B = T1; g.sBk = N; g.sBn = 1;
+  g.C = h->F; g.sCm = N; g.sCn = 1;
+  gemm64(g, st);
+  k_scalars<<<1, 32, 0, st>>>(h->F, h->lam, h->scal, No, Nv);
+  h->launches += 3;
+  ce = cudaGetLastError();
+  cudaStreamSynchronize(st);
+  double sc[2];
+  cudaMemcpy(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost);
+  h->omega = sc[0];
+  h->E0 = sc[1];
+  cudaFree(work); cudaFree(Jm); cudaFree(A); cudaFree(R); cudaFree(ww); cudaFree(E); cudaFree(T1);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  return check_cuda(h, ce, "TOP basis");
+}
+
+// Integral transforms (in place on the handle's copies) + f0 + right-hand side.
+// ovov_in / ooov_in / ovvv_in are device copies of the inputs; ovvv_in is consumed.
+esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, double *ovvv_in, double *scratch) {
+  const int No = h->d.No, Nv = h->d.Nv;
+  cudaStream_t st = h->stream;
+  {
+    const int dims[4] = {No, Nv, No, Nv};
+    double *src = ovov_in, *dst = scratch;
+    const double *R[4] = {h->U, h->Wv, h->U, h->Wv};
+    const int K[4] = {No, Nv, No, Nv};
+    for (int m = 0; m < 4; ++m) {
+      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+      double *t = src; src = dst; dst = t;
+    }
+    cudaMemcpyAsync(h->ovov, src, sizeof(double) * h->d.B, cudaMemcpyDeviceToDevice, st);
+  }
+  {
+    const int dims[4] = {No, No, No, Nv};
+    double *src = ooov_in, *dst = scratch;
+    const double *R[4] = {h->U, h->U, h->U, h->Wv};
+    const int K[4] = {No, No, No, Nv};
+    for (int m = 0; m < 4; ++m) {
+      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+      double *t = src; src = dst; dst = t;
+    }
+    cudaMemcpyAsync(h->ooov, src, sizeof(double) * (size_t)No * No * No * Nv, cudaMemcpyDeviceToDevice, st);
+  }
+  {
+    int dims[4] = {No, Nv, Nv, Nv};
+    mode_product(ovvv_in, scratch, dims, 3, h->Wv, No, Nv, st);  // c -> u' (first No columns of Wv)
+    dims[3] = No;
+    double *src = scratch, *dst = ovvv_in;
+    const double *R[3] = {h->U, h->Wv, h->Wv};
+    const int K[3] = {No, Nv, Nv};
+    for (int m = 0; m < 3; ++m) {
+      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+      double *t = src; src = dst; dst = t;
+    }
+    cudaMemcpyAsync(h->ovvt, src, sizeof(double) * (size_t)No * Nv * Nv * No, cudaMemcpyDeviceToDevice, st);
+  }
+  k_f0vo<<<(unsigned)cdiv((int64_t)No * Nv, 256), 256, 0, st>>>(h->F, h->lam, h->ooov, h->ovvt, h->f0vo, No, Nv);
+  k_rhs<<<1216, 256, 0, st>>>(h->lam, h->f0vo, h->ovov, h->ooov, h->ovvt, h->b, No, Nv);
+  h->launches += 2;
+  return check_cuda(h, cudaGetLastError(), "rhs");
+}
+
+}  // namespace esmp2

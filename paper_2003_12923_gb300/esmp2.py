@@ -1,0 +1,211 @@
+"""Thin ctypes binding of libesmp2 (include/esmp2.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch supplies
+device memory and the current stream.  The binding never falls back to host code: if
+the library cannot be loaded, importing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libesmp2.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_NOT_CONVERGED, ERR_INDEFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(9)
+FP64, MIXED_BF16, MIXED_TF32 = 0, 1, 2
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "NOT_CONVERGED", 5: "INDEFINITE",
+           6: "CUDA", 7: "TIMEOUT", 8: "STATE"}
+
+
+class Esmp2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"esmp2 {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("No", ctypes.c_int), ("Nv", ctypes.c_int), ("F", ctypes.c_void_p), ("ovov", ctypes.c_void_p),
+                ("ooov", ctypes.c_void_p), ("ovvv", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("spin", ctypes.c_int), ("inputs_on_device", ctypes.c_int)]
+
+
+class LayoutInfo(ctypes.Structure):
+    _fields_ = [("No", ctypes.c_int), ("Nv", ctypes.c_int), ("block_elems", ctypes.c_int64),
+                ("n_elems", ctypes.c_int64), ("weights", ctypes.c_double * 5), ("omega", ctypes.c_double),
+                ("E0", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("sigma_fp64", ctypes.c_int),
+                ("sigma_lowp", ctypes.c_int), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class EnergyParts(ctypes.Structure):
+    _fields_ = [("E2", ctypes.c_double), ("E2_D", ctypes.c_double), ("E2_L", ctypes.c_double),
+                ("E2_S", ctypes.c_double)]
+
+
+EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
+           "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
+           "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches")
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libesmp2 (no GPU needed to load it).  Raises OSError when it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"libesmp2 not built: {p} is missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(p)
+        P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        L.esmp2_create.restype = I
+        L.esmp2_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Desc)]
+        L.esmp2_destroy.restype = None
+        L.esmp2_destroy.argtypes = [P]
+        L.esmp2_last_error.restype = ctypes.c_char_p
+        L.esmp2_last_error.argtypes = [P]
+        L.esmp2_set_stream.restype = I
+        L.esmp2_set_stream.argtypes = [P, P]
+        L.esmp2_layout.restype = I
+        L.esmp2_layout.argtypes = [P, ctypes.POINTER(LayoutInfo)]
+        L.esmp2_top_basis.restype = I
+        L.esmp2_top_basis.argtypes = [P, P, P, P, P]
+        L.esmp2_sigma.restype = I
+        L.esmp2_sigma.argtypes = [P, P, P, I]
+        L.esmp2_rhs.restype = I
+        L.esmp2_rhs.argtypes = [P, P]
+        L.esmp2_solve.restype = I
+        L.esmp2_solve.argtypes = [P, D, I, I, ctypes.POINTER(SolveInfo)]
+        L.esmp2_get_solution.restype = I
+        L.esmp2_get_solution.argtypes = [P, P]
+        L.esmp2_set_solution.restype = I
+        L.esmp2_set_solution.argtypes = [P, P]
+        L.esmp2_energy.restype = I
+        L.esmp2_energy.argtypes = [P, ctypes.POINTER(EnergyParts)]
+        L.esmp2_kernel_launches.restype = I64
+        L.esmp2_kernel_launches.argtypes = [P]
+        if path is None:
+            _lib = L
+        return L
+
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Handle:
+    """One ESMP2-TOP(1) problem on the current CUDA device.
+
+    Inputs (F, ovov, ooov, ovvv, C) may be float64 numpy arrays (host) or CUDA torch
+    tensors; they are copied during construction."""
+
+    def __init__(self, F, ovov, ooov, ovvv, C, spin: int = 1, stream=None):
+        import torch
+        self.torch = torch
+        self.L = load()
+        No, Nv = C.shape
+        on_dev = hasattr(F, "is_cuda") and F.is_cuda
+        keep = []
+
+        def prep(a):
+            if on_dev:
+                t = a.to(dtype=torch.float64).contiguous()
+            else:
+                t = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+            keep.append(t)
+            return _ptr(t)
+
+        d = Desc(No, Nv, prep(F), prep(ovov), prep(ooov), prep(ovvv), prep(C), spin, 1 if on_dev else 0)
+        self._h = ctypes.c_void_p()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        st = self.L.esmp2_create(ctypes.byref(self._h), ctypes.byref(d))
+        if st != OK:
+            msg = self.L.esmp2_last_error(self._h).decode() if self._h else ""
+            if self._h:
+                self.L.esmp2_destroy(self._h)
+                self._h = None
+            raise Esmp2Error(st, msg)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.L.esmp2_set_stream(self._h, ctypes.c_void_p(s.cuda_stream))
+        lay = LayoutInfo()
+        self._check(self.L.esmp2_layout(self._h, ctypes.byref(lay)))
+        self.No, self.Nv = No, Nv
+        self.n = lay.n_elems
+        self.shape = (5, No, No, Nv, Nv)
+        self.weights = np.array(list(lay.weights))
+        self.omega, self.E0 = lay.omega, lay.E0
+
+    def _check(self, st):
+        if st != OK:
+            raise Esmp2Error(st, self.L.esmp2_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.esmp2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def top_basis(self):
+        No, Nv = self.No, self.Nv
+        U = np.empty((No, No)); lam = np.empty(No); Wv = np.empty((Nv, Nv)); F = np.empty((No + Nv, No + Nv))
+        self._check(self.L.esmp2_top_basis(self._h, U.ctypes.data, lam.ctypes.data, Wv.ctypes.data, F.ctypes.data))
+        return U, lam, Wv, F
+
+    def empty(self):
+        return self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
+
+    def sigma(self, x, precision: int = FP64, out=None):
+        y = self.empty() if out is None else out
+        assert x.is_contiguous() and x.dtype == self.torch.float64 and x.numel() == self.n
+        self._check(self.L.esmp2_sigma(self._h, x.data_ptr(), y.data_ptr(), precision))
+        return y
+
+    def rhs(self):
+        b = self.empty()
+        self._check(self.L.esmp2_rhs(self._h, b.data_ptr()))
+        return b
+
+    def solve(self, tol: float = 1e-10, maxit: int = 500, precision: int = FP64, raise_on_error: bool = True):
+        info = SolveInfo()
+        st = self.L.esmp2_solve(self._h, tol, maxit, precision, ctypes.byref(info))
+        if raise_on_error:
+            self._check(st)
+        return {"status": st, "iterations": info.iterations, "outer": info.outer, "sigma_fp64": info.sigma_fp64,
+                "sigma_lowp": info.sigma_lowp, "rel_residual": info.rel_residual, "seconds": info.seconds}
+
+    def solution(self):
+        x = self.empty()
+        self._check(self.L.esmp2_get_solution(self._h, x.data_ptr()))
+        return x
+
+    def set_solution(self, x):
+        self._check(self.L.esmp2_set_solution(self._h, x.contiguous().data_ptr()))
+
+    def energy(self):
+        e = EnergyParts()
+        self._check(self.L.esmp2_energy(self._h, ctypes.byref(e)))
+        return {"E2": e.E2, "E2_D": e.E2_D, "E2_L": e.E2_L, "E2_S": e.E2_S}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.L.esmp2_kernel_launches(self._h))
