@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""ESMP2-TOP(1) benchmark: time-to-solution of the first-order equation on one GB300.
+
+One step = the whole hot path on one synthetic instance with its inputs already
+resident in HBM: esmp2_create (TOP basis, integral transforms, right-hand side),
+esmp2_solve to a true relative residual below --tol, esmp2_energy (E2_D + E2_L by the
+Hylleraas functional, E2_S by the direct S-space sum), esmp2_destroy.
+value = mean seconds per step (time-to-solution, lower is better).
+e2e   = the same through the public API from pinned HOST buffers (host->device copy
+        of every input and the device->host read of the energy inside the timed region).
+Multi-GPU: instances are independent, so N ranks run N replicas (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ESMP2 time-to-solution (res<1e-8) & sigma TFLOP/s at No=30 Nv=400, mixed vs FP64"
+WORKLOADS = {
+    # name: (No, Nv, seed, sigma_off)
+    "c3": (30, 400, 3, 1e-3),
+    "c2": (20, 200, 1, 1e-3),
+    "c1": (6, 30, 0, 1e-3),
+}
+NOMINAL_FP64_TFLOPS = 1.25      # GB300 float64 (CUDA-core) nominal rate
+NOMINAL_BF16_TFLOPS = 2250.0
+
+
+def comb2(n):
+    return n * (n - 1) // 2
+
+
+def unique_amplitudes(No, Nv):
+    """Unique D+L amplitudes of TOP(1) (S counted once per spin-flip pair)."""
+    T = comb2(No) * comb2(Nv)
+    S = No * No * Nv * Nv / 2.0
+    X = comb2(No - 1) * comb2(Nv - 1)
+    Y = comb2(No) * comb2(Nv)
+    Z = (No * Nv - 1) * (No - 1) * (Nv - 1)
+    return T + S + X + Y + Z
+
+
+def sigma_flops(No, Nv):
+    n = unique_amplitudes(No, Nv)
+    return {"alg_total": 4.0 * n * (No + Nv), "alg_virtual": 4.0 * n * Nv,
+            "exec_virtual": 20.0 * No * No * Nv ** 3, "exec_total": 20.0 * No * No * Nv * Nv * (No + Nv)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(No, Nv, seed, sigma_off):
+    import synth
+    return synth.make_instance(No, Nv, seed, sigma_off=sigma_off)
+
+
+def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
+    """The oracle (O2, as it stands) on this host's cores: sampled sigma elements of the same
+    workload extrapolated to one full sigma build, times the number of sigma builds the
+    oracle's own CG needs on the small instance of the same recipe (No=6, Nv=30, seed 0)."""
+    from oracle import o2, top
+    import synth
+    t0 = time.time()
+    if inst is None:
+        F = synth.fock(No, Nv, seed, sigma_off)
+        C = synth.singles_coefficients(F, No, Nv, seed)
+    else:
+        F, C = inst["F"], inst["C"]
+    U, lam, Wv = top.top_basis(top.normalise_singles(C))
+    Ft = top.transform_fock(F, U, Wv)
+    prep = {"No": No, "Nv": Nv, "F": Ft, "lam": lam,
+            "ovov": np.zeros((No, Nv, No, Nv)), "ooov": np.zeros((No, No, No, Nv)),
+            "ovvt": np.zeros((No, Nv, Nv, No))}   # sigma needs no integrals
+    o = o2.O2(prep)
+    n = 5 * No * No * Nv * Nv
+    x = np.full(n, 1e-3)
+    rng = np.random.default_rng(0)
+    done, t_spent, batch = 0, 0.0, 256
+    while t_spent < budget_s:
+        idx = rng.integers(0, n, batch)
+        ts = time.perf_counter()
+        o.sigma_at(x, idx)
+        t_spent += time.perf_counter() - ts
+        done += batch
+        batch = min(batch * 2, 65536)
+    t_elem = t_spent / done
+    small = synth.make_instance(6, 30, 0)
+    res = o2.solve(top.prepare(small), tol=1e-8)
+    n_sigma = res["iters"] + 2
+    t_sigma = t_elem * n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": t_sigma * n_sigma, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": (f"O2 sigma at {done} random elements of the No={No} Nv={Nv} block vector "
+                       f"({t_spent:.1f} s), extrapolated to {n} elements = {t_sigma:.1f} s per sigma build, "
+                       f"x {n_sigma} builds (O2 plain CG to 1e-8 on No=6 Nv=30 seed 0)"),
+            "t_sigma_s": t_sigma, "n_sigma": n_sigma, "wall_s": time.time() - t0}
+
+
+def run_reference(args):
+    No, Nv, seed, so = WORKLOADS[args.config]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    last = None
+    for _ in range(args.warmup + args.steps):
+        last = cpu_baseline(No, Nv, seed, so, budget_s=args.ref_budget)
+        vals.append(last["value"])
+    v = statistics.mean(vals[args.warmup:])
+    cb = dict(last)
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1) tol={args.tol}"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=2000)
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2003_12923_gb300 import esmp2
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    No, Nv, seed, so = WORKLOADS[args.config]
+    seed = seed + 1000 * rank
+    inst = make_inputs(No, Nv, seed, so)
+    names = ("F", "ovov", "ooov", "ovvv", "C")
+    dins = {k: torch.from_numpy(inst[k]).to(dev) for k in names}
+    lib = esmp2.load()
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = "mixed" if os.environ.get("ESMP2_BENCH_FP64") is None and _mixed_available() else "fp64"
+    prec = esmp2.MIXED_BF16 if prec_name == "mixed" else esmp2.FP64
+    stream = torch.cuda.current_stream()
+
+    def step(inputs):
+        h = esmp2.Handle(*(inputs[k] for k in names))
+        info = h.solve(tol=args.tol, maxit=args.maxit, precision=prec)
+        e = h.energy()
+        n_l = h.kernel_launches
+        h.close()
+        return info, e, n_l
+
+    for _ in range(args.warmup):
+        step(dins)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(uuid)
+    clk.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos, launches = [], 0
+    for _ in range(args.steps):
+        info, e, n_l = step(dins)
+        infos.append((info, e))
+        launches += n_l
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    tts = elapsed / args.steps
+
+    # dominant kernel, timed live: the virtual-index contraction stage of sigma
+    h = esmp2.Handle(*(dins[k] for k in names))
+    x = h.rhs()
+    ms = h.profile_sigma(x, precision=prec, reps=3)
+    fl = sigma_flops(No, Nv)
+    peaks, peak_src = load_peaks()
+    if prec == esmp2.FP64:
+        peak = NOMINAL_FP64_TFLOPS
+        peak_note = "GB300 nominal float64 rate (recipe table); float64 runs on the CUDA cores"
+        bound = "alu"
+        kern_ms = ms[0]
+    else:
+        peak = peaks["bf16_tflops"]
+        peak_note = f"bf16 dense burst, {peak_src} (MEASURED_PEAKS.json)"
+        bound = "tensor"
+        kern_ms = ms[1]
+    achieved = fl["alg_virtual"] / (kern_ms * 1e-3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "virtual-index contraction (N_o^2 N_v^3 terms)",
+                "kernel_ms": kern_ms, "peak_source": peak_note,
+                "achieved_executed": fl["exec_virtual"] / (kern_ms * 1e-3) / 1e12,
+                "stage_ms": [float(v) for v in ms[:5]]}
+    sigma_alg_tflops = fl["alg_total"] / (ms[4] * 1e-3) / 1e12
+    h.close()
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = {}
+        for k in names:
+            t = torch.empty(inst[k].shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = inst[k]
+            pinned[k] = t.numpy()
+        h2d = sum(pinned[k].nbytes for k in names)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info_e, e_e, _ = step(pinned)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        d2h = 8 * 32 * (info_e["iterations"] + 4 * info_e["outer"] + 8) + 8 * 32 * 6
+        e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(No, Nv, seed, so, inst=inst)
+
+    info, e = infos[-1]
+    line = {"metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == esmp2.FP64 else "bf16+f64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1)",
+                       "tol": args.tol, "precision": prec_name, "step": "create+solve+energy, inputs resident",
+                       "l2": "no flush: every block vector (5.8 GB at No=30 Nv=400) is larger than L2"},
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+            "sigma_builds_per_s": 1e3 / ms[4], "sigma_tflops_alg": sigma_alg_tflops,
+            "iterations": info["iterations"], "outer": info["outer"], "sigma_fp64": info["sigma_fp64"],
+            "sigma_lowp": info["sigma_lowp"], "rel_residual": info["rel_residual"], "E2": e["E2"],
+            "E2_parts": e}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _mixed_available():
+    from paper_2003_12923_gb300 import esmp2
+    return getattr(esmp2, "MIXED_READY", False)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -123,6 +123,16 @@ esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv
  * in fp32/fp64.  x and y must not overlap. */
 esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
 
+/* Per-stage device timing of `reps` sigma builds y = A x (same arguments as esmp2_sigma),
+ * measured with CUDA events on the handle's stream; ms[0..7] receives average
+ * milliseconds per build.  ESMP2_FP64: [0] virtual-index contractions, [1] occupied-index
+ * contractions, [2] coupling intermediates, [3] element-wise coupling pass, [4] total.
+ * ESMP2_MIXED_BF16: [0] bf16 rounding of x, [1] virtual-index tcgen05 contraction,
+ * [2] occupied-index pass, [3] coupling + fp32->fp64 pass, [4] total.  Not part of the
+ * method: it exists so that benchmarks can attribute time to kernels. */
+esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p, int reps,
+                                 double *ms);
+
 /* Right-hand side b = Q H Psi0 on D+L (Slater-Condon, Sec. II.B), copied into a
  * caller-owned DEVICE buffer of n_elems float64. */
 esmp2_status esmp2_rhs(esmp2_handle *h, double *b);

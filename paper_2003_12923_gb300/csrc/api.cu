@@ -157,6 +157,15 @@ esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_prec
   return ESMP2_ERR_UNSUPPORTED;
 }
 
+esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p, int reps,
+                                 double *ms) {
+  if (!h || !x || !y || !ms || x == y || reps < 1) return ESMP2_ERR_INVALID_ARG;
+  if (p == ESMP2_FP64) return profile64(h, x, y, reps, ms);
+  if (p == ESMP2_MIXED_BF16) return profile_mixed(h, x, y, reps, ms);
+  h->err = "precision not supported";
+  return ESMP2_ERR_UNSUPPORTED;
+}
+
 esmp2_status esmp2_rhs(esmp2_handle *h, double *b) {
   if (!h || !b) return ESMP2_ERR_INVALID_ARG;
   cudaMemcpyAsync(b, h->b, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);

@@ -96,6 +96,8 @@ esmp2_status setup_top_basis(esmp2_handle *h);
 esmp2_status setup_rhs(esmp2_handle *h);
 esmp2_status sigma64(esmp2_handle *h, const double *x, double *y);
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
+esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
+esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);

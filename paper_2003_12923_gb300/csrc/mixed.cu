@@ -8,6 +8,11 @@ esmp2_status sigma_mixed(esmp2_handle *h, const double *, double *) {
   return ESMP2_ERR_UNSUPPORTED;
 }
 
+esmp2_status profile_mixed(esmp2_handle *h, const double *, double *, int, double *) {
+  h->err = "mixed precision path not built yet";
+  return ESMP2_ERR_UNSUPPORTED;
+}
+
 esmp2_status solve_mixed(esmp2_handle *h, double, int, esmp2_solve_info *) {
   h->err = "mixed precision path not built yet";
   return ESMP2_ERR_UNSUPPORTED;

@@ -208,12 +208,14 @@ void launch_couple32(esmp2_handle *h, const float *x, float *y) {
 }
 
 // Part (1) in float64: four strided batched GEMM passes over all five blocks.
-void contractions64(esmp2_handle *h, const double *x, double *y) {
+// stage 1: the two virtual-index passes (N_o^2 N_v^3); stage 2: the two occupied-index passes.
+void contractions64(esmp2_handle *h, const double *x, double *y, int stage = 3) {
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
   const int64_t B = h->d.B, NvNv = (int64_t)Nv * Nv;
   const double *Fv = h->F + (int64_t)No * N + No;
   const double *Fo = h->F;
   Gemm64 g{};
+  if (stage & 1) {
   // y[r][b] = sum_d x[r][d] Fv[d][b], r = (blk,i,j,a)
   g = Gemm64{};
   g.M = (int)(5 * (int64_t)No * No * Nv); g.N = Nv; g.K = Nv; g.batch = 1; g.alpha = 1.0; g.beta = 0.0;
@@ -228,6 +230,9 @@ void contractions64(esmp2_handle *h, const double *x, double *y) {
   g.B = x; g.sBk = Nv; g.sBn = 1; g.sBb = NvNv;
   g.C = y; g.sCm = Nv; g.sCn = 1; g.sCb = NvNv;
   gemm64(g, h->stream);
+  h->launches += 2;
+  }
+  if (!(stage & 2)) return;
   // y[blk][i][(j a b)] -= sum_l Fo[l][i] x[blk][l][(j a b)]
   g = Gemm64{};
   g.M = No; g.N = (int)((int64_t)No * NvNv); g.K = No; g.batch = 5; g.alpha = -1.0; g.beta = 1.0;
@@ -242,7 +247,39 @@ void contractions64(esmp2_handle *h, const double *x, double *y) {
   g.B = x; g.sBk = NvNv; g.sBn = 1; g.sBb = (int64_t)No * NvNv;
   g.C = y; g.sCm = NvNv; g.sCn = 1; g.sCb = (int64_t)No * NvNv;
   gemm64(g, h->stream);
-  h->launches += 4;
+  h->launches += 2;
+}
+
+// Per-stage timing of `reps` float64 sigma builds (CUDA events on the handle's stream):
+// ms[0] virtual-index GEMMs, ms[1] occupied-index GEMMs, ms[2] coupling intermediates,
+// ms[3] element-wise coupling pass, ms[4] whole sigma.
+esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms) {
+  cudaEvent_t ev[5];
+  for (auto &e : ev) cudaEventCreate(&e);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(ev[0], h->stream);
+    contractions64(h, x, y, 1);
+    cudaEventRecord(ev[1], h->stream);
+    contractions64(h, x, y, 2);
+    cudaEventRecord(ev[2], h->stream);
+    launch_intermediates64(h, x);
+    cudaEventRecord(ev[3], h->stream);
+    launch_couple64(h, x, y);
+    cudaEventRecord(ev[4], h->stream);
+    cudaEventSynchronize(ev[4]);
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[4]);
+    acc[4] += t;
+  }
+  for (int k = 0; k < 5; ++k) ms[k] = acc[k] / reps;
+  for (auto &e : ev) cudaEventDestroy(e);
+  return check_cuda(h, cudaGetLastError(), "profile64");
 }
 
 esmp2_status sigma64(esmp2_handle *h, const double *x, double *y) {

@@ -53,7 +53,7 @@ class EnergyParts(ctypes.Structure):
 
 EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
-           "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches")
+           "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma")
 
 
 def lib_path() -> str:
@@ -95,6 +95,8 @@ def load(path: str | None = None):
         L.esmp2_set_solution.argtypes = [P, P]
         L.esmp2_energy.restype = I
         L.esmp2_energy.argtypes = [P, ctypes.POINTER(EnergyParts)]
+        L.esmp2_profile_sigma.restype = I
+        L.esmp2_profile_sigma.argtypes = [P, P, P, I, I, P]
         L.esmp2_kernel_launches.restype = I64
         L.esmp2_kernel_launches.argtypes = [P]
         if path is None:
@@ -179,6 +181,13 @@ class Handle:
         assert x.is_contiguous() and x.dtype == self.torch.float64 and x.numel() == self.n
         self._check(self.L.esmp2_sigma(self._h, x.data_ptr(), y.data_ptr(), precision))
         return y
+
+    def profile_sigma(self, x, precision: int = FP64, reps: int = 3, out=None):
+        """Average per-stage milliseconds of `reps` sigma builds (see esmp2_profile_sigma)."""
+        y = self.empty() if out is None else out
+        ms = np.zeros(8)
+        self._check(self.L.esmp2_profile_sigma(self._h, x.data_ptr(), y.data_ptr(), precision, reps, ms.ctypes.data))
+        return ms
 
     def rhs(self):
         b = self.empty()
