@@ -133,6 +133,12 @@ esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_prec
 esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p, int reps,
                                  double *ms);
 
+/* The virtual-index contractions alone, y_s = X_s F_vv + F_vv X_s for every slice
+ * s = (block, i, j) of the block vector (no masks, couplings or occupied terms):
+ * ESMP2_FP64 with float64 GEMMs, ESMP2_MIXED_BF16 with the bf16 tcgen05 kernel (fp32
+ * accumulation).  A diagnostic for testing and timing the tensor-core path. */
+esmp2_status esmp2_virtual_contraction(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
+
 /* Right-hand side b = Q H Psi0 on D+L (Slater-Condon, Sec. II.B), copied into a
  * caller-owned DEVICE buffer of n_elems float64. */
 esmp2_status esmp2_rhs(esmp2_handle *h, double *b);

@@ -29,7 +29,7 @@ void free_handle(esmp2_handle *h) {
   void *ptrs[] = {h->C, h->U, h->lam, h->Wv, h->W, h->F, h->f0vo, h->scal, h->ovov, h->ooov, h->ovvt, h->b,
                   h->s64.x, h->s64.r, h->s64.p, h->s64.q, h->s64.w, h->cp.VX, h->cp.OX, h->cp.WZ, h->cp.OZ,
                   h->cp.G, h->cp.H, h->cp.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
-                  h->q32, h->x32};
+                  h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->hred) cudaFreeHost(h->hred);
@@ -166,6 +166,12 @@ esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, es
   return ESMP2_ERR_UNSUPPORTED;
 }
 
+esmp2_status esmp2_virtual_contraction(esmp2_handle *h, const double *x, double *y, esmp2_precision p) {
+  if (!h || !x || !y || x == y) return ESMP2_ERR_INVALID_ARG;
+  if (p != ESMP2_FP64 && p != ESMP2_MIXED_BF16) { h->err = "precision not supported"; return ESMP2_ERR_UNSUPPORTED; }
+  return virtual_contraction(h, x, y, p == ESMP2_MIXED_BF16);
+}
+
 esmp2_status esmp2_rhs(esmp2_handle *h, double *b) {
   if (!h || !b) return ESMP2_ERR_INVALID_ARG;
   cudaMemcpyAsync(b, h->b, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
@@ -182,13 +188,17 @@ esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision
 
 esmp2_status esmp2_get_solution(esmp2_handle *h, double *x) {
   if (!h || !x) return ESMP2_ERR_INVALID_ARG;
-  cudaMemcpyAsync(x, h->s64.x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  if (h->x_semi)
+    rotate_occ(h, h->s64.x, x, h->s64.p, false);
+  else
+    cudaMemcpyAsync(x, h->s64.x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
   return check_cuda(h, cudaGetLastError(), "get_solution");
 }
 
 esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
   if (!h || !x) return ESMP2_ERR_INVALID_ARG;
   cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  h->x_semi = 0;
   return check_cuda(h, cudaGetLastError(), "set_solution");
 }
 

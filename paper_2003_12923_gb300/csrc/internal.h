@@ -46,6 +46,8 @@ struct Couplings {
   double *G;   // [No][Nv]      sum_kc Fov[k][c] (X+Z)[k][j][c][b]
   double *H;   // [No][Nv]      sum_kc Fov[k][c] (Y+Z)[i][k][a][c]
   double *CYZ; // [No][Nv]      sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
+  double *OC1; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][l][j][ab]   (arrow form only)
+  double *OC2; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][i][l][ab]   (arrow form only)
 };
 
 struct Solver64 {
@@ -88,6 +90,13 @@ struct esmp2_handle {
   void *Fvlp = nullptr;     // bf16 Fvv (Nv x Nv, padded)
   float *ylp = nullptr;     // fp32 sigma output (n)
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr;  // inner PCG vectors
+  int *dflag = nullptr;     // device error flag of bounded waits (tcgen05 kernel)
+  // basis whose occupied orbitals 1..No-1 diagonalise F_oo (mixed-precision solves)
+  bool mixed_ready = false;
+  double *Rocc = nullptr, *Rocct = nullptr;  // No x No rotation and its transpose
+  double *Fsemi = nullptr;  // N x N
+  double *bsemi = nullptr;  // right-hand side in that basis (n)
+  int x_semi = 0;           // 1: s64.x is stored in that basis
 };
 
 namespace esmp2 {
@@ -95,6 +104,11 @@ namespace esmp2 {
 esmp2_status setup_top_basis(esmp2_handle *h);
 esmp2_status setup_rhs(esmp2_handle *h);
 esmp2_status sigma64(esmp2_handle *h, const double *x, double *y);
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
+esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
+esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int lowp);
+void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);
+void couple32(esmp2_handle *h, const double *F, const float *x, float *y);
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
@@ -102,5 +116,10 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
+esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
+esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q);
+esmp2_status check_device_flag(esmp2_handle *h);
+void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
+void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 }  // namespace esmp2

@@ -144,6 +144,71 @@ __global__ void k_pcg_p(VCtx c, const double *slots, const double *r, double *p)
     p[e] = c.dinv(e) * r[e] + beta * p[e];
 }
 
+// ---- low-precision inner PCG (vectors of type T, float64 reductions)
+// r = r64 (the fp64 outer residual); d = 0; p = M^-1 r; partials <r,M^-1 r>, <r,r>
+template <typename T>
+__global__ void kt_init(VCtx c, const double *r64, T *r, T *p, T *d, double *red) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = (T)r64[e];
+    const double z = c.dinv(e) * (double)ri, w = c.w(e);
+    r[e] = ri;
+    p[e] = (T)z;
+    d[e] = (T)0;
+    v[0] += w * (double)ri * z;
+    v[1] += w * (double)ri * (double)ri;
+  }
+  block_partials<2>(v, red);
+}
+
+template <typename T>
+__global__ void kt_dot(VCtx c, const T *u, const T *v_, double *red) {
+  double v[1] = {0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    v[0] += c.w(e) * (double)u[e] * (double)v_[e];
+  block_partials<1>(v, red);
+}
+
+template <typename T>
+__global__ void kt_update(VCtx c, const double *slots, T *d, T *r, const T *p, const T *q, double *red) {
+  const double alpha = slots[4];
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    d[e] = (T)((double)d[e] + alpha * (double)p[e]);
+    const double ri = (double)r[e] - alpha * (double)q[e];
+    r[e] = (T)ri;
+    const double w = c.w(e);
+    v[0] += w * ri * c.dinv(e) * ri;
+    v[1] += w * ri * ri;
+  }
+  block_partials<2>(v, red);
+}
+
+template <typename T>
+__global__ void kt_p(VCtx c, const double *slots, const T *r, T *p) {
+  const double beta = slots[5];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = (T)(c.dinv(e) * (double)r[e] + beta * (double)p[e]);
+}
+
+// r = -b - q (fp64 true residual); partials <r,r>, <b,b>
+__global__ void k_residual(VCtx c, const double *b, const double *q, double *r, double *red) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = -b[e] - q[e], w = c.w(e);
+    r[e] = ri;
+    v[0] += w * ri * ri;
+    v[1] += w * b[e] * b[e];
+  }
+  block_partials<2>(v, red);
+}
+
+template <typename T>
+__global__ void kt_accumulate(VCtx c, double *x, const T *d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += (double)d[e];
+}
+
 // per-block <b,x> and <x,Ax> for the Hylleraas functional (10 partial sums)
 __global__ void k_hylleraas(VCtx c, const double *b, const double *x, const double *q, double *red) {
   double v[10];
@@ -256,9 +321,9 @@ __global__ void k_e2s_c(SCtx s, double *red) {
 
 void launch_pcg_init(esmp2_handle *h, const double *b, const double *q, double *r, double *p);
 
-static VCtx vctx(const esmp2_handle *h) {
+static VCtx vctx(const esmp2_handle *h, const double *F = nullptr) {
   VCtx c;
-  c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = h->F; c.omega = h->omega;
+  c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = F ? F : h->F; c.omega = h->omega;
   return c;
 }
 
@@ -281,6 +346,10 @@ double dot_w(esmp2_handle *h, const double *u, const double *v) {
 
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
   auto t0 = std::chrono::steady_clock::now();
+  if (h->x_semi) {  // the plain fp64 solve works in the TOP basis
+    rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
+    h->x_semi = 0;
+  }
   const VCtx c = vctx(h);
   double *x = h->s64.x, *r = h->s64.r, *p = h->s64.p, *q = h->s64.q;
   cudaStream_t st = h->stream;
@@ -340,9 +409,11 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   if (!h->solved) { h->err = "esmp2_energy needs a previous esmp2_solve"; return ESMP2_ERR_STATE; }
   cudaStream_t st = h->stream;
-  esmp2_status s = sigma64(h, h->s64.x, h->s64.q);
+  const double *F = h->x_semi ? h->Fsemi : h->F;
+  const double *bb = h->x_semi ? h->bsemi : h->b;
+  esmp2_status s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q);
   if (s) return s;
-  k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h), h->b, h->s64.x, h->s64.q, h->red);
+  k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.q, h->red);
   k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 10, h->red_out, 3);
   h->launches += 2;
   double sl[32];
@@ -372,6 +443,81 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   parts->E2_S = h->e2s;
   parts->E2 = parts->E2_D + parts->E2_L + parts->E2_S;
   return check_cuda(h, cudaGetLastError(), "energy");
+}
+
+// Mixed precision: float64 iterative refinement around a low-precision inner PCG.
+//   outer:  r = -b - A x with the float64 sigma (true residual; stop when |r|/|b| <= tol)
+//   inner:  A d = r by Jacobi PCG on float32 vectors whose sigma uses the bf16 tcgen05
+//           contraction (fp32 accumulation); x += d.
+// Everything runs in the basis whose occupied orbitals other than t diagonalise F_oo
+// (the solution is rotated back to the TOP basis on request).
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  esmp2_status s = ensure_mixed(h, true);
+  if (s) return s;
+  if (!h->x_semi) {
+    rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);
+    h->x_semi = 1;
+  }
+  cudaStream_t st = h->stream;
+  const VCtx c = vctx(h, h->Fsemi);
+  double *x = h->s64.x, *r = h->s64.r, *q = h->s64.q;
+  float *r32 = h->r32, *p32 = h->p32, *q32 = h->q32, *d32 = h->x32;
+  int outer = 0, inner_total = 0, nsig64 = 0, nsiglow = 0;
+  double relres = 1.0, sl[32];
+  esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
+  const double eta = 0.05;
+  while (true) {
+    if ((s = sigma64_F(h, h->Fsemi, 1, x, q))) return s;
+    ++nsig64;
+    k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, q, r, h->red);
+    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 3);
+    h->launches += 2;
+    if ((s = read_slots(h, sl, 32))) return s;
+    const double rn = std::sqrt(sl[8]), bn = std::sqrt(sl[9]);
+    relres = bn > 0 ? rn / bn : 0.0;
+    if (relres <= tol) { result = ESMP2_OK; break; }
+    if (inner_total >= maxit) break;
+    // inner PCG on A d = r
+    kt_init<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, r, r32, p32, d32, h->red);
+    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 0);
+    h->launches += 2;
+    if ((s = read_slots(h, sl, 32))) return s;
+    const double r0 = std::sqrt(sl[1]);
+    const double target = std::max(eta * r0, 0.25 * tol * bn);
+    int inner = 0;
+    while (inner_total < maxit) {
+      if ((s = sigma_inner(h, p32, q32))) return s;
+      ++nsiglow;
+      kt_dot<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, p32, q32, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
+      kt_update<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, h->red_out, d32, r32, p32, q32, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
+      kt_p<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, h->red_out, r32, p32);
+      h->launches += 5;
+      if ((s = read_slots(h, sl, 32))) return s;
+      ++inner;
+      ++inner_total;
+      if (!(sl[3] > 0.0)) { h->err = "inner CG: p.Ap <= 0"; result = ESMP2_ERR_INDEFINITE; break; }
+      if (std::sqrt(sl[1]) <= target || inner >= 200) break;
+    }
+    if (result == ESMP2_ERR_INDEFINITE) break;
+    kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
+    h->launches += 1;
+    ++outer;
+    if ((s = check_device_flag(h))) return s;
+  }
+  if (result == ESMP2_ERR_NOT_CONVERGED) h->err = "refinement did not reach the tolerance within maxit inner iterations";
+  if (info) {
+    info->iterations = inner_total;
+    info->outer = outer;
+    info->sigma_fp64 = nsig64;
+    info->sigma_lowp = nsiglow;
+    info->rel_residual = relres;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  h->solved = (result == ESMP2_OK || result == ESMP2_ERR_NOT_CONVERGED);
+  return result;
 }
 
 }  // namespace esmp2

@@ -347,7 +347,40 @@ __global__ void k_rhs(const double *lam, const double *f0, const double *ovov, c
 #undef F0
 }
 
+// Eigenvectors of a symmetric m x m block M of F (rows/cols off..off+m-1): one-sided
+// Jacobi SVD of M + shift I, with the shift (1 + largest absolute row sum) making it
+// positive definite so that its singular vectors are its eigenvectors.
+__global__ void k_shifted_block(const double *F, int N, int off, int m, double *M) {
+  __shared__ double shift;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int p = 0; p < m; ++p) {
+      double r = 0.0;
+      for (int q = 0; q < m; ++q) r += fabs(F[(int64_t)(off + p) * N + off + q]);
+      mx = fmax(mx, r);
+    }
+    shift = 1.0 + mx;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int p = e / m, q = e % m;
+    M[e] = F[(int64_t)(off + p) * N + off + q] + (p == q ? shift : 0.0);
+  }
+}
+
 }  // namespace
+
+void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work) {
+  // work: 3 m^2 + m doubles
+  double *M = work, *B = work + m * m, *J = work + 2 * m * m, *lam = work + 3 * m * m;
+  double *Vt = nullptr;
+  cudaMalloc(&Vt, sizeof(double) * m * m);
+  k_shifted_block<<<1, 256, 0, h->stream>>>(F, h->d.N, off, m, M);
+  k_jacobi_svd<<<1, 1024, 0, h->stream>>>(M, B, J, V, lam, Vt, m, m);
+  h->launches += 2;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(Vt);
+}
 
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return ESMP2_OK;

@@ -22,6 +22,7 @@ struct Ctx {
   int64_t B;
   const double *F;
   double omega;
+  int arrow;  // 1: F_oo is diagonal apart from the t row/column (occupied terms done here)
   __device__ __forceinline__ double Fo(int k, int l) const { return F[(int64_t)k * N + l]; }
   __device__ __forceinline__ double Fv(int a, int b) const { return F[(int64_t)(No + a) * N + No + b]; }
   __device__ __forceinline__ double Fov(int k, int a) const { return F[(int64_t)k * N + No + a]; }
@@ -96,6 +97,24 @@ __global__ void k_intermediates(Ctx c, const T *x, Couplings cp) {
     s = warp_sum(s);
     if (lane == 0) cp.H[r] = s;
   }
+  // arrow form of the occupied terms: OC1[blk][j][ab] = sum_{l>=1} Foo[l][0] x[blk][l][j][ab],
+  //                                   OC2[blk][i][ab] = sum_{l>=1} Foo[l][0] x[blk][i][l][ab]
+  if (c.arrow) {
+    const int64_t NvNv = (int64_t)Nv * Nv;
+    for (int64_t e = tid; e < 5 * (int64_t)No * NvNv; e += nthr) {
+      const int64_t ab = e % NvNv;
+      const int64_t r = e / NvNv;
+      const int q = (int)(r % No), blk = (int)(r / No);
+      double s1 = 0.0, s2 = 0.0;
+      for (int l = 1; l < No; ++l) {
+        const double f = c.Fo(l, 0);
+        s1 += f * (double)x[c.at(blk, l, q, 0, 0) + ab];
+        s2 += f * (double)x[c.at(blk, q, l, 0, 0) + ab];
+      }
+      cp.OC1[e] = s1;
+      cp.OC2[e] = s2;
+    }
+  }
   // CYZ[k][c] = sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
   for (int64_t e = tid; e < (int64_t)No * Nv; e += nthr) {
     const int k = (int)(e / Nv), cc = (int)(e % Nv);
@@ -125,6 +144,14 @@ __global__ void k_couple(Ctx c, const TX *x, TY *y, Couplings cp) {
     double v = -c.omega * xe;
     const bool i0 = i == 0, j0 = j == 0, a0 = a == 0, b0 = b == 0;
     const int64_t NoNv = (int64_t)No * Nv, NvNv = (int64_t)Nv * Nv;
+    if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
+      const int64_t ab = (int64_t)a * Nv + b;
+      v -= (c.Fo(i, i) + c.Fo(j, j)) * xe;
+      if (!i0) v -= c.Fo(0, i) * X(blk, 0, j, a, b);
+      else v -= cp.OC1[((int64_t)blk * No + j) * NvNv + ab];
+      if (!j0) v -= c.Fo(0, j) * X(blk, i, 0, a, b);
+      else v -= cp.OC2[((int64_t)blk * No + i) * NvNv + ab];
+    }
     switch (blk) {
       case BT: {
         v += f00 * (X(BX, i, j, a, b) + X(BY, i, j, a, b));
@@ -184,36 +211,37 @@ __global__ void k_couple(Ctx c, const TX *x, TY *y, Couplings cp) {
 
 }  // namespace
 
-static Ctx make_ctx(const esmp2_handle *h) {
+static Ctx make_ctx(const esmp2_handle *h, const double *F, int arrow) {
   Ctx c;
   c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B;
-  c.F = h->F; c.omega = h->omega;
+  c.F = F; c.omega = h->omega; c.arrow = arrow;
   return c;
 }
 
-void launch_intermediates64(esmp2_handle *h, const double *x) {
-  k_intermediates<double><<<1216, 256, 0, h->stream>>>(make_ctx(h), x, h->cp);
+void launch_intermediates64(esmp2_handle *h, const double *F, int arrow, const double *x) {
+  k_intermediates<double><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, arrow), x, h->cp);
   h->launches += 1;
 }
 
-void launch_couple64(esmp2_handle *h, const double *x, double *y) {
-  k_couple<double, double><<<1216, 256, 0, h->stream>>>(make_ctx(h), x, y, h->cp);
+void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
+  k_couple<double, double><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, arrow), x, y, h->cp);
   h->launches += 1;
 }
 
-void launch_couple32(esmp2_handle *h, const float *x, float *y) {
-  k_intermediates<float><<<1216, 256, 0, h->stream>>>(make_ctx(h), x, h->cp);
-  k_couple<float, float><<<1216, 256, 0, h->stream>>>(make_ctx(h), x, y, h->cp);
+// fp32 coupling + arrow occupied pass of the inner (low-precision) sigma
+void couple32(esmp2_handle *h, const double *F, const float *x, float *y) {
+  k_intermediates<float><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, 1), x, h->cp);
+  k_couple<float, float><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, 1), x, y, h->cp);
   h->launches += 2;
 }
 
 // Part (1) in float64: four strided batched GEMM passes over all five blocks.
 // stage 1: the two virtual-index passes (N_o^2 N_v^3); stage 2: the two occupied-index passes.
-void contractions64(esmp2_handle *h, const double *x, double *y, int stage = 3) {
+void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage = 3) {
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
   const int64_t B = h->d.B, NvNv = (int64_t)Nv * Nv;
-  const double *Fv = h->F + (int64_t)No * N + No;
-  const double *Fo = h->F;
+  const double *Fv = F + (int64_t)No * N + No;
+  const double *Fo = F;
   Gemm64 g{};
   if (stage & 1) {
   // y[r][b] = sum_d x[r][d] Fv[d][b], r = (blk,i,j,a)
@@ -259,13 +287,13 @@ esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, do
   double acc[5] = {0, 0, 0, 0, 0};
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(ev[0], h->stream);
-    contractions64(h, x, y, 1);
+    contractions64(h, h->F, x, y, 1);
     cudaEventRecord(ev[1], h->stream);
-    contractions64(h, x, y, 2);
+    contractions64(h, h->F, x, y, 2);
     cudaEventRecord(ev[2], h->stream);
-    launch_intermediates64(h, x);
+    launch_intermediates64(h, h->F, 0, x);
     cudaEventRecord(ev[3], h->stream);
-    launch_couple64(h, x, y);
+    launch_couple64(h, h->F, 0, x, y);
     cudaEventRecord(ev[4], h->stream);
     cudaEventSynchronize(ev[4]);
     for (int k = 0; k < 4; ++k) {
@@ -282,11 +310,23 @@ esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, do
   return check_cuda(h, cudaGetLastError(), "profile64");
 }
 
-esmp2_status sigma64(esmp2_handle *h, const double *x, double *y) {
-  contractions64(h, x, y);
-  launch_intermediates64(h, x);
-  launch_couple64(h, x, y);
+// float64 sigma with an arbitrary orthonormal-basis Fock matrix F (t = occupied 0, t' =
+// virtual 0).  arrow = 1 when F_oo is diagonal apart from its t row and column: then the
+// occupied-index terms are applied element-wise instead of by GEMM.
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
+  contractions64(h, F, x, y, arrow ? 1 : 3);
+  launch_intermediates64(h, F, arrow, x);
+  launch_couple64(h, F, arrow, x, y);
   return check_cuda(h, cudaGetLastError(), "sigma64");
+}
+
+esmp2_status sigma64(esmp2_handle *h, const double *x, double *y) { return sigma64_F(h, h->F, 0, x, y); }
+
+// parts (2)-(3) only: couplings, shift and masks added to y
+esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
+  launch_intermediates64(h, F, arrow, x);
+  launch_couple64(h, F, arrow, x, y);
+  return check_cuda(h, cudaGetLastError(), "sigma64 tail");
 }
 
 }  // namespace esmp2

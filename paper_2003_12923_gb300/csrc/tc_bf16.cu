@@ -1,0 +1,382 @@
+// Virtual-index contractions of the sigma build on the 5th-generation tensor cores.
+//
+// For every slice s = (block, i, j) of the block vector (an Nv x Nv matrix X_s) the two
+// virtual-index terms of the one-body operator are
+//     Y_s = X_s F + F X_s            (F = F_vv, symmetric)
+// i.e. the N_o^2 N_v^3 part of Table 1.  One CTA tile is (s, 128 rows a, <= 256 columns b);
+// both terms accumulate into the same fp32 TMEM accumulator:
+//     term 2: A = X_s[a-tile][c]   (K-major)   B = F[b-tile][c]      (K-major)
+//     term 1: A = F[a-tile][c]     (K-major)   B = X_s[c][b-tile]    (MN-major)
+// so each output element is written once.  Operands are bf16 (rounded copies of x and F),
+// accumulation fp32.
+//
+// Structure (persistent, one CTA per SM, 192 threads):
+//   warp 0      TMA producer: 3-D / 2-D tiled bulk copies, 128-byte swizzle, 2-stage ring
+//   warp 1      tcgen05.mma issuer (one elected thread), commits to mbarriers
+//   warps 2..5  epilogue: tcgen05.ld 32x32b from the accumulator, fp32 stores
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of tile k overlap the main
+// loop of tile k+1.  Every mbarrier wait is bounded by a globaltimer limit; a wait that
+// runs out sets an error flag, skips the remaining work and the CTA still waits (bounded)
+// for its own copies in flight and frees its TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
+#include "internal.h"
+
+namespace esmp2 {
+namespace tc {
+
+constexpr int BM = 128;           // accumulator rows (TMEM lanes)
+constexpr int BN_MAX = 256;       // accumulator columns per tile
+constexpr int BK = 64;            // K elements per stage (128 bytes of bf16)
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+constexpr int B_BYTES = BN_MAX * BK * 2;      // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int NTHREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase of the given parity has completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint64_t limit = WAIT_NS) {
+  const uint32_t a = smem_u32(b);
+  if (mbar_test(a, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_test(a, parity))
+    if (gtimer() - t0 > limit) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *m, uint64_t *bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *m, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4, LBO >> 4 at bit 16, SBO >> 4 at
+// bit 32, descriptor version 1 at bit 46, layout type at bit 61 (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+// Instruction descriptor, kind::f16: D fp32 (bit 4), A bf16 (bits 7-9 = 1), B bf16
+// (bits 10-12 = 1), A K-major, B major at bit 16, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+struct Args {
+  int Nv;          // virtual orbitals (rows and columns of every slice)
+  int S;           // number of slices
+  int a_tiles;     // ceil(Nv / 128)
+  int b_tiles;     // column tiles per slice
+  int bn;          // columns of a full column tile (multiple of 16, <= 256)
+  int nk;          // K chunks: ceil(Nv / 64)
+  int64_t tiles;   // S * a_tiles * b_tiles
+  float *y;        // [S][Nv][Nv]
+  int *err;        // error flag (device)
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_virt(const __grid_constant__ CUtensorMap tXa, const __grid_constant__ CUtensorMap tXb,
+           const __grid_constant__ CUtensorMap tFa, const __grid_constant__ CUtensorMap tFb, Args g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < 2; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], 4); }
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  const int per_slice = g.a_tiles * g.b_tiles;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------------ TMA producer
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+        const int s = (int)(t / per_slice), rem = (int)(t % per_slice);
+        const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
+        for (int kc = 0; kc < g.nk; ++kc, ++it) {
+          const int st = (int)(it % STAGES);
+          const uint32_t rnd = (uint32_t)(it / STAGES);
+          if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) { ok = false; break; }
+          uint8_t *base = smem + st * STAGE_BYTES;
+          uint8_t *A2 = base, *A1 = base + A_BYTES, *B2 = base + 2 * A_BYTES, *B1 = B2 + B_BYTES;
+          // bytes of the boxes below: A2, A1 (128 x 64), B2 (bn x 64), B1 (4 boxes 64 x 64)
+          mbar_expect_tx(&full[st], (uint32_t)(2 * A_BYTES + g.bn * BK * 2 + (BN_MAX / 64) * 64 * BK * 2));
+          const int c0 = kc * BK;
+          tma_3d(A2, &tXa, &full[st], c0, a0, s);
+          tma_2d(A1, &tFa, &full[st], c0, a0);
+          tma_2d(B2, &tFb, &full[st], c0, b0);
+#pragma unroll
+          for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B1 + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, s);
+        }
+      }
+      if (!ok) atomicExch(&fail, 1);
+      // wait (bounded) until no copy of this CTA is still in flight
+      for (int64_t j = it > STAGES ? it - STAGES : 0; j < it; ++j)
+        mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), 100000000ull);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------------ MMA issuer
+      int64_t it = 0;
+      int lt = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++lt) {
+        const int rem = (int)(t % per_slice);
+        const int b0 = (rem % g.b_tiles) * g.bn;
+        const int nvalid = min(g.bn, g.Nv - b0);
+        const int nmma = (nvalid + 15) & ~15;
+        const uint32_t id2 = idesc_bf16(BM, nmma, 0), id1 = idesc_bf16(BM, nmma, 1);
+        const int ab = lt & 1;
+        const uint32_t ar = (uint32_t)(lt >> 1);
+        if (!mbar_wait(&acc_empty[ab], (ar & 1) ^ 1)) { ok = false; break; }
+        tc_after();
+        const uint32_t d = tmem + (uint32_t)(ab * BN_MAX);
+        for (int kc = 0; kc < g.nk; ++kc, ++it) {
+          const int st = (int)(it % STAGES);
+          const uint32_t rnd = (uint32_t)(it / STAGES);
+          if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
+          tc_after();
+          const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t A2 = base, A1 = base + A_BYTES, B2 = base + 2 * A_BYTES, B1 = B2 + B_BYTES;
+          const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);
+          for (int k = 0; k < ksteps; ++k)   // X_s[a][c] F[c][b]
+            umma(d, sdesc(A2 + 32 * k, 16, 1024), sdesc(B2 + 32 * k, 16, 1024), id2, (kc > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < ksteps; ++k)   // F[a][c] X_s[c][b]
+            umma(d, sdesc(A1 + 32 * k, 16, 1024), sdesc(B1 + 2048 * k, BK * 128, 1024), id1, 1u);
+          umma_commit(&empty[st]);
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[ab]);
+      }
+      if (!ok) atomicExch(&fail, 1);
+    }
+  } else {  // ---------------------------------------------------------- epilogue
+    const int quarter = warp & 3;
+    int lt = 0;
+    for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x, ++lt) {
+      const int s = (int)(t / per_slice), rem = (int)(t % per_slice);
+      const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
+      const int nvalid = min(g.bn, g.Nv - b0);
+      const int ab = lt & 1;
+      const uint32_t ar = (uint32_t)(lt >> 1);
+      const bool got = mbar_wait(&acc_full[ab], ar & 1);
+      if (!got) { if (lane == 0) atomicExch(&fail, 1); break; }
+      tc_after();
+      const int row = quarter * 32 + lane;
+      const int a = a0 + row;
+      float *dst = g.y + ((int64_t)s * g.Nv + a) * g.Nv + b0;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * BN_MAX);
+      for (int c = 0; c < nvalid; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)c, v);
+        if (a < g.Nv) {
+          const int m = min(16, nvalid - c);
+          if (m == 16 && (g.Nv & 3) == 0) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            for (int q = 0; q < m; ++q) dst[c + q] = v[q];
+          }
+        }
+      }
+      tc_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+  if (threadIdx.x == 0 && fail) atomicOr(g.err, 1);
+}
+
+// bf16 copies: dst[s][r][c] (row pitch Nvp) = src[s][r][c] (row pitch Nv); pad columns zero.
+template <typename T>
+__global__ void k_to_bf16(const T *src, __nv_bfloat16 *dst, int64_t rows, int Nv, int Nvp) {
+  const int64_t n = rows * Nvp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Nvp;
+    const int c = (int)(e % Nvp);
+    dst[e] = __float2bfloat16_rn(c < Nv ? (float)src[r * Nv + c] : 0.f);
+  }
+}
+
+__global__ void k_fvv_bf16(const double *F, int No, int Nv, int Nvp, __nv_bfloat16 *dst) {
+  const int N = No + Nv;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Nv * Nvp; e += gridDim.x * blockDim.x) {
+    const int r = e / Nvp, c = e % Nvp;
+    dst[e] = __float2bfloat16_rn(c < Nv ? (float)F[(int64_t)(No + r) * N + No + c] : 0.f);
+  }
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------ host side
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encode() {
+  if (g_encode) return true;
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+// bf16 tensor of `rank` dims (innermost first), 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+              const uint32_t *box) {
+  uint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base),
+                        reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides_bytes),
+                        reinterpret_cast<const cuuint32_t *>(box), estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+}  // namespace
+
+// y[s][a][b] = sum_c xb[s][a][c] F[c][b] + sum_c F[a][c] xb[s][c][b]  for S slices (fp32 out).
+// xb: bf16 [S][Nv][Nvp], Fb: bf16 [Nv][Nvp], Nvp = Nv rounded up to 8 (16-byte row pitch).
+esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err) {
+  const int Nv = h->d.Nv;
+  const int Nvp = (Nv + 7) & ~7;
+  if (!get_encode()) { h->err = "cuTensorMapEncodeTiled unavailable"; return ESMP2_ERR_CUDA; }
+  CUtensorMap mXa, mXb, mFa, mFb;
+  const uint64_t dX[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)S};
+  const uint64_t sX[2] = {(uint64_t)Nvp * 2, (uint64_t)Nvp * Nv * 2};
+  const uint64_t dF[2] = {(uint64_t)Nvp, (uint64_t)Nv};
+  const uint64_t sF[1] = {(uint64_t)Nvp * 2};
+  tc::Args g;
+  g.Nv = Nv;
+  g.S = S;
+  g.a_tiles = (Nv + tc::BM - 1) / tc::BM;
+  g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
+  g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
+  g.nk = (Nv + tc::BK - 1) / tc::BK;
+  g.tiles = (int64_t)S * g.a_tiles * g.b_tiles;
+  g.y = y;
+  g.err = err;
+  const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[2] = {64, 128};
+  const uint32_t boxFb[2] = {64, (uint32_t)g.bn};
+  if (!make_map(&mXa, xb, 3, dX, sX, boxXa) || !make_map(&mXb, xb, 3, dX, sX, boxXb) ||
+      !make_map(&mFa, Fb, 2, dF, sF, boxFa) || !make_map(&mFb, Fb, 2, dF, sF, boxFb)) {
+    h->err = "tensor map encoding failed";
+    return ESMP2_ERR_CUDA;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_virt, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(g.tiles, sms);
+  tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, h->stream>>>(mXa, mXb, mFa, mFb, g);
+  h->launches += 1;
+  return check_cuda(h, cudaGetLastError(), "virt_bf16");
+}
+
+void to_bf16_f64(esmp2_handle *h, const double *src, void *dst, int64_t rows) {
+  const int Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  tc::k_to_bf16<double><<<1216, 256, 0, h->stream>>>(src, static_cast<__nv_bfloat16 *>(dst), rows, Nv, Nvp);
+  h->launches += 1;
+}
+void to_bf16_f32(esmp2_handle *h, const float *src, void *dst, int64_t rows) {
+  const int Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  tc::k_to_bf16<float><<<1216, 256, 0, h->stream>>>(src, static_cast<__nv_bfloat16 *>(dst), rows, Nv, Nvp);
+  h->launches += 1;
+}
+void fvv_bf16(esmp2_handle *h, const double *F, void *dst) {
+  const int Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  tc::k_fvv_bf16<<<256, 256, 0, h->stream>>>(F, h->d.No, Nv, Nvp, static_cast<__nv_bfloat16 *>(dst));
+  h->launches += 1;
+}
+
+}  // namespace esmp2

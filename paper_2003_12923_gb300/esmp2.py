@@ -53,7 +53,9 @@ class EnergyParts(ctypes.Structure):
 
 EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
-           "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma")
+           "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma",
+           "esmp2_virtual_contraction")
+MIXED_READY = True
 
 
 def lib_path() -> str:
@@ -97,6 +99,8 @@ def load(path: str | None = None):
         L.esmp2_energy.argtypes = [P, ctypes.POINTER(EnergyParts)]
         L.esmp2_profile_sigma.restype = I
         L.esmp2_profile_sigma.argtypes = [P, P, P, I, I, P]
+        L.esmp2_virtual_contraction.restype = I
+        L.esmp2_virtual_contraction.argtypes = [P, P, P, I]
         L.esmp2_kernel_launches.restype = I64
         L.esmp2_kernel_launches.argtypes = [P]
         if path is None:
@@ -188,6 +192,11 @@ class Handle:
         ms = np.zeros(8)
         self._check(self.L.esmp2_profile_sigma(self._h, x.data_ptr(), y.data_ptr(), precision, reps, ms.ctypes.data))
         return ms
+
+    def virtual_contraction(self, x, precision: int = FP64, out=None):
+        y = self.empty() if out is None else out
+        self._check(self.L.esmp2_virtual_contraction(self._h, x.data_ptr(), y.data_ptr(), precision))
+        return y
 
     def rhs(self):
         b = self.empty()

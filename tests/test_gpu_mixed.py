@@ -1,0 +1,82 @@
+"""The bf16 tcgen05 path: the virtual-index contraction against float64 GEMMs within the
+bf16 rounding bound, the mixed sigma against the oracle, and the refined solve against the
+oracle to float64 tolerances."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import o2, top
+from tests.gpu_util import handle_for, masks, random_block_vector
+
+pytestmark = pytest.mark.gpu
+
+# Nv < 128, Nv > 128 (several row tiles), Nv > 256 (two column tiles), Nv not a multiple of 8
+SIZES = [(3, 5, 21), (4, 9, 22), (5, 13, 23), (7, 70, 24), (6, 30, 0), (4, 130, 25), (3, 300, 26), (2, 450, 27),
+         (3, 401, 28)]
+
+
+def _torch(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _bound(h, x_t, F_vv):
+    """Elementwise bound of the bf16 error: each product carries <= 2^-8 relative error
+    (both operands rounded to 8 significant bits), fp32 accumulation adds far less."""
+    import torch
+    Fa = torch.from_numpy(np.abs(F_vv)).cuda()
+    xa = x_t.abs().reshape(-1, h.Nv, h.Nv)
+    b = xa @ Fa + Fa @ xa
+    return (2.0 ** -7) * b.reshape(h.shape) + 1e-30
+
+
+@pytest.mark.parametrize("No,Nv,seed", SIZES)
+def test_virtual_contraction_bf16(No, Nv, seed):
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed, sigma_off=0.05)
+    h = handle_for(inst)
+    rng = np.random.default_rng(seed)
+    x = _torch(rng.standard_normal((5, No, No, Nv, Nv)))
+    y64 = h.virtual_contraction(x, esmp2.FP64)
+    y16 = h.virtual_contraction(x, esmp2.MIXED_BF16)
+    F = h.top_basis()[3][No:, No:]
+    bound = _bound(h, x, F)
+    err = (y16 - y64).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+    # and it is not trivially passing: the bf16 result differs from fp64 but tracks it closely
+    rel = float(err.norm() / y64.norm())
+    assert 1e-6 < rel < 1e-2, rel
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(4, 9, 31), (6, 30, 0), (3, 300, 32)])
+def test_sigma_mixed_vs_oracle(No, Nv, seed):
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed, sigma_off=0.02)
+    h = handle_for(inst)
+    x = random_block_vector(No, Nv, seed + 7)
+    xt = _torch(x)
+    y = h.sigma(xt, esmp2.MIXED_BF16)
+    ref = o2.O2(top.prepare(inst)).sigma(x)
+    F = h.top_basis()[3][No:, No:]
+    bound = _bound(h, xt, F).cpu().numpy() + 1e-12 * np.abs(ref).max()
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert not np.any(y.cpu().numpy()[~masks(No, Nv)])
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(3, 5, 11), (4, 9, 12), (5, 13, 13), (6, 30, 0)])
+def test_solve_mixed_matches_oracle(No, Nv, seed):
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed)
+    h = handle_for(inst)
+    info = h.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
+    e = h.energy()
+    ref = o2.solve(top.prepare(inst), tol=1e-12)
+    assert info["rel_residual"] <= 1e-11 and info["outer"] >= 1 and info["sigma_lowp"] > 0
+    assert abs(e["E2"] - ref["E2"]) < 1e-10
+    assert abs(e["E2_S"] - ref["E2_S"]) < 1e-12
+    x = h.solution().cpu().numpy()
+    assert np.abs(x - ref["x"]).max() < 1e-8 * np.abs(ref["x"]).max()
+    # the plain fp64 solve continues from the mixed solution (basis handled by the library)
+    info2 = h.solve(tol=1e-11, maxit=50)
+    assert info2["iterations"] <= 2
