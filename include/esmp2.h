@@ -165,6 +165,32 @@ esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
 /* Number of CUDA kernels this handle has launched since creation (for accounting). */
 int64_t esmp2_kernel_launches(const esmp2_handle *h);
 
+/* Allocation-free bf16 virtual-index contraction (the paper has no counterpart; this is a
+ * library service).  Computes, like esmp2_virtual_contraction(..., ESMP2_MIXED_BF16),
+ *     y_s = X_s F + F X_s   for s = 0..S-1,  X_s = x[s] (Nv x Nv),  F = Fvv (Nv x Nv)
+ * with bf16 operands and fp32 accumulation, written to y as float64.  x, Fvv, y are
+ * caller-owned DEVICE buffers (S*Nv*Nv, Nv*Nv, S*Nv*Nv float64), on the current device;
+ * no handle is needed.
+ * For callers that cannot allocate device memory where they call it: code running while
+ * another framework owns the whole device heap through its own caching allocator, and
+ * latency-critical loops where a cudaMalloc/cudaFree pair would synchronise the device.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch (bf16 copies
+ * of x and F, the fp32 accumulator, an error flag) is one file-scope device array of
+ * ESMP2_NOALLOC_MAX_BYTES that every GPU loading this library holds until process exit.
+ * The scratch needed is 256 + (2 Nv Nvp) + (2 S Nv Nvp) + (4 S Nv Nv) bytes (each term
+ * rounded up to 256, Nvp = Nv rounded up to 8); larger requests return
+ * ESMP2_ERR_UNSUPPORTED without touching the device.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (the error flag is cleared on entry), so
+ * calls that overlap on the GPU (different streams or threads) race; serialise them.
+ * The call synchronises `stream` (a cudaStream_t, NULL = legacy default) to read the
+ * kernel's error flag: ESMP2_ERR_TIMEOUT if a bounded device wait gave up, ESMP2_ERR_CUDA
+ * on a CUDA error, ESMP2_ERR_INVALID_ARG on NULL pointers or non-positive sizes. */
+#define ESMP2_NOALLOC_MAX_BYTES (64u << 20)
+esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const double *Fvv, double *y, int S, int Nv,
+                                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -380,3 +380,91 @@ void fvv_bf16(esmp2_handle *h, const double *F, void *dst) {
 }
 
 }  // namespace esmp2
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the bf16 virtual-index contraction.
+//
+// Some callers cannot allocate device memory at the point where they need this
+// contraction: code that runs while another framework owns the whole device heap through
+// its own caching allocator (a cudaMalloc there fails or fragments that allocator's
+// budget), and latency-critical loops where a cudaMalloc/cudaFree pair would synchronise
+// the device.  For them the scratch (bf16 copies of x and F, the fp32 accumulator output
+// and an error flag) lives in one file-scope device array of ESMP2_NOALLOC_MAX_BYTES.
+// Every GPU that loads this library holds that array until the process exits.
+namespace esmp2 {
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[ESMP2_NOALLOC_MAX_BYTES];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+__global__ void k_noalloc_f32_to_f64(const float *src, double *dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace esmp2
+
+extern "C" esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const double *Fvv, double *y, int S,
+                                                         int Nv, void *stream) {
+  using namespace esmp2;
+  if (!x || !Fvv || !y || S < 1 || Nv < 1) return ESMP2_ERR_INVALID_ARG;
+  const int Nvp = (Nv + 7) & ~7;
+  const size_t off_F = 256;
+  const size_t off_x = off_F + align256(sizeof(__nv_bfloat16) * (size_t)Nv * Nvp);
+  const size_t off_y = off_x + align256(sizeof(__nv_bfloat16) * (size_t)S * Nv * Nvp);
+  const size_t total = off_y + align256(sizeof(float) * (size_t)S * Nv * Nv);
+  if (total > (size_t)ESMP2_NOALLOC_MAX_BYTES) return ESMP2_ERR_UNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ESMP2_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device (must precede any stream capture)
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ESMP2_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  if (!get_encode()) return ESMP2_ERR_CUDA;
+  unsigned char *base = g_noalloc_ptr[dev];
+  int *err = reinterpret_cast<int *>(base);
+  auto *Fb = reinterpret_cast<__nv_bfloat16 *>(base + off_F);
+  auto *xb = reinterpret_cast<__nv_bfloat16 *>(base + off_x);
+  float *y32 = reinterpret_cast<float *>(base + off_y);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(err, 0, sizeof(int), st);  // the array keeps the previous call's contents
+  tc::k_fvv_bf16<<<256, 256, 0, st>>>(Fvv, 0, Nv, Nvp, Fb);
+  tc::k_to_bf16<double><<<1216, 256, 0, st>>>(x, xb, (int64_t)S * Nv, Nv, Nvp);
+  CUtensorMap mXa, mXb, mFa, mFb;
+  const uint64_t dX[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)S};
+  const uint64_t sX[2] = {(uint64_t)Nvp * 2, (uint64_t)Nvp * Nv * 2};
+  const uint64_t dF[2] = {(uint64_t)Nvp, (uint64_t)Nv};
+  const uint64_t sF[1] = {(uint64_t)Nvp * 2};
+  tc::Args g;
+  g.Nv = Nv;
+  g.S = S;
+  g.a_tiles = (Nv + tc::BM - 1) / tc::BM;
+  g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
+  g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
+  g.nk = (Nv + tc::BK - 1) / tc::BK;
+  g.tiles = (int64_t)S * g.a_tiles * g.b_tiles;
+  g.y = y32;
+  g.err = err;
+  const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[2] = {64, 128};
+  const uint32_t boxFb[2] = {64, (uint32_t)g.bn};
+  if (!make_map(&mXa, xb, 3, dX, sX, boxXa) || !make_map(&mXb, xb, 3, dX, sX, boxXb) ||
+      !make_map(&mFa, Fb, 2, dF, sF, boxFa) || !make_map(&mFb, Fb, 2, dF, sF, boxFb))
+    return ESMP2_ERR_CUDA;
+  cudaFuncSetAttribute(tc::k_virt, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(g.tiles, sms);
+  tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, st>>>(mXa, mXb, mFa, mFb, g);
+  k_noalloc_f32_to_f64<<<1216, 256, 0, st>>>(y32, y, (int64_t)S * Nv * Nv);
+  int flag = 0;
+  cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ESMP2_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return ESMP2_ERR_CUDA;
+  return flag ? ESMP2_ERR_TIMEOUT : ESMP2_OK;
+}

@@ -54,7 +54,7 @@ class EnergyParts(ctypes.Structure):
 EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
            "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma",
-           "esmp2_virtual_contraction")
+           "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc")
 MIXED_READY = True
 
 
@@ -101,11 +101,24 @@ def load(path: str | None = None):
         L.esmp2_profile_sigma.argtypes = [P, P, P, I, I, P]
         L.esmp2_virtual_contraction.restype = I
         L.esmp2_virtual_contraction.argtypes = [P, P, P, I]
+        L.esmp2_virtual_contraction_noalloc.restype = I
+        L.esmp2_virtual_contraction_noalloc.argtypes = [P, P, P, I, I, P]
         L.esmp2_kernel_launches.restype = I64
         L.esmp2_kernel_launches.argtypes = [P]
         if path is None:
             _lib = L
         return L
+
+
+NOALLOC_MAX_BYTES = 64 << 20
+
+
+def virtual_contraction_noalloc(x, Fvv, y, S: int, Nv: int, stream=None) -> int:
+    """Allocation-free bf16 virtual-index contraction (see include/esmp2.h); returns the status."""
+    L = load()
+    st = 0 if stream is None else stream.cuda_stream
+    return int(L.esmp2_virtual_contraction_noalloc(x.data_ptr(), Fvv.data_ptr(), y.data_ptr(), S, Nv,
+                                                   ctypes.c_void_p(st)))
 
 
 def _ptr(a):
