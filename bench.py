@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the single plain-fp64 solve reported beside the mixed headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -308,6 +310,20 @@ def main():
         d2h = 8 * 32 * (info_e["iterations"] + 4 * info_e["outer"] + 8) + 8 * 32 * 6
         e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    fp64_cmp = None
+    if prec != esmp2.FP64 and not args.no_fp64_compare:
+        # the plain float64 GPU form on the same instance, timed once with CUDA events
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h64 = esmp2.Handle(*(dins[k] for k in names))
+        info64 = h64.solve(tol=args.tol, maxit=args.maxit, precision=esmp2.FP64)
+        en64 = h64.energy()
+        h64.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_cmp = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": info64["iterations"],
+                    "rel_residual": info64["rel_residual"], "E2": en64["E2"]}
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(No, Nv, seed, so, inst=inst)
@@ -325,6 +341,10 @@ def main():
             "iterations": info["iterations"], "outer": info["outer"], "sigma_fp64": info["sigma_fp64"],
             "sigma_lowp": info["sigma_lowp"], "rel_residual": info["rel_residual"], "E2": e["E2"],
             "E2_parts": e}
+    if fp64_cmp is not None:
+        fp64_cmp["E2_mixed_minus_fp64"] = e["E2"] - fp64_cmp["E2"]
+        fp64_cmp["speedup_mixed_over_fp64"] = fp64_cmp["time_to_solution_s"] / tts
+        line["fp64_form"] = fp64_cmp
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -162,6 +162,35 @@ esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x);
  * All reductions in float64.  Requires a previous esmp2_solve (else ERR_STATE). */
 esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
 
+/* Batched solve of independent instances of uneven No/Nv (e.g. several excited states
+ * or molecules).  Each instance i is created from descs[i], solved to the true relative
+ * residual tol with precision p, its energy evaluated, and destroyed; results[i] receives
+ * the status, energies, solve info and launches of instance i.  `concurrency` host
+ * workers each drive their own non-blocking CUDA stream on the current device and take
+ * instances in order from a shared counter, so small instances overlap; device memory in
+ * use is that of `concurrency` instances at a time.  Returns ESMP2_OK if every instance
+ * succeeded, else the first failing status (every instance is still attempted). */
+typedef struct {
+  esmp2_status status;
+  esmp2_energy_parts e2;
+  esmp2_solve_info info;
+  int64_t kernel_launches;
+  char message[160];
+} esmp2_batch_result;
+esmp2_status esmp2_batch_solve(const esmp2_desc *descs, int count, double tol, int maxit, esmp2_precision p,
+                               int concurrency, esmp2_batch_result *results);
+
+/* Analytic gradient of E2 (after esmp2_solve, else ESMP2_ERR_STATE) with respect to the
+ * inputs F and (ia|jb), in the ESMF orbital basis, written to HOST arrays (either may be NULL):
+ *   dF[p][q]           = dE2/dF_pq with E2 evaluated on (F + F^T)/2 (dF is symmetric; a step
+ *                        that moves F_pq and F_qp together changes E2 by (dF_pq + dF_qp) h),
+ *   dOVOV[i][a][j][b]  = dE2/d(ia|jb) with E2 evaluated on the (ia)<->(jb) symmetrised block.
+ * Uses dE2 = 2 <x, db> + <x, dA x> + dE2_S (first-order equation A x = -b, A symmetric, so
+ * the adjoint vector is x; the TOP rotation depends on C only).  adjoint_solve != 0 also
+ * solves A^T lambda = -b in float64 from zero and returns |lambda - x| / |x| in
+ * *adjoint_rel_diff (may be NULL).  The solution in the handle is left unchanged. */
+esmp2_status esmp2_grad(esmp2_handle *h, double *dF, double *dOVOV, int adjoint_solve, double *adjoint_rel_diff);
+
 /* Number of CUDA kernels this handle has launched since creation (for accounting). */
 int64_t esmp2_kernel_launches(const esmp2_handle *h);
 

@@ -28,7 +28,8 @@ bool finite_host(const double *p, size_t n) {
 void free_handle(esmp2_handle *h) {
   void *ptrs[] = {h->C, h->U, h->lam, h->Wv, h->W, h->F, h->f0vo, h->scal, h->ovov, h->ooov, h->ovvt, h->b,
                   h->s64.x, h->s64.r, h->s64.p, h->s64.q, h->s64.w, h->cp.VX, h->cp.OX, h->cp.WZ, h->cp.OZ,
-                  h->cp.G, h->cp.H, h->cp.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
+                  h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
+                  h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -37,18 +38,28 @@ void free_handle(esmp2_handle *h) {
 
 }  // namespace
 
+namespace esmp2 {
+// esmp2_create on a given stream (the batch driver gives each worker its own stream).
+esmp2_status create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStream_t stream);
+}
+
 extern "C" {
 
 const char *esmp2_last_error(const esmp2_handle *h) { return h ? h->err.c_str() : "null handle"; }
 
 int64_t esmp2_kernel_launches(const esmp2_handle *h) { return h ? h->launches : 0; }
 
-esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) {
+esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) { return create_impl(out, d, nullptr); }
+
+}  // extern "C"
+
+esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStream_t stream) {
   if (!out || !d) return ESMP2_ERR_INVALID_ARG;
   *out = nullptr;
   esmp2_handle *h = new (std::nothrow) esmp2_handle();
   if (!h) return ESMP2_ERR_OOM;
   *out = h;
+  h->stream = stream;
   const int No = d->No, Nv = d->Nv;
   if (No < 1 || No > 64 || Nv < No || Nv > 4096) {
     h->err = "require 1 <= No <= 64 and No <= Nv <= 4096";
@@ -81,7 +92,8 @@ esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) {
   ALLOC(h->s64.x, (size_t)h->d.n); ALLOC(h->s64.r, (size_t)h->d.n); ALLOC(h->s64.p, (size_t)h->d.n);
   ALLOC(h->s64.q, (size_t)h->d.n);
   ALLOC(h->cp.VX, (size_t)No * No * Nv); ALLOC(h->cp.OX, (size_t)No * Nv * Nv); ALLOC(h->cp.WZ, (size_t)No * No * Nv);
-  ALLOC(h->cp.OZ, (size_t)No * Nv * Nv); ALLOC(h->cp.G, nC); ALLOC(h->cp.H, nC); ALLOC(h->cp.CYZ, nC);
+  ALLOC(h->cp.OZ, (size_t)No * Nv * Nv); ALLOC(h->cp.G, nC);
+  ALLOC(h->cp.GP, (size_t)No * No * Nv); ALLOC(h->cp.HP, (size_t)No * No * Nv); ALLOC(h->cp.H, nC); ALLOC(h->cp.CYZ, nC);
   {
     const size_t nred = std::max<size_t>((size_t)16 * 1216, (size_t)No * No * No);
     ALLOC(h->red, nred);
@@ -98,11 +110,11 @@ esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) {
     cudaFree(ovov_in); cudaFree(ooov_in); cudaFree(ovvv_in); cudaFree(scratch);
     return check_cuda(h, ce, "input staging");
   }
-  cudaMemcpy(h->F, d->F, sizeof(double) * nF, kind);
-  cudaMemcpy(h->C, d->C, sizeof(double) * nC, kind);
-  cudaMemcpy(ovov_in, d->ovov, sizeof(double) * nOVOV, kind);
-  cudaMemcpy(ooov_in, d->ooov, sizeof(double) * nOOOV, kind);
-  cudaMemcpy(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind);
+  cudaMemcpyAsync(h->F, d->F, sizeof(double) * nF, kind, h->stream);
+  cudaMemcpyAsync(h->C, d->C, sizeof(double) * nC, kind, h->stream);
+  cudaMemcpyAsync(ovov_in, d->ovov, sizeof(double) * nOVOV, kind, h->stream);
+  cudaMemcpyAsync(ooov_in, d->ooov, sizeof(double) * nOOOV, kind, h->stream);
+  cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
   ce = cudaGetLastError();
   esmp2_status s = check_cuda(h, ce, "input copy");
   if (!s) s = setup_top_basis(h);
@@ -116,6 +128,8 @@ esmp2_status esmp2_create(esmp2_handle **out, const esmp2_desc *d) {
   return s;
 #undef ALLOC
 }
+
+extern "C" {
 
 void esmp2_destroy(esmp2_handle *h) {
   if (!h) return;
@@ -200,6 +214,11 @@ esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
   cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
   h->x_semi = 0;
   return check_cuda(h, cudaGetLastError(), "set_solution");
+}
+
+esmp2_status esmp2_grad(esmp2_handle *h, double *dF, double *dOVOV, int adjoint_solve, double *adjoint_rel_diff) {
+  if (!h) return ESMP2_ERR_INVALID_ARG;
+  return gradient(h, dF, dOVOV, adjoint_solve, adjoint_rel_diff);
 }
 
 esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts) {

@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(NT) gemm64_kernel(Gemm64 g, int mtiles) {
       int m, k;
       if (a_kfast) { k = idx % BK; m = idx / BK; } else { m = idx % BM; k = idx / BM; }
       const int gm = m0 + m, gk = k0 + k;
-      As[k][m] = (gm < g.M && gk < g.K) ? A[(int64_t)gm * g.sAm + (int64_t)gk * g.sAk] : 0.0;
+      int64_t ko = (int64_t)gk * g.sAk;
+      if (g.Kin > 0) ko = (int64_t)(gk / g.Kin) * g.sAk1 + (int64_t)(gk % g.Kin) * g.sAk;
+      As[k][m] = (gm < g.M && gk < g.K) ? A[(int64_t)gm * g.sAm + ko] : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < (BN * BK) / NT; ++r) {
@@ -47,7 +49,9 @@ __global__ void __launch_bounds__(NT) gemm64_kernel(Gemm64 g, int mtiles) {
       int n, k;
       if (b_nfast) { n = idx % BN; k = idx / BN; } else { k = idx % BK; n = idx / BK; }
       const int gn = n0 + n, gk = k0 + k;
-      Bs[k][n] = (gn < g.N && gk < g.K) ? B[(int64_t)gk * g.sBk + (int64_t)gn * g.sBn] : 0.0;
+      int64_t ko = (int64_t)gk * g.sBk;
+      if (g.Kin > 0) ko = (int64_t)(gk / g.Kin) * g.sBk1 + (int64_t)(gk % g.Kin) * g.sBk;
+      Bs[k][n] = (gn < g.N && gk < g.K) ? B[ko + (int64_t)gn * g.sBn] : 0.0;
     }
     __syncthreads();
 #pragma unroll

@@ -23,12 +23,16 @@ struct Dims {
 };
 
 // Strided batched float64 GEMM: C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+// Optional K split (Kin > 0): k = k1 * Kin + k0 is addressed as k1 * sAk1 + k0 * sAk in A and
+// k1 * sBk1 + k0 * sBk in B (a sum over slices and one index of each slice in one GEMM).
 struct Gemm64 {
   int M, N, K, batch;
   double alpha, beta;
   const double *A; int64_t sAm, sAk, sAb;
   const double *B; int64_t sBk, sBn, sBb;
   double *C; int64_t sCm, sCn, sCb;
+  int Kin;
+  int64_t sAk1, sBk1;
 };
 void gemm64(const Gemm64 &g, cudaStream_t st);
 
@@ -37,18 +41,22 @@ void gemm64(const Gemm64 &g, cudaStream_t st);
 void mode_product(const double *in, double *out, const int dims[4], int mode, const double *R,
                   int Kout, int64_t ldR, cudaStream_t st);
 
-// Device intermediates of the N^4 coupling terms of sigma.
-struct Couplings {
-  double *VX;  // [No][No][Nv]  sum_c Fov[0][c] X[i][j][c][b]
-  double *OX;  // [No][Nv][Nv]  sum_k Fov[k][0] X[k][j][a][b]
-  double *WZ;  // [No][No][Nv]  sum_c Fov[0][c] Z[i][j][a][c]
-  double *OZ;  // [No][Nv][Nv]  sum_k Fov[k][0] Z[i][k][a][b]
-  double *G;   // [No][Nv]      sum_kc Fov[k][c] (X+Z)[k][j][c][b]
-  double *H;   // [No][Nv]      sum_kc Fov[k][c] (Y+Z)[i][k][a][c]
-  double *CYZ; // [No][Nv]      sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
-  double *OC1; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][l][j][ab]   (arrow form only)
-  double *OC2; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][i][l][ab]   (arrow form only)
+// Device intermediates of the N^4 coupling terms of sigma (compute type CT).
+template <typename CT>
+struct CouplingsT {
+  CT *VX;  // [No][No][Nv]  sum_c Fov[0][c] X[i][j][c][b]
+  CT *OX;  // [No][Nv][Nv]  sum_k Fov[k][0] X[k][j][a][b]
+  CT *WZ;  // [No][No][Nv]  sum_c Fov[0][c] Z[i][j][a][c]
+  CT *OZ;  // [No][Nv][Nv]  sum_k Fov[k][0] Z[i][k][a][b]
+  CT *G;   // [No][Nv]      sum_kc Fov[k][c] (X+Z)[k][j][c][b]
+  CT *GP;  // [No][No][Nv]  sum_c Fov[k][c] (X+Z)[k][j][c][b]   (partial of G)
+  CT *HP;  // [No][No][Nv]  sum_c Fov[j][c] (Y+Z)[i][j][a][c]   (partial of H)
+  CT *H;   // [No][Nv]      sum_kc Fov[k][c] (Y+Z)[i][k][a][c]
+  CT *CYZ; // [No][Nv]      sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
+  CT *OC1; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][l][j][ab]   (arrow form only)
+  CT *OC2; // [5][No][Nv][Nv] sum_{l>=1} Foo[l][0] x[blk][i][l][ab]   (arrow form only)
 };
+using Couplings = CouplingsT<double>;
 
 struct Solver64 {
   double *x, *r, *p, *q, *w;  // fp64 vectors (n)
@@ -79,6 +87,10 @@ struct esmp2_handle {
   double *b = nullptr;      // right-hand side (n)
   esmp2::Solver64 s64{};
   esmp2::Couplings cp{};
+  esmp2::CouplingsT<float> cp32{};
+  float *F32 = nullptr;     // float copy of Fsemi (inner solve)
+  float *dinv32 = nullptr;  // Jacobi preconditioner in that basis (n floats)
+  double *P64 = nullptr;    // x F for the T, S, X, Y blocks (float64 sigma workspace, 4 blocks)
   double *red = nullptr;    // reduction partials
   double *red_out = nullptr;// reduction results (device)
   double *hred = nullptr;   // pinned host copy of reduction results
@@ -108,17 +120,19 @@ esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
 esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int lowp);
 void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);
-void couple32(esmp2_handle *h, const double *F, const float *x, float *y);
+void couple32(esmp2_handle *h, const float *F32, const float *x, float *y);
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
+esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
 esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
 esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q);
 esmp2_status check_device_flag(esmp2_handle *h);
+void antisym_project(esmp2_handle *h, double *v);
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
 void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -103,6 +103,17 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   A(reinterpret_cast<void **>(&h->p32), sizeof(float) * n);
   A(reinterpret_cast<void **>(&h->q32), sizeof(float) * n);
   A(reinterpret_cast<void **>(&h->x32), sizeof(float) * n);
+  A(reinterpret_cast<void **>(&h->F32), sizeof(float) * (size_t)N * N);
+  {
+    const size_t ooN = (size_t)No * No * Nv, oNN = (size_t)No * Nv * Nv, oN = (size_t)No * Nv;
+    auto &c = h->cp32;
+    A(reinterpret_cast<void **>(&c.VX), sizeof(float) * ooN); A(reinterpret_cast<void **>(&c.GP), sizeof(float) * ooN);
+    A(reinterpret_cast<void **>(&c.WZ), sizeof(float) * ooN); A(reinterpret_cast<void **>(&c.HP), sizeof(float) * ooN);
+    A(reinterpret_cast<void **>(&c.OX), sizeof(float) * oNN); A(reinterpret_cast<void **>(&c.OZ), sizeof(float) * oNN);
+    A(reinterpret_cast<void **>(&c.OC1), sizeof(float) * 5 * oNN); A(reinterpret_cast<void **>(&c.OC2), sizeof(float) * 5 * oNN);
+    A(reinterpret_cast<void **>(&c.G), sizeof(float) * oN); A(reinterpret_cast<void **>(&c.H), sizeof(float) * oN);
+    A(reinterpret_cast<void **>(&c.CYZ), sizeof(float) * oN);
+  }
   double *V = nullptr, *work = nullptr, *W2 = nullptr, *T1 = nullptr;
   A(reinterpret_cast<void **>(&V), sizeof(double) * std::max(1, m * m));
   A(reinterpret_cast<void **>(&work), sizeof(double) * (3 * std::max(1, m * m) + std::max(1, m)));
@@ -122,6 +133,8 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   gemm64(g, h->stream);
   h->launches += 3;
   rotate_occ(h, h->b, h->bsemi, h->s64.w ? h->s64.w : h->s64.p, true);
+  k_f64_to_f32<<<64, 256, 0, h->stream>>>(h->Fsemi, h->F32, (int64_t)N * N);
+  h->launches += 1;
   cudaStreamSynchronize(h->stream);
   cudaFree(V); cudaFree(work); cudaFree(W2); cudaFree(T1);
   h->mixed_ready = true;
@@ -149,7 +162,7 @@ esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q) {
   to_bf16_f32(h, p, h->xlp, rows);
   esmp2_status s = virt_bf16(h, h->xlp, h->Fvlp, 5 * No * No, q, h->dflag);
   if (s) return s;
-  couple32(h, h->Fsemi, p, q);
+  couple32(h, h->F32, p, q);
   return check_cuda(h, cudaGetLastError(), "sigma_inner");
 }
 
@@ -204,7 +217,7 @@ esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps
     cudaEventRecord(ev[1], h->stream);
     if ((s = virt_bf16(h, h->xlp, h->Fvlp, 5 * No * No, h->q32, h->dflag))) return s;
     cudaEventRecord(ev[2], h->stream);
-    couple32(h, h->Fsemi, h->p32, h->q32);
+    couple32(h, h->F32, h->p32, h->q32);
     cudaEventRecord(ev[3], h->stream);
     cudaEventSynchronize(ev[3]);
     for (int k = 0; k < 3; ++k) {

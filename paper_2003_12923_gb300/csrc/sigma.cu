@@ -15,23 +15,26 @@
 #include "internal.h"
 
 namespace esmp2 {
+void virt64_sym(esmp2_handle *h, const double *F, const double *x, double *y);
 namespace {
 
-struct Ctx {
+template <typename CT>
+struct CtxT {
   int No, Nv, N;
   int64_t B;
-  const double *F;
-  double omega;
+  const CT *F;
+  CT omega;
   int arrow;  // 1: F_oo is diagonal apart from the t row/column (occupied terms done here)
-  __device__ __forceinline__ double Fo(int k, int l) const { return F[(int64_t)k * N + l]; }
-  __device__ __forceinline__ double Fv(int a, int b) const { return F[(int64_t)(No + a) * N + No + b]; }
-  __device__ __forceinline__ double Fov(int k, int a) const { return F[(int64_t)k * N + No + a]; }
+  __device__ __forceinline__ CT Fo(int k, int l) const { return F[(int64_t)k * N + l]; }
+  __device__ __forceinline__ CT Fv(int a, int b) const { return F[(int64_t)(No + a) * N + No + b]; }
+  __device__ __forceinline__ CT Fov(int k, int a) const { return F[(int64_t)k * N + No + a]; }
   __device__ __forceinline__ int64_t at(int blk, int i, int j, int a, int b) const {
     return blk * B + (((int64_t)i * No + j) * Nv + a) * Nv + b;
   }
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename CT>
+__device__ __forceinline__ CT warp_sum(CT v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -44,104 +47,139 @@ __device__ __forceinline__ bool valid_elem(int blk, int i, int j, int a, int b) 
   return true;
 }
 
-template <typename T>
-__global__ void k_intermediates(Ctx c, const T *x, Couplings cp) {
+// Intermediates of the N^4 coupling terms, spread over four launches so that every sum
+// has enough parallel work (No^2 Nv, No Nv^2 or No^2 Nv warps).
+// (a) per (i, j, b): VX[i][j][b] = sum_c Fov[0][c] X[i][j][c][b],
+//                    GP[k][j][b] = sum_c Fov[k][c] (X+Z)[k][j][c][b]
+template <typename T, typename CT>
+__global__ void k_inter_a(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
   const int No = c.No, Nv = c.Nv;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = tid >> 5, nwarp = nthr >> 5;
-  // VX[i][j][b] = sum_c Fov[0][c] X[i][j][c][b]
-  for (int64_t e = tid; e < (int64_t)No * No * Nv; e += nthr) {
-    const int b = (int)(e % Nv); const int ij = (int)(e / Nv);
-    double s = 0.0;
-    for (int cc = 0; cc < Nv; ++cc) s += c.Fov(0, cc) * (double)x[c.at(BX, 0, 0, 0, 0) + ((int64_t)ij * Nv + cc) * Nv + b];
-    cp.VX[e] = s;
-  }
-  // OX[j][a][b] = sum_k Fov[k][0] X[k][j][a][b];  OZ[i][a][b] = sum_k Fov[k][0] Z[i][k][a][b]
-  for (int64_t e = tid; e < (int64_t)No * Nv * Nv; e += nthr) {
-    const int64_t ab = e % ((int64_t)Nv * Nv);
-    const int j = (int)(e / ((int64_t)Nv * Nv));
-    double s = 0.0, z = 0.0;
-    for (int k = 0; k < No; ++k) {
-      s += c.Fov(k, 0) * (double)x[c.at(BX, k, j, 0, 0) + ab];
-      z += c.Fov(k, 0) * (double)x[c.at(BZ, j, k, 0, 0) + ab];
+  const int64_t n = (int64_t)No * No * Nv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % Nv), ij = (int)(e / Nv), k = ij / No;
+    const T *X = x + c.at(BX, 0, 0, 0, 0) + (int64_t)ij * Nv * Nv + b;
+    const T *Z = x + c.at(BZ, 0, 0, 0, 0) + (int64_t)ij * Nv * Nv + b;
+    CT vx = CT(0), g = CT(0);
+    for (int cc = 0; cc < Nv; ++cc) {
+      const CT xv = (CT)X[(int64_t)cc * Nv], zv = (CT)Z[(int64_t)cc * Nv];
+      vx += c.Fov(0, cc) * xv;
+      g += c.Fov(k, cc) * (xv + zv);
     }
-    cp.OX[e] = s;
-    cp.OZ[e] = z;
-  }
-  // WZ[i][j][a] = sum_c Fov[0][c] Z[i][j][a][c]   (warp per row)
-  for (int64_t r = warp; r < (int64_t)No * No * Nv; r += nwarp) {
-    const T *row = x + c.at(BZ, 0, 0, 0, 0) + r * Nv;
-    double s = 0.0;
-    for (int cc = lane; cc < Nv; cc += 32) s += c.Fov(0, cc) * (double)row[cc];
-    s = warp_sum(s);
-    if (lane == 0) cp.WZ[r] = s;
-  }
-  // G[j][b] = sum_kc Fov[k][c] (X+Z)[k][j][c][b]
-  for (int64_t e = tid; e < (int64_t)No * Nv; e += nthr) {
-    const int j = (int)(e / Nv), b = (int)(e % Nv);
-    double s = 0.0;
-    for (int k = 0; k < No; ++k)
-      for (int cc = 0; cc < Nv; ++cc)
-        s += c.Fov(k, cc) * ((double)x[c.at(BX, k, j, cc, b)] + (double)x[c.at(BZ, k, j, cc, b)]);
-    cp.G[e] = s;
-  }
-  // H[i][a] = sum_kc Fov[k][c] (Y+Z)[i][k][a][c]   (warp per (i,a))
-  for (int64_t r = warp; r < (int64_t)No * Nv; r += nwarp) {
-    const int i = (int)(r / Nv), a = (int)(r % Nv);
-    double s = 0.0;
-    for (int k = 0; k < No; ++k)
-      for (int cc = lane; cc < Nv; cc += 32)
-        s += c.Fov(k, cc) * ((double)x[c.at(BY, i, k, a, cc)] + (double)x[c.at(BZ, i, k, a, cc)]);
-    s = warp_sum(s);
-    if (lane == 0) cp.H[r] = s;
-  }
-  // arrow form of the occupied terms: OC1[blk][j][ab] = sum_{l>=1} Foo[l][0] x[blk][l][j][ab],
-  //                                   OC2[blk][i][ab] = sum_{l>=1} Foo[l][0] x[blk][i][l][ab]
-  if (c.arrow) {
-    const int64_t NvNv = (int64_t)Nv * Nv;
-    for (int64_t e = tid; e < 5 * (int64_t)No * NvNv; e += nthr) {
-      const int64_t ab = e % NvNv;
-      const int64_t r = e / NvNv;
-      const int q = (int)(r % No), blk = (int)(r / No);
-      double s1 = 0.0, s2 = 0.0;
-      for (int l = 1; l < No; ++l) {
-        const double f = c.Fo(l, 0);
-        s1 += f * (double)x[c.at(blk, l, q, 0, 0) + ab];
-        s2 += f * (double)x[c.at(blk, q, l, 0, 0) + ab];
-      }
-      cp.OC1[e] = s1;
-      cp.OC2[e] = s2;
-    }
-  }
-  // CYZ[k][c] = sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
-  for (int64_t e = tid; e < (int64_t)No * Nv; e += nthr) {
-    const int k = (int)(e / Nv), cc = (int)(e % Nv);
-    double s = 0.0;
-    for (int d = 0; d < Nv; ++d) s += c.Fv(0, d) * (double)x[c.at(BZ, 0, k, d, cc)];
-    for (int l = 0; l < No; ++l) s -= c.Fo(l, 0) * (double)x[c.at(BZ, l, k, 0, cc)];
-    cp.CYZ[e] = s;
+    cp.VX[e] = vx;
+    cp.GP[e] = g;
   }
 }
 
-// y += couplings - omega x (+ pair energy on L blocks); y = 0 on non-amplitude slots.
-template <typename TX, typename TY>
-__global__ void k_couple(Ctx c, const TX *x, TY *y, Couplings cp) {
+// (b) per (q, a, b): OX[q][ab] = sum_k Fov[k][0] X[k][q][ab], OZ[q][ab] = sum_k Fov[k][0] Z[q][k][ab];
+//     arrow form: OC1[blk][q][ab] = sum_{l>=1} Foo[l][0] x[blk][l][q][ab], OC2 likewise on the 2nd index
+template <typename T, typename CT>
+__global__ void k_inter_b(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
   const int No = c.No, Nv = c.Nv;
-  const double shift = c.Fv(0, 0) - c.Fo(0, 0);
-  const double f00 = c.Fov(0, 0);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t f = e;
-    const int b = (int)(f % Nv); f /= Nv;
-    const int a = (int)(f % Nv); f /= Nv;
-    const int j = (int)(f % No); f /= No;
-    const int i = (int)(f % No); f /= No;
-    const int blk = (int)f;
+  const int64_t NvNv = (int64_t)Nv * Nv, n = (int64_t)No * NvNv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = e % NvNv;
+    const int q = (int)(e / NvNv);
+    CT s = CT(0), z = CT(0);
+    for (int k = 0; k < No; ++k) {
+      s += c.Fov(k, 0) * (CT)x[c.at(BX, k, q, 0, 0) + ab];
+      z += c.Fov(k, 0) * (CT)x[c.at(BZ, q, k, 0, 0) + ab];
+    }
+    cp.OX[e] = s;
+    cp.OZ[e] = z;
+    if (c.arrow) {
+      for (int blk = 0; blk < 5; ++blk) {
+        CT s1 = CT(0), s2 = CT(0);
+        for (int l = 1; l < No; ++l) {
+          const CT f = c.Fo(l, 0);
+          s1 += f * (CT)x[c.at(blk, l, q, 0, 0) + ab];
+          s2 += f * (CT)x[c.at(blk, q, l, 0, 0) + ab];
+        }
+        cp.OC1[(int64_t)blk * n + e] = s1;
+        cp.OC2[(int64_t)blk * n + e] = s2;
+      }
+    }
+  }
+}
+
+// (c) warp per row (i, j, a): WZ[i][j][a] = sum_c Fov[0][c] Z[i][j][a][c],
+//                             HP[i][j][a] = sum_c Fov[j][c] (Y+Z)[i][j][a][c]
+template <typename T, typename CT>
+__global__ void k_inter_c(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
+  const int No = c.No, Nv = c.Nv, lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)No * No * Nv;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += nw) {
+    const int j = (int)((r / Nv) % No);
+    const T *Y = x + c.at(BY, 0, 0, 0, 0) + r * Nv;
+    const T *Z = x + c.at(BZ, 0, 0, 0, 0) + r * Nv;
+    CT wz = CT(0), hp = CT(0);
+    for (int cc = lane; cc < Nv; cc += 32) {
+      const CT zv = (CT)Z[cc];
+      wz += c.Fov(0, cc) * zv;
+      hp += c.Fov(j, cc) * ((CT)Y[cc] + zv);
+    }
+    wz = warp_sum<CT>(wz);
+    hp = warp_sum<CT>(hp);
+    if (lane == 0) { cp.WZ[r] = wz; cp.HP[r] = hp; }
+  }
+}
+
+// (d) G[j][b] = sum_k GP[k][j][b];  H[i][a] = sum_k HP[i][k][a];
+//     CYZ[k][c] = sum_d Fvv[0][d] Z[0][k][d][c] - sum_l Foo[l][0] Z[l][k][0][c]
+template <typename T, typename CT>
+__global__ void k_inter_d(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
+  const int No = c.No, Nv = c.Nv;
+  const int64_t n = (int64_t)No * Nv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int part = (int)(e / n);
+    const int64_t f = e % n;
+    const int p = (int)(f / Nv), q = (int)(f % Nv);
+    CT s = CT(0);
+    if (part == 0) {
+      for (int k = 0; k < No; ++k) s += cp.GP[((int64_t)k * No + p) * Nv + q];
+      cp.G[f] = s;
+    } else if (part == 1) {
+      for (int k = 0; k < No; ++k) s += cp.HP[((int64_t)p * No + k) * Nv + q];
+      cp.H[f] = s;
+    } else {
+      for (int d = 0; d < Nv; ++d) s += c.Fv(0, d) * (CT)x[c.at(BZ, 0, p, d, q)];
+      for (int l = 0; l < No; ++l) s -= c.Fo(l, 0) * (CT)x[c.at(BZ, l, p, 0, q)];
+      cp.CYZ[f] = s;
+    }
+  }
+}
+
+template <typename T, typename CT>
+void launch_inter(esmp2_handle *h, const CtxT<CT> &c, const T *x, const CouplingsT<CT> &cp) {
+  k_inter_a<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
+  k_inter_b<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
+  k_inter_c<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
+  k_inter_d<T, CT><<<(unsigned)cdiv(3LL * c.No * c.Nv, 256), 256, 0, h->stream>>>(c, x, cp);
+  h->launches += 4;
+}
+
+// y += couplings - omega x (+ pair energy on L blocks); y = 0 on non-amplitude slots.
+template <typename TX, typename TY, typename CT>
+__global__ void k_couple(CtxT<CT> c, const TX *x, TY *y, CouplingsT<CT> cp) {
+  const int No = c.No, Nv = c.Nv, lane = threadIdx.x & 31;
+  const CT shift = c.Fv(0, 0) - c.Fo(0, 0);
+  const CT f00 = c.Fov(0, 0);
+  const int rows = 5 * No * No * Nv;
+  const int w0 = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  for (int r = w0; r < rows; r += nw) {
+    int f = r;
+    const int a = f % Nv; f /= Nv;
+    const int j = f % No; f /= No;
+    const int i = f % No;
+    const int blk = f / No;
+    for (int b = lane; b < Nv; b += 32) {
+    const int64_t e = (int64_t)r * Nv + b;
     if (!valid_elem(blk, i, j, a, b)) { y[e] = (TY)0; continue; }
-    auto X = [&](int bl, int ii, int jj, int aa, int bb) { return (double)x[c.at(bl, ii, jj, aa, bb)]; };
-    const double xe = (double)x[e];
-    double v = -c.omega * xe;
+    auto X = [&](int bl, int ii, int jj, int aa, int bb) { return (CT)x[c.at(bl, ii, jj, aa, bb)]; };
+    const CT xe = (CT)x[e];
+    CT v = -c.omega * xe;
     const bool i0 = i == 0, j0 = j == 0, a0 = a == 0, b0 = b == 0;
     const int64_t NoNv = (int64_t)No * Nv, NvNv = (int64_t)Nv * Nv;
     if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
@@ -199,40 +237,43 @@ __global__ void k_couple(Ctx c, const TX *x, TY *y, Couplings cp) {
         v += shift * xe;
         v += f00 * X(BS, i, j, a, b) - c.Fov(0, b) * X(BS, i, j, a, 0) - c.Fov(j, 0) * X(BS, i, 0, a, b)
            + c.Fov(j, b) * X(BS, i, 0, a, 0) + c.Fov(i, a) * X(BT, 0, j, 0, b);
-        const double y0 = X(BY, 0, j, 0, b);
+        const CT y0 = X(BY, 0, j, 0, b);
         if (i0) v += c.Fv(a, 0) * y0;
         if (a0) v -= c.Fo(0, i) * y0;
         break;
       }
     }
-    y[e] = (TY)((double)y[e] + v);
+    y[e] = (TY)((CT)y[e] + v);
+    }
   }
 }
 
 }  // namespace
 
-static Ctx make_ctx(const esmp2_handle *h, const double *F, int arrow) {
-  Ctx c;
+template <typename CT>
+static CtxT<CT> make_ctx(const esmp2_handle *h, const CT *F, int arrow) {
+  CtxT<CT> c;
   c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B;
-  c.F = F; c.omega = h->omega; c.arrow = arrow;
+  c.F = F; c.omega = (CT)h->omega; c.arrow = arrow;
   return c;
 }
 
 void launch_intermediates64(esmp2_handle *h, const double *F, int arrow, const double *x) {
-  k_intermediates<double><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, arrow), x, h->cp);
-  h->launches += 1;
+  launch_inter<double, double>(h, make_ctx<double>(h, F, arrow), x, h->cp);
 }
 
 void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
-  k_couple<double, double><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, arrow), x, y, h->cp);
+  k_couple<double, double, double><<<1216, 256, 0, h->stream>>>(make_ctx<double>(h, F, arrow), x, y, h->cp);
   h->launches += 1;
 }
 
-// fp32 coupling + arrow occupied pass of the inner (low-precision) sigma
-void couple32(esmp2_handle *h, const double *F, const float *x, float *y) {
-  k_intermediates<float><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, 1), x, h->cp);
-  k_couple<float, float><<<1216, 256, 0, h->stream>>>(make_ctx(h, F, 1), x, y, h->cp);
-  h->launches += 2;
+// float coupling + arrow occupied pass of the inner (low-precision) sigma: float arithmetic
+// throughout (float64 runs at a small fraction of the float32 rate on this part).
+void couple32(esmp2_handle *h, const float *F32, const float *x, float *y) {
+  const CtxT<float> c = make_ctx<float>(h, F32, 1);
+  launch_inter<float, float>(h, c, x, h->cp32);
+  k_couple<float, float, float><<<1216, 256, 0, h->stream>>>(c, x, y, h->cp32);
+  h->launches += 1;
 }
 
 // Part (1) in float64: four strided batched GEMM passes over all five blocks.
@@ -287,7 +328,8 @@ esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, do
   double acc[5] = {0, 0, 0, 0, 0};
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(ev[0], h->stream);
-    contractions64(h, h->F, x, y, 1);
+    if (!h->P64) cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
+    virt64_sym(h, h->F, x, y);
     cudaEventRecord(ev[1], h->stream);
     contractions64(h, h->F, x, y, 2);
     cudaEventRecord(ev[2], h->stream);
@@ -310,11 +352,166 @@ esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, do
   return check_cuda(h, cudaGetLastError(), "profile64");
 }
 
+// ---- float64 virtual-index terms using the storage symmetries of the blocks.
+// T, X, Y slices are antisymmetric (x_s^T = -x_s) and slice (j,i) = -slice (i,j):
+//     y_ij = P_ij - P_ij^T (i < j),  y_ji = -y_ij,  P = x F;
+// S and Z take both GEMM terms (no symmetry is assumed of an input S).
+// Work: 4.75 of the 10 GEMM units of the plain form.
+__global__ void k_combine_sym(int No, int Nv, const double *P, double *y) {
+  __shared__ double t1[32][33], t2[32][33];
+  const int64_t NvNv = (int64_t)Nv * Nv, B = (int64_t)No * No * NvNv;
+  const int tiles = (Nv + 31) / 32;
+  int64_t bid = blockIdx.x;
+  const int tb = (int)(bid % tiles); bid /= tiles;
+  const int ta = (int)(bid % tiles); bid /= tiles;
+  const int j = (int)(bid % No); bid /= No;
+  const int i = (int)(bid % No);
+  const int blk = (int)(bid / No) == 0 ? BT : ((int)(bid / No) == 1 ? BX : BY);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int a0 = ta * 32, b0 = tb * 32;
+  int p = i, q = j;
+  double sg = 1.0;
+  if (i > j) { p = j; q = i; sg = -1.0; }                // y_ij = -(P_ji - P_ji^T)
+  const double *P1 = P + blk * B + ((int64_t)p * No + q) * NvNv;
+  const double *P2 = P1;
+  double *Y = y + blk * B + ((int64_t)i * No + j) * NvNv;
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    t1[r][tx] = (a < Nv && b < Nv) ? P1[(int64_t)a * Nv + b] : 0.0;
+    const int a2 = b0 + r, b2 = a0 + tx;                  // transposed tile of P2
+    t2[r][tx] = (a2 < Nv && b2 < Nv) ? P2[(int64_t)a2 * Nv + b2] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < Nv && b < Nv) {
+      const double v = (i == j) ? 0.0 : sg * (t1[r][tx] - t2[tx][r]);
+      Y[(int64_t)a * Nv + b] = v;
+    }
+  }
+}
+
+// In-place projection of the T, X, Y blocks onto exactly antisymmetric amplitudes:
+// w = (v_ij^ab - v_ji^ab - v_ij^ba + v_ji^ba) / 4 is computed once per canonical element and
+// written with the exact signs to all four images (i == j or a == b slots become zero).
+// The float64 virtual-index pass above relies on this symmetry, so solvers keep their
+// vectors on it.  One CTA per (block, slice pair i <= j, tile pair ta <= tb).
+__global__ void k_antisym_project(int No, int Nv, double *v) {
+  __shared__ double s1[32][33], s2[32][33], s3[32][33], s4[32][33];
+  const int64_t NvNv = (int64_t)Nv * Nv, B = (int64_t)No * No * NvNv;
+  const int tiles = (Nv + 31) / 32;
+  const int npairs = tiles * (tiles + 1) / 2, nslice = No * (No + 1) / 2;
+  int64_t bid = blockIdx.x;
+  int tp = (int)(bid % npairs); bid /= npairs;
+  int sp = (int)(bid % nslice);
+  const int blk = (int)(bid / nslice) == 0 ? BT : ((int)(bid / nslice) == 1 ? BX : BY);
+  int ta = 0;
+  while (tp >= tiles - ta) { tp -= tiles - ta; ++ta; }   // row ta of the upper triangle has tiles-ta pairs
+  const int tb = ta + tp;
+  int i = 0;
+  while (sp >= No - i) { sp -= No - i; ++i; }
+  const int j = i + sp;
+  double *Vij = v + blk * B + ((int64_t)i * No + j) * NvNv;
+  double *Vji = v + blk * B + ((int64_t)j * No + i) * NvNv;
+  const int a0 = ta * 32, b0 = tb * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx, a2 = b0 + r, b2 = a0 + tx;
+    const bool in1 = a < Nv && b < Nv, in2 = a2 < Nv && b2 < Nv;
+    s1[r][tx] = in1 ? Vij[(int64_t)a * Nv + b] : 0.0;
+    s2[r][tx] = in1 ? Vji[(int64_t)a * Nv + b] : 0.0;
+    s3[r][tx] = in2 ? Vij[(int64_t)a2 * Nv + b2] : 0.0;   // v_ij[b][a] with b = b0 + r
+    s4[r][tx] = in2 ? Vji[(int64_t)a2 * Nv + b2] : 0.0;
+  }
+  __syncthreads();
+  // w for element (a = a0 + r, b = b0 + c): needs v_ij[b][a] = s3[c][r]
+  for (int r = ty; r < 32; r += 8) {
+    const int c = tx, a = a0 + r, b = b0 + c;
+    double w = 0.0;
+    const bool canon = (ta < tb) || (r < c);
+    if (i != j && canon) w = 0.25 * (s1[r][c] - s2[r][c] - s3[c][r] + s4[c][r]);
+    s1[r][c] = canon ? w : 0.0;
+    (void)a; (void)b;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < Nv && b < Nv) {
+      const double w = s1[r][tx];
+      if (ta < tb || r < tx) {
+        Vij[(int64_t)a * Nv + b] = w;
+        Vji[(int64_t)a * Nv + b] = -w;
+      } else if (r == tx) {
+        Vij[(int64_t)a * Nv + b] = 0.0;
+        Vji[(int64_t)a * Nv + b] = 0.0;
+      }
+    }
+    // transposed images: (b, a) positions hold -w (ij) and +w (ji)
+    const int a2 = b0 + r, b2 = a0 + tx;   // element (a2, b2) = (b, a) of canonical (b2, a2)
+    if (a2 < Nv && b2 < Nv && (ta < tb || tx < r)) {
+      const double w = s1[tx][r];
+      Vij[(int64_t)a2 * Nv + b2] = -w;
+      Vji[(int64_t)a2 * Nv + b2] = w;
+    }
+  }
+}
+
+void antisym_project(esmp2_handle *h, double *v) {
+  const int No = h->d.No, Nv = h->d.Nv, tiles = (Nv + 31) / 32;
+  const int64_t nb = 3LL * (No * (No + 1) / 2) * (tiles * (tiles + 1) / 2);
+  k_antisym_project<<<(unsigned)nb, 256, 0, h->stream>>>(No, Nv, v);
+  h->launches += 1;
+}
+
+void virt64_sym(esmp2_handle *h, const double *F, const double *x, double *y) {
+  const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
+  const int64_t B = h->d.B, NvNv = (int64_t)Nv * Nv;
+  const double *Fv = F + (int64_t)No * N + No;
+  Gemm64 g{};
+  // P = x F for T, X, Y on the slices i < j
+  g.N = Nv; g.K = Nv; g.batch = 1; g.alpha = 1.0; g.beta = 0.0;
+  g.sAm = Nv; g.sAk = 1; g.B = Fv; g.sBk = N; g.sBn = 1; g.sCm = Nv; g.sCn = 1;
+  int nl = 0;
+  for (int blk : {BT, BX, BY})
+    for (int i = 0; i + 1 < No; ++i) {
+      const int64_t r0 = ((int64_t)i * No + i + 1) * Nv;
+      g.M = (int)((int64_t)(No - 1 - i) * Nv);
+      g.A = x + blk * B + r0 * Nv;
+      g.C = h->P64 + blk * B + r0 * Nv;
+      gemm64(g, h->stream);
+      ++nl;
+    }
+  // S and Z: y = x F + F x directly
+  for (int blk : {BS, BZ}) {
+    g = Gemm64{};
+    g.N = Nv; g.K = Nv; g.batch = 1; g.alpha = 1.0; g.beta = 0.0;
+    g.sAm = Nv; g.sAk = 1; g.B = Fv; g.sBk = N; g.sBn = 1; g.sCm = Nv; g.sCn = 1;
+    g.M = (int)((int64_t)No * No * Nv);
+    g.A = x + blk * B; g.C = y + blk * B;
+    gemm64(g, h->stream);
+    g = Gemm64{};
+    g.M = Nv; g.N = Nv; g.K = Nv; g.batch = No * No; g.alpha = 1.0; g.beta = 1.0;
+    g.A = Fv; g.sAm = N; g.sAk = 1; g.sAb = 0;
+    g.B = x + blk * B; g.sBk = Nv; g.sBn = 1; g.sBb = NvNv;
+    g.C = y + blk * B; g.sCm = Nv; g.sCn = 1; g.sCb = NvNv;
+    gemm64(g, h->stream);
+    nl += 2;
+  }
+  const int tiles = (Nv + 31) / 32;
+  const int64_t nblocks = 3LL * No * No * tiles * tiles;
+  k_combine_sym<<<(unsigned)nblocks, 256, 0, h->stream>>>(No, Nv, h->P64, y);
+  h->launches += nl + 1;
+}
+
 // float64 sigma with an arbitrary orthonormal-basis Fock matrix F (t = occupied 0, t' =
 // virtual 0).  arrow = 1 when F_oo is diagonal apart from its t row and column: then the
 // occupied-index terms are applied element-wise instead of by GEMM.
 esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
-  contractions64(h, F, x, y, arrow ? 1 : 3);
+  if (!h->P64) {
+    cudaError_t e = cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
+    if (e != cudaSuccess) return check_cuda(h, e, "sigma64 workspace");
+  }
+  virt64_sym(h, F, x, y);
+  if (!arrow) contractions64(h, F, x, y, 2);
   launch_intermediates64(h, F, arrow, x);
   launch_couple64(h, F, arrow, x, y);
   return check_cuda(h, cudaGetLastError(), "sigma64");

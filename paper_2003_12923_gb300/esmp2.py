@@ -51,10 +51,15 @@ class EnergyParts(ctypes.Structure):
                 ("E2_S", ctypes.c_double)]
 
 
+class BatchResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("e2", EnergyParts), ("info", SolveInfo),
+                ("kernel_launches", ctypes.c_int64), ("message", ctypes.c_char * 160)]
+
+
 EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
            "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma",
-           "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc")
+           "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc", "esmp2_batch_solve", "esmp2_grad")
 MIXED_READY = True
 
 
@@ -103,6 +108,10 @@ def load(path: str | None = None):
         L.esmp2_virtual_contraction.argtypes = [P, P, P, I]
         L.esmp2_virtual_contraction_noalloc.restype = I
         L.esmp2_virtual_contraction_noalloc.argtypes = [P, P, P, I, I, P]
+        L.esmp2_batch_solve.restype = I
+        L.esmp2_batch_solve.argtypes = [ctypes.POINTER(Desc), I, D, I, I, I, ctypes.POINTER(BatchResult)]
+        L.esmp2_grad.restype = I
+        L.esmp2_grad.argtypes = [P, P, P, I, P]
         L.esmp2_kernel_launches.restype = I64
         L.esmp2_kernel_launches.argtypes = [P]
         if path is None:
@@ -111,6 +120,28 @@ def load(path: str | None = None):
 
 
 NOALLOC_MAX_BYTES = 64 << 20
+
+
+def batch_solve(instances, tol: float = 1e-8, maxit: int = 2000, precision: int = FP64, concurrency: int = 2):
+    """Solve independent instances (dicts with F, ovov, ooov, ovvv, C as float64 host arrays)
+    through esmp2_batch_solve; returns (status, list of per-instance result dicts)."""
+    L = load()
+    keep = []
+    descs = (Desc * len(instances))()
+    for k, inst in enumerate(instances):
+        arrs = [np.ascontiguousarray(np.asarray(inst[n], dtype=np.float64)) for n in ("F", "ovov", "ooov", "ovvv", "C")]
+        keep.append(arrs)
+        No, Nv = arrs[4].shape
+        descs[k] = Desc(No, Nv, *(a.ctypes.data for a in arrs), 1, 0)
+    res = (BatchResult * len(instances))()
+    st = L.esmp2_batch_solve(descs, len(instances), tol, maxit, precision, concurrency, res)
+    out = []
+    for r in res:
+        out.append({"status": r.status, "E2": r.e2.E2, "E2_D": r.e2.E2_D, "E2_L": r.e2.E2_L, "E2_S": r.e2.E2_S,
+                    "iterations": r.info.iterations, "outer": r.info.outer, "rel_residual": r.info.rel_residual,
+                    "seconds": r.info.seconds, "kernel_launches": r.kernel_launches,
+                    "message": r.message.decode(errors="replace")})
+    return int(st), out
 
 
 def virtual_contraction_noalloc(x, Fvv, y, S: int, Nv: int, stream=None) -> int:
@@ -236,6 +267,16 @@ class Handle:
         e = EnergyParts()
         self._check(self.L.esmp2_energy(self._h, ctypes.byref(e)))
         return {"E2": e.E2, "E2_D": e.E2_D, "E2_L": e.E2_L, "E2_S": e.E2_S}
+
+    def grad(self, adjoint_solve: bool = False):
+        """(dE2/dF, dE2/d(ia|jb), adjoint |lambda - x|/|x|) in the ESMF basis (see esmp2_grad)."""
+        No, Nv = self.No, self.Nv
+        dF = np.empty((No + Nv, No + Nv))
+        dov = np.empty((No, Nv, No, Nv))
+        diff = ctypes.c_double(0.0)
+        self._check(self.L.esmp2_grad(self._h, dF.ctypes.data, dov.ctypes.data, 1 if adjoint_solve else 0,
+                                      ctypes.byref(diff)))
+        return dF, dov, diff.value
 
     @property
     def kernel_launches(self) -> int:
