@@ -55,7 +55,12 @@ typedef enum {
 typedef enum {
   ESMP2_FP64 = 0,        /* every contraction in float64 */
   ESMP2_MIXED_BF16 = 1,  /* sigma contractions bf16 x bf16 -> fp32 (tcgen05) inside fp64 refinement */
-  ESMP2_MIXED_TF32 = 2   /* reserved: tf32 inner contractions (returns ESMP2_ERR_UNSUPPORTED) */
+  ESMP2_MIXED_TF32 = 2,  /* reserved: tf32 inner contractions (returns ESMP2_ERR_UNSUPPORTED) */
+  ESMP2_FP64_TC = 3      /* float64-accurate virtual-index terms: x and F_vv split into exact 6-bit
+                            bf16 digits (per-slice power-of-two scale), digit products summed exactly
+                            in fp32 on tcgen05 level by level (levels 2..10) and combined in float64;
+                            other terms float64.  Agrees with float64 GEMMs to a few 1e-15 of each
+                            slice's largest element.  Needs Nv < 910 (exact fp32 level sums). */
 } esmp2_precision;
 
 typedef struct esmp2_handle esmp2_handle;

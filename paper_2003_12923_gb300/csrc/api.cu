@@ -1,5 +1,6 @@
 // C ABI entry points of the ESMP2 library (declared in include/esmp2.h).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -30,7 +31,8 @@ void free_handle(esmp2_handle *h) {
                   h->s64.x, h->s64.r, h->s64.p, h->s64.q, h->s64.w, h->cp.VX, h->cp.OX, h->cp.WZ, h->cp.OZ,
                   h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
                   h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
-                  h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2};
+                  h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
+                  h->xdig, h->Fdig, h->es, h->slist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->hred) cudaFreeHost(h->hred);
@@ -166,6 +168,10 @@ esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv
 esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p) {
   if (!h || !x || !y || x == y) return ESMP2_ERR_INVALID_ARG;
   if (p == ESMP2_FP64) return sigma64(h, x, y);
+  if (p == ESMP2_FP64_TC) {
+    if (!split_supported(h, kFp64TcLevels)) { h->err = "ESMP2_FP64_TC needs Nv < 910"; return ESMP2_ERR_UNSUPPORTED; }
+    return sigma64(h, x, y, kFp64TcLevels);
+  }
   if (p == ESMP2_MIXED_BF16) return sigma_mixed(h, x, y);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
@@ -175,6 +181,7 @@ esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, es
                                  double *ms) {
   if (!h || !x || !y || !ms || x == y || reps < 1) return ESMP2_ERR_INVALID_ARG;
   if (p == ESMP2_FP64) return profile64(h, x, y, reps, ms);
+  if (p == ESMP2_FP64_TC && split_supported(h, kFp64TcLevels)) return profile64(h, x, y, reps, ms, kFp64TcLevels);
   if (p == ESMP2_MIXED_BF16) return profile_mixed(h, x, y, reps, ms);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
@@ -182,8 +189,11 @@ esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, es
 
 esmp2_status esmp2_virtual_contraction(esmp2_handle *h, const double *x, double *y, esmp2_precision p) {
   if (!h || !x || !y || x == y) return ESMP2_ERR_INVALID_ARG;
-  if (p != ESMP2_FP64 && p != ESMP2_MIXED_BF16) { h->err = "precision not supported"; return ESMP2_ERR_UNSUPPORTED; }
-  return virtual_contraction(h, x, y, p == ESMP2_MIXED_BF16);
+  if (p == ESMP2_FP64) return virtual_contraction(h, x, y, 0);
+  if (p == ESMP2_MIXED_BF16) return virtual_contraction(h, x, y, 1);
+  if (p == ESMP2_FP64_TC && split_supported(h, kFp64TcLevels)) return virtual_contraction(h, x, y, 2);
+  h->err = "precision not supported";
+  return ESMP2_ERR_UNSUPPORTED;
 }
 
 esmp2_status esmp2_rhs(esmp2_handle *h, double *b) {
@@ -195,6 +205,10 @@ esmp2_status esmp2_rhs(esmp2_handle *h, double *b) {
 esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision p, esmp2_solve_info *info) {
   if (!h || !(tol > 0) || maxit < 1) return ESMP2_ERR_INVALID_ARG;
   if (p == ESMP2_FP64) return solve64(h, tol, maxit, info);
+  if (p == ESMP2_FP64_TC) {
+    if (!split_supported(h, kFp64TcLevels)) { h->err = "ESMP2_FP64_TC needs Nv < 910"; return ESMP2_ERR_UNSUPPORTED; }
+    return solve64(h, tol, maxit, info, 1);
+  }
   if (p == ESMP2_MIXED_BF16) return solve_mixed(h, tol, maxit, info);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
@@ -213,6 +227,7 @@ esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
   if (!h || !x) return ESMP2_ERR_INVALID_ARG;
   cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
   h->x_semi = 0;
+  h->x_zero = false;
   return check_cuda(h, cudaGetLastError(), "set_solution");
 }
 

@@ -401,6 +401,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
     if (ce != cudaSuccess) return check_cuda(h, ce, "adjoint");
     cudaMemcpyAsync(xs, h->s64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(h->s64.x, 0, sizeof(double) * n, st);
+    h->x_zero = true;
     esmp2_solve_info info{};
     esmp2_status s = solve64(h, 1e-12, 5000, &info);
     if (s != ESMP2_OK && s != ESMP2_ERR_NOT_CONVERGED) { cudaFree(xs); return s; }
@@ -412,6 +413,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
     for (int64_t k = 0; k < n; ++k) { dd += (a[k] - b[k]) * (a[k] - b[k]); xx += b[k] * b[k]; }
     if (adj_diff) *adj_diff = xx > 0 ? std::sqrt(dd / xx) : 0.0;
     cudaMemcpyAsync(h->s64.x, xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    h->x_zero = false;
     cudaStreamSynchronize(st);
     cudaFree(xs);
   }

@@ -109,22 +109,30 @@ struct esmp2_handle {
   double *Fsemi = nullptr;  // N x N
   double *bsemi = nullptr;  // right-hand side in that basis (n)
   int x_semi = 0;           // 1: s64.x is stored in that basis
+  bool x_zero = true;       // s64.x is known to be zero (its sigma is zero, no build needed)
+  // float64-accurate virtual-index terms from exact bf16 digit products (tcgen05)
+  void *xdig = nullptr;     // digit planes of x [levels-1][5 No^2][Nv][Nvp] bf16
+  void *Fdig = nullptr;     // digit planes of F_vv [levels-1][Nv][Nvp] bf16
+  int *es = nullptr;        // per-slice exponents (5 No^2) and that of F_vv (last entry)
+  int *slist = nullptr;     // slices of the symmetric form (T, X, Y with i < j; all S, Z)
+  int nslist = 0, eF = 0;
+  int last_precision = 0;   // precision of the last solve (the energy's sigma follows it)
 };
 
 namespace esmp2 {
 // kernels.cu
 esmp2_status setup_top_basis(esmp2_handle *h);
 esmp2_status setup_rhs(esmp2_handle *h);
-esmp2_status sigma64(esmp2_handle *h, const double *x, double *y);
-esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
+esmp2_status sigma64(esmp2_handle *h, const double *x, double *y, int tc_levels = 0);
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels = 0);
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
-esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int lowp);
+esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int mode);
 void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);
 void couple32(esmp2_handle *h, const float *F32, const float *x, float *y);
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
-esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
+esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels = 0);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
-esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
+esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc = 0);
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
@@ -133,6 +141,12 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
 esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q);
 esmp2_status check_device_flag(esmp2_handle *h);
 void antisym_project(esmp2_handle *h, double *v);
+void combine_sym(esmp2_handle *h, double *y);
+constexpr int kFp64TcLevels = 10;  // digit levels of the float64-exact tensor-core contraction
+int split_levels_for(double tol);
+bool split_supported(const esmp2_handle *h, int levels);
+esmp2_status ensure_split(esmp2_handle *h);
+esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64, int sym, int levels);
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
 void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -421,7 +421,7 @@ double dot_w(esmp2_handle *h, const double *u, const double *v) {
   return s[8];
 }
 
-esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
+esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc) {
   auto t0 = std::chrono::steady_clock::now();
   if (h->x_semi) {  // the plain fp64 solve works in the TOP basis
     rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
@@ -430,10 +430,18 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
   const VCtx c = vctx(h);
   double *x = h->s64.x, *r = h->s64.r, *p = h->s64.p, *q = h->s64.q;
   cudaStream_t st = h->stream;
+  h->last_precision = virt_tc ? ESMP2_FP64_TC : ESMP2_FP64;
+  const int lv = virt_tc ? kFp64TcLevels : 0;
   antisym_project(h, x);
-  esmp2_status s = sigma64(h, x, q);
-  if (s) return s;
-  int nsig = 1;
+  esmp2_status s = ESMP2_OK;
+  int nsig = 0;
+  if (h->x_zero) {  // cold start: A x = 0, the first residual is b
+    cudaMemsetAsync(q, 0, sizeof(double) * h->d.n, st);
+  } else {
+    if ((s = sigma64(h, x, q, lv))) return s;
+    nsig = 1;
+  }
+  h->x_zero = false;
   k_pcg_init<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->b, q, r, p, h->red);
   k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 3, h->red_out, 0);
   h->launches += 2;
@@ -448,7 +456,7 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
   if (bnorm == 0.0) result = ESMP2_OK;
   while (result != ESMP2_OK && it < maxit) {
     if (std::sqrt(rr) <= tol * bnorm) {  // confirm with the true residual
-      if ((s = sigma64(h, x, q))) return s;
+      if ((s = sigma64(h, x, q, lv))) return s;
       ++nsig;
       k_pcg_init<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->b, q, r, p, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 3, h->red_out, 0);
@@ -459,7 +467,8 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
       relres = std::sqrt(rr) / bnorm;
       if (relres <= tol) { result = ESMP2_OK; break; }
     }
-    if ((s = sigma64(h, p, q))) return s;
+    if ((s = sigma64(h, p, q, lv))) return s;
+    if (virt_tc && (s = check_device_flag(h))) return s;
     ++nsig;
     k_dot_w<<<kRedBlocks, kRedThreads, 0, st>>>(c, p, q, h->red);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
@@ -492,7 +501,9 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   cudaStream_t st = h->stream;
   const double *F = h->x_semi ? h->Fsemi : h->F;
   const double *bb = h->x_semi ? h->bsemi : h->b;
-  esmp2_status s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q);
+  // after a tensor-core solve the Hylleraas sigma uses the float64-exact digit levels
+  const int lv = (h->last_precision != ESMP2_FP64 && split_supported(h, kFp64TcLevels)) ? kFp64TcLevels : 0;
+  esmp2_status s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q, lv);
   if (s) return s;
   k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.q, h->red);
   k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 10, h->red_out, 3);
@@ -559,11 +570,19 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
   // relative tolerance of each inner solve; ESMP2_INNER_ETA overrides it (tuning knob)
   // (the bf16 rounding of the inner operand limits the inner residual to ~1e-3 relative)
-  double eta = 2e-2;
+  // the float64 true residual takes its virtual-index terms from exact digit products on
+  // the tensor cores when that is exact for this Nv, else from float64 GEMMs
+  const int lv = split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
+  h->last_precision = ESMP2_MIXED_BF16;
+  double eta = 1e-2;
   if (const char *ev = std::getenv("ESMP2_INNER_ETA")) eta = std::max(1e-12, std::atof(ev));
   while (true) {
-    if ((s = sigma64_F(h, h->Fsemi, 1, x, q))) return s;
-    ++nsig64;
+    if (outer == 0 && h->x_zero) {  // cold start: the first true residual is b itself
+      cudaMemsetAsync(q, 0, sizeof(double) * h->d.n, st);
+    } else {
+      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv))) return s;
+      ++nsig64;
+    }
     k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, q, r, h->red);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 3);
     h->launches += 2;
@@ -603,6 +622,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine:   inner %d  |r_in|/|r0| %.3e\n", inner, std::sqrt(sl[1]) / r0);
     kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
     h->launches += 1;
+    h->x_zero = false;
     antisym_project(h, x);  // the float64 residual pass assumes exactly antisymmetric T, X, Y
     ++outer;
     if ((s = check_device_flag(h))) return s;

@@ -182,10 +182,17 @@ esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y) {
 
 // Only the virtual-index contractions (both terms, all blocks), for testing the tensor-core
 // kernel against the float64 GEMMs.
-esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int lowp) {
-  if (!lowp) {
+// mode 0: float64 GEMMs; 1: bf16 operands, fp32 accumulation; 2: exact digit products
+// summed in float64 (every slice, both terms, any input).
+esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int mode) {
+  if (mode == 0) {
     contractions64(h, h->F, x, y, 1);
     return check_cuda(h, cudaGetLastError(), "virtual contraction");
+  }
+  if (mode == 2) {
+    esmp2_status s = virt_split(h, x, y, nullptr, 0, kFp64TcLevels);
+    if (!s) s = check_device_flag(h);
+    return s ? s : check_cuda(h, cudaGetLastError(), "virtual contraction");
   }
   esmp2_status s = ensure_mixed(h, false);
   if (s) return s;

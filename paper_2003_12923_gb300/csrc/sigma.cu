@@ -160,90 +160,110 @@ void launch_inter(esmp2_handle *h, const CtxT<CT> &c, const T *x, const Coupling
 }
 
 // y += couplings - omega x (+ pair energy on L blocks); y = 0 on non-amplitude slots.
+// One CTA iteration per 32 x 32 tile (a, b) of one slice (blk, i, j): block, slice and tile
+// are uniform over the CTA, so every gather is either a coalesced row of a slice or a
+// broadcast; the one transposed operand (Z_ji^ba of the S block) goes through shared memory.
 template <typename TX, typename TY, typename CT>
-__global__ void k_couple(CtxT<CT> c, const TX *x, TY *y, CouplingsT<CT> cp) {
-  const int No = c.No, Nv = c.Nv, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256, 4) k_couple(CtxT<CT> c, const TX *__restrict__ x, TY *__restrict__ y,
+                                                CouplingsT<CT> cp) {
+  __shared__ CT zt[32][33];
+  const int No = c.No, Nv = c.Nv;
+  const int nt = (Nv + 31) >> 5;
+  const int64_t NvNv = (int64_t)Nv * Nv, NN = (int64_t)No * No;
+  const int64_t ntiles = 5 * NN * nt * nt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const CT shift = c.Fv(0, 0) - c.Fo(0, 0);
   const CT f00 = c.Fov(0, 0);
-  const int rows = 5 * No * No * Nv;
-  const int w0 = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
-  for (int r = w0; r < rows; r += nw) {
-    int f = r;
-    const int a = f % Nv; f /= Nv;
-    const int j = f % No; f /= No;
-    const int i = f % No;
-    const int blk = f / No;
-    for (int b = lane; b < Nv; b += 32) {
-    const int64_t e = (int64_t)r * Nv + b;
-    if (!valid_elem(blk, i, j, a, b)) { y[e] = (TY)0; continue; }
-    auto X = [&](int bl, int ii, int jj, int aa, int bb) { return (CT)x[c.at(bl, ii, jj, aa, bb)]; };
-    const CT xe = (CT)x[e];
-    CT v = -c.omega * xe;
-    const bool i0 = i == 0, j0 = j == 0, a0 = a == 0, b0 = b == 0;
-    const int64_t NoNv = (int64_t)No * Nv, NvNv = (int64_t)Nv * Nv;
-    if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
+  auto slice = [&](int bl, int ii, int jj) { return x + ((int64_t)bl * NN + (int64_t)ii * No + jj) * NvNv; };
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t f = t;
+    const int tb = (int)(f % nt); f /= nt;
+    const int ta = (int)(f % nt); f /= nt;
+    const int j = (int)(f % No); f /= No;
+    const int i = (int)(f % No);
+    const int blk = (int)(f / No);
+    const int a0 = ta << 5, b0 = tb << 5, b = b0 + tx;
+    const bool i0 = i == 0, j0 = j == 0, b0f = b == 0;
+    const TX *xs = slice(blk, i, j);
+    TY *ys = y + (xs - x);
+    if (blk == BS) {  // Z_ji[b][a] for the tile, read along a and used along b
+      __syncthreads();
+      const TX *zji = slice(BZ, j, i);
+      for (int r = ty; r < 32; r += 8) {
+        const int bb = b0 + r, aa = a0 + tx;
+        zt[r][tx] = (bb < Nv && aa < Nv) ? (CT)zji[(int64_t)bb * Nv + aa] : CT(0);
+      }
+      __syncthreads();
+    }
+    if (b >= Nv) continue;
+    const CT foi = c.Fo(0, i), foj = c.Fo(0, j), fdiag = c.Fo(i, i) + c.Fo(j, j);
+    for (int r = ty; r < 32; r += 8) {
+      const int a = a0 + r;
+      if (a >= Nv) break;
       const int64_t ab = (int64_t)a * Nv + b;
-      v -= (c.Fo(i, i) + c.Fo(j, j)) * xe;
-      if (!i0) v -= c.Fo(0, i) * X(blk, 0, j, a, b);
-      else v -= cp.OC1[((int64_t)blk * No + j) * NvNv + ab];
-      if (!j0) v -= c.Fo(0, j) * X(blk, i, 0, a, b);
-      else v -= cp.OC2[((int64_t)blk * No + i) * NvNv + ab];
-    }
-    switch (blk) {
-      case BT: {
-        v += f00 * (X(BX, i, j, a, b) + X(BY, i, j, a, b));
-        const int64_t ij = ((int64_t)i * No + j) * Nv, ji = ((int64_t)j * No + i) * Nv;
-        if (a0) v -= cp.VX[ij + b];
-        if (b0) v += cp.VX[ij + a];
-        if (i0) v -= cp.OX[j * NvNv + (int64_t)a * Nv + b];
-        if (j0) v += cp.OX[i * NvNv + (int64_t)a * Nv + b];
-        if (i0 && a0) v += cp.G[j * Nv + b];
-        if (j0 && a0) v -= cp.G[i * Nv + b];
-        if (i0 && b0) v -= cp.G[j * Nv + a];
-        if (j0 && b0) v += cp.G[i * Nv + a];
-        (void)ji; (void)NoNv;
-        break;
+      if (!valid_elem(blk, i, j, a, b)) { ys[ab] = (TY)0; continue; }
+      const bool a0f = a == 0;
+      const CT xe = (CT)xs[ab];
+      CT v = -c.omega * xe;
+      if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
+        v -= fdiag * xe;
+        v -= i0 ? cp.OC1[((int64_t)blk * No + j) * NvNv + ab] : foi * (CT)slice(blk, 0, j)[ab];
+        v -= j0 ? cp.OC2[((int64_t)blk * No + i) * NvNv + ab] : foj * (CT)slice(blk, i, 0)[ab];
       }
-      case BS: {
-        if (j0 && b0) v += cp.H[i * Nv + a];
-        if (i0 && a0) v += cp.H[j * Nv + b];
-        v += f00 * (X(BZ, i, j, a, b) + X(BZ, j, i, b, a));
-        if (b0) v -= cp.WZ[((int64_t)i * No + j) * Nv + a];
-        if (a0) v -= cp.WZ[((int64_t)j * No + i) * Nv + b];
-        if (j0) v -= cp.OZ[i * NvNv + (int64_t)a * Nv + b];
-        if (i0) v -= cp.OZ[j * NvNv + (int64_t)b * Nv + a];
-        break;
+      switch (blk) {
+        case BT: {
+          v += f00 * ((CT)slice(BX, i, j)[ab] + (CT)slice(BY, i, j)[ab]);
+          const int64_t ij = ((int64_t)i * No + j) * Nv;
+          if (a0f) v -= cp.VX[ij + b];
+          if (b0f) v += cp.VX[ij + a];
+          if (i0) v -= cp.OX[j * NvNv + ab];
+          if (j0) v += cp.OX[i * NvNv + ab];
+          if (i0 && a0f) v += cp.G[j * Nv + b];
+          if (j0 && a0f) v -= cp.G[i * Nv + b];
+          if (i0 && b0f) v -= cp.G[j * Nv + a];
+          if (j0 && b0f) v += cp.G[i * Nv + a];
+          break;
+        }
+        case BS: {
+          if (j0 && b0f) v += cp.H[i * Nv + a];
+          if (i0 && a0f) v += cp.H[j * Nv + b];
+          v += f00 * ((CT)slice(BZ, i, j)[ab] + zt[tx][r]);
+          if (b0f) v -= cp.WZ[((int64_t)i * No + j) * Nv + a];
+          if (a0f) v -= cp.WZ[((int64_t)j * No + i) * Nv + b];
+          if (j0) v -= cp.OZ[i * NvNv + ab];
+          if (i0) v -= cp.OZ[j * NvNv + (int64_t)b * Nv + a];
+          break;
+        }
+        case BX: {
+          const TX *T = slice(BT, i, j), *T0j = slice(BT, 0, j), *T0i = slice(BT, 0, i);
+          v += shift * xe + f00 * (CT)T[ab];
+          v += -c.Fov(0, a) * (CT)T[b] + c.Fov(0, b) * (CT)T[a];
+          v += -c.Fov(i, 0) * (CT)T0j[ab] + c.Fov(j, 0) * (CT)T0i[ab];
+          v += c.Fov(i, a) * (CT)T0j[b] - c.Fov(j, a) * (CT)T0i[b] - c.Fov(i, b) * (CT)T0j[a] + c.Fov(j, b) * (CT)T0i[a];
+          break;
+        }
+        case BY: {
+          const TX *S0i = slice(BS, 0, i), *S0j = slice(BS, 0, j);
+          v += shift * xe + f00 * (CT)slice(BT, i, j)[ab];
+          v += c.Fov(j, b) * (CT)S0i[a] - c.Fov(i, b) * (CT)S0j[a] - c.Fov(j, a) * (CT)S0i[b] + c.Fov(i, a) * (CT)S0j[b];
+          if (i0 && a0f) v += cp.CYZ[j * Nv + b];
+          if (j0 && a0f) v -= cp.CYZ[i * Nv + b];
+          if (i0 && b0f) v -= cp.CYZ[j * Nv + a];
+          if (j0 && b0f) v += cp.CYZ[i * Nv + a];
+          break;
+        }
+        default: {  // BZ
+          const TX *Sij = slice(BS, i, j), *Si0 = slice(BS, i, 0);
+          v += shift * xe;
+          v += f00 * (CT)Sij[ab] - c.Fov(0, b) * (CT)Sij[(int64_t)a * Nv] - c.Fov(j, 0) * (CT)Si0[ab]
+             + c.Fov(j, b) * (CT)Si0[(int64_t)a * Nv] + c.Fov(i, a) * (CT)slice(BT, 0, j)[b];
+          const CT y0 = (CT)slice(BY, 0, j)[b];
+          if (i0) v += c.Fv(a, 0) * y0;
+          if (a0f) v -= foi * y0;
+          break;
+        }
       }
-      case BX: {
-        v += shift * xe + f00 * X(BT, i, j, a, b);
-        v += -c.Fov(0, a) * X(BT, i, j, 0, b) + c.Fov(0, b) * X(BT, i, j, 0, a);
-        v += -c.Fov(i, 0) * X(BT, 0, j, a, b) + c.Fov(j, 0) * X(BT, 0, i, a, b);
-        v += c.Fov(i, a) * X(BT, 0, j, 0, b) - c.Fov(j, a) * X(BT, 0, i, 0, b)
-           - c.Fov(i, b) * X(BT, 0, j, 0, a) + c.Fov(j, b) * X(BT, 0, i, 0, a);
-        break;
-      }
-      case BY: {
-        v += shift * xe + f00 * X(BT, i, j, a, b);
-        v += c.Fov(j, b) * X(BS, 0, i, 0, a) - c.Fov(i, b) * X(BS, 0, j, 0, a)
-           - c.Fov(j, a) * X(BS, 0, i, 0, b) + c.Fov(i, a) * X(BS, 0, j, 0, b);
-        if (i0 && a0) v += cp.CYZ[j * Nv + b];
-        if (j0 && a0) v -= cp.CYZ[i * Nv + b];
-        if (i0 && b0) v -= cp.CYZ[j * Nv + a];
-        if (j0 && b0) v += cp.CYZ[i * Nv + a];
-        break;
-      }
-      default: {  // BZ
-        v += shift * xe;
-        v += f00 * X(BS, i, j, a, b) - c.Fov(0, b) * X(BS, i, j, a, 0) - c.Fov(j, 0) * X(BS, i, 0, a, b)
-           + c.Fov(j, b) * X(BS, i, 0, a, 0) + c.Fov(i, a) * X(BT, 0, j, 0, b);
-        const CT y0 = X(BY, 0, j, 0, b);
-        if (i0) v += c.Fv(a, 0) * y0;
-        if (a0) v -= c.Fo(0, i) * y0;
-        break;
-      }
-    }
-    y[e] = (TY)((CT)y[e] + v);
+      ys[ab] = (TY)((CT)ys[ab] + v);
     }
   }
 }
@@ -322,14 +342,20 @@ void contractions64(esmp2_handle *h, const double *F, const double *x, double *y
 // Per-stage timing of `reps` float64 sigma builds (CUDA events on the handle's stream):
 // ms[0] virtual-index GEMMs, ms[1] occupied-index GEMMs, ms[2] coupling intermediates,
 // ms[3] element-wise coupling pass, ms[4] whole sigma.
-esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms) {
+esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels) {
   cudaEvent_t ev[5];
   for (auto &e : ev) cudaEventCreate(&e);
   double acc[5] = {0, 0, 0, 0, 0};
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(ev[0], h->stream);
     if (!h->P64) cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
-    virt64_sym(h, h->F, x, y);
+    if (tc_levels) {
+      esmp2_status s = virt_split(h, x, y, h->P64, 1, tc_levels);
+      if (s) return s;
+      combine_sym(h, y);
+    } else {
+      virt64_sym(h, h->F, x, y);
+    }
     cudaEventRecord(ev[1], h->stream);
     contractions64(h, h->F, x, y, 2);
     cudaEventRecord(ev[2], h->stream);
@@ -496,28 +522,42 @@ void virt64_sym(esmp2_handle *h, const double *F, const double *x, double *y) {
     gemm64(g, h->stream);
     nl += 2;
   }
-  const int tiles = (Nv + 31) / 32;
+  h->launches += nl;
+  combine_sym(h, y);
+}
+
+// y_ij = P_ij - P_ij^T for the T, X, Y blocks from P (= x F on the slices i < j) in P64
+void combine_sym(esmp2_handle *h, double *y) {
+  const int No = h->d.No, Nv = h->d.Nv, tiles = (Nv + 31) / 32;
   const int64_t nblocks = 3LL * No * No * tiles * tiles;
   k_combine_sym<<<(unsigned)nblocks, 256, 0, h->stream>>>(No, Nv, h->P64, y);
-  h->launches += nl + 1;
+  h->launches += 1;
 }
 
 // float64 sigma with an arbitrary orthonormal-basis Fock matrix F (t = occupied 0, t' =
 // virtual 0).  arrow = 1 when F_oo is diagonal apart from its t row and column: then the
 // occupied-index terms are applied element-wise instead of by GEMM.
-esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
+// tc_levels >= 2: the virtual-index terms come from exact digit products on the tensor
+// cores, digit levels 2 .. tc_levels (F_vv of the handle); 0: float64 GEMMs with F.
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels) {
   if (!h->P64) {
     cudaError_t e = cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
     if (e != cudaSuccess) return check_cuda(h, e, "sigma64 workspace");
   }
-  virt64_sym(h, F, x, y);
+  if (tc_levels) {
+    esmp2_status s = virt_split(h, x, y, h->P64, 1, tc_levels);
+    if (s) return s;
+    combine_sym(h, y);
+  } else {
+    virt64_sym(h, F, x, y);
+  }
   if (!arrow) contractions64(h, F, x, y, 2);
   launch_intermediates64(h, F, arrow, x);
   launch_couple64(h, F, arrow, x, y);
   return check_cuda(h, cudaGetLastError(), "sigma64");
 }
 
-esmp2_status sigma64(esmp2_handle *h, const double *x, double *y) { return sigma64_F(h, h->F, 0, x, y); }
+esmp2_status sigma64(esmp2_handle *h, const double *x, double *y, int tc_levels) { return sigma64_F(h, h->F, 0, x, y, tc_levels); }
 
 // parts (2)-(3) only: couplings, shift and masks added to y
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {

@@ -22,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "internal.h"
@@ -127,16 +129,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 struct Args {
-  int Nv;          // virtual orbitals (rows and columns of every slice)
-  int S;           // number of slices
-  int a_tiles;     // ceil(Nv / 128)
-  int b_tiles;     // column tiles per slice
-  int bn;          // columns of a full column tile (multiple of 16, <= 256)
-  int nk;          // K chunks: ceil(Nv / 64)
-  int64_t tiles;   // S * a_tiles * b_tiles
-  float *y;        // [S][Nv][Nv]
-  int *err;        // error flag (device)
+  int Nv;            // virtual orbitals (rows and columns of every slice)
+  int nslices;       // slices of this launch
+  const int *slices; // global slice index of each launched slice (nullptr: 0 .. nslices-1)
+  int per_block;     // slices per amplitude block (No^2); block of slice s = s / per_block
+  int sym;           // 1: slices of T, X, Y take only the term x F (antisymmetric slices)
+  int a_tiles;       // ceil(Nv / 128)
+  int b_tiles;       // column tiles per slice
+  int bn;            // columns of a full column tile (multiple of 16, <= 256)
+  int nk;            // K chunks: ceil(Nv / 64)
+  int64_t tiles;     // nslices * a_tiles * b_tiles
+  int npairs;        // operand pairs accumulated into one tile (digit products of one level)
+  int dx[9], df[9];  // digit plane of x and of F for each pair
+  int S_plane;       // slices per digit plane of x
+  int mode;          // 0: fp32 store into y32; 1: float64 (y64 | p64) (+)= 2^(es[s] + eF - 6 level) acc
+  float *y32;        // [S][Nv][Nv]
+  double *y64;       // [S][Nv][Nv] (two-term slices in mode 1)
+  double *p64;       // [S][Nv][Nv] (one-term slices in mode 1)
+  const int *es;     // per-slice binary exponent of the x digits
+  int eF, level, first;
+  int *err;          // error flag (device)
 };
+
+__device__ __forceinline__ int slice_of(const Args &g, int64_t li) {
+  return g.slices ? g.slices[li] : (int)li;
+}
+__device__ __forceinline__ int terms_of(const Args &g, int s) {
+  if (!g.sym) return 2;
+  const int blk = s / g.per_block;
+  return (blk == 1 || blk == 4) ? 2 : 1;   // S and Z blocks keep both terms
+}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_virt(const __grid_constant__ CUtensorMap tXa, const __grid_constant__ CUtensorMap tXb,
@@ -169,23 +191,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {  // ------------------------------------------------ TMA producer
       int64_t it = 0;
       bool ok = true;
+      const uint32_t bytes2 = (uint32_t)(2 * A_BYTES + g.bn * BK * 2 + (BN_MAX / 64) * 64 * BK * 2);
+      const uint32_t bytes1 = (uint32_t)(A_BYTES + g.bn * BK * 2);
       for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
-        const int s = (int)(t / per_slice), rem = (int)(t % per_slice);
+        const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
+        const int terms = terms_of(g, s);
         const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
-        for (int kc = 0; kc < g.nk; ++kc, ++it) {
-          const int st = (int)(it % STAGES);
-          const uint32_t rnd = (uint32_t)(it / STAGES);
-          if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) { ok = false; break; }
-          uint8_t *base = smem + st * STAGE_BYTES;
-          uint8_t *A2 = base, *A1 = base + A_BYTES, *B2 = base + 2 * A_BYTES, *B1 = B2 + B_BYTES;
-          // bytes of the boxes below: A2, A1 (128 x 64), B2 (bn x 64), B1 (4 boxes 64 x 64)
-          mbar_expect_tx(&full[st], (uint32_t)(2 * A_BYTES + g.bn * BK * 2 + (BN_MAX / 64) * 64 * BK * 2));
-          const int c0 = kc * BK;
-          tma_3d(A2, &tXa, &full[st], c0, a0, s);
-          tma_2d(A1, &tFa, &full[st], c0, a0);
-          tma_2d(B2, &tFb, &full[st], c0, b0);
+        for (int pr = 0; pr < g.npairs && ok; ++pr) {
+          const int zx = g.dx[pr] * g.S_plane + s, zf = g.df[pr];
+          for (int kc = 0; kc < g.nk; ++kc, ++it) {
+            const int st = (int)(it % STAGES);
+            const uint32_t rnd = (uint32_t)(it / STAGES);
+            if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) { ok = false; break; }
+            uint8_t *base = smem + st * STAGE_BYTES;
+            uint8_t *A2 = base, *A1 = base + A_BYTES, *B2 = base + 2 * A_BYTES, *B1 = B2 + B_BYTES;
+            // boxes: A2 (128 x 64), B2 (bn x 64); two-term slices also A1 (128 x 64), B1 (4 x 64 x 64)
+            mbar_expect_tx(&full[st], terms == 2 ? bytes2 : bytes1);
+            const int c0 = kc * BK;
+            tma_3d(A2, &tXa, &full[st], c0, a0, zx);
+            tma_3d(B2, &tFb, &full[st], c0, b0, zf);
+            if (terms == 2) {
+              tma_3d(A1, &tFa, &full[st], c0, a0, zf);
 #pragma unroll
-          for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B1 + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, s);
+              for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B1 + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, zx);
+            }
+          }
         }
       }
       if (!ok) atomicExch(&fail, 1);
@@ -199,7 +229,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int lt = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++lt) {
-        const int rem = (int)(t % per_slice);
+        const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
+        const int terms = terms_of(g, s);
         const int b0 = (rem % g.b_tiles) * g.bn;
         const int nvalid = min(g.bn, g.Nv - b0);
         const int nmma = (nvalid + 15) & ~15;
@@ -209,19 +240,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&acc_empty[ab], (ar & 1) ^ 1)) { ok = false; break; }
         tc_after();
         const uint32_t d = tmem + (uint32_t)(ab * BN_MAX);
-        for (int kc = 0; kc < g.nk; ++kc, ++it) {
-          const int st = (int)(it % STAGES);
-          const uint32_t rnd = (uint32_t)(it / STAGES);
-          if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
-          tc_after();
-          const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-          const uint32_t A2 = base, A1 = base + A_BYTES, B2 = base + 2 * A_BYTES, B1 = B2 + B_BYTES;
-          const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);
-          for (int k = 0; k < ksteps; ++k)   // X_s[a][c] F[c][b]
-            umma(d, sdesc(A2 + 32 * k, 16, 1024), sdesc(B2 + 32 * k, 16, 1024), id2, (kc > 0 || k > 0) ? 1u : 0u);
-          for (int k = 0; k < ksteps; ++k)   // F[a][c] X_s[c][b]
-            umma(d, sdesc(A1 + 32 * k, 16, 1024), sdesc(B1 + 2048 * k, BK * 128, 1024), id1, 1u);
-          umma_commit(&empty[st]);
+        for (int pr = 0; pr < g.npairs && ok; ++pr) {
+          for (int kc = 0; kc < g.nk; ++kc, ++it) {
+            const int st = (int)(it % STAGES);
+            const uint32_t rnd = (uint32_t)(it / STAGES);
+            if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
+            tc_after();
+            const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t A2 = base, A1 = base + A_BYTES, B2 = base + 2 * A_BYTES, B1 = B2 + B_BYTES;
+            const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);
+            for (int k = 0; k < ksteps; ++k)   // X_s[a][c] F[c][b]
+              umma(d, sdesc(A2 + 32 * k, 16, 1024), sdesc(B2 + 32 * k, 16, 1024), id2,
+                   (pr > 0 || kc > 0 || k > 0) ? 1u : 0u);
+            if (terms == 2)
+              for (int k = 0; k < ksteps; ++k)   // F[a][c] X_s[c][b]
+                umma(d, sdesc(A1 + 32 * k, 16, 1024), sdesc(B1 + 2048 * k, BK * 128, 1024), id1, 1u);
+            umma_commit(&empty[st]);
+          }
         }
         if (!ok) break;
         umma_commit(&acc_full[ab]);
@@ -232,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int quarter = warp & 3;
     int lt = 0;
     for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x, ++lt) {
-      const int s = (int)(t / per_slice), rem = (int)(t % per_slice);
+      const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
       const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
       const int nvalid = min(g.bn, g.Nv - b0);
       const int ab = lt & 1;
@@ -242,19 +277,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc_after();
       const int row = quarter * 32 + lane;
       const int a = a0 + row;
-      float *dst = g.y + ((int64_t)s * g.Nv + a) * g.Nv + b0;
+      const int64_t off = ((int64_t)s * g.Nv + a) * g.Nv + b0;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * BN_MAX);
-      for (int c = 0; c < nvalid; c += 16) {
-        float v[16];
-        tmem_ld16(taddr + (uint32_t)c, v);
-        if (a < g.Nv) {
-          const int m = min(16, nvalid - c);
-          if (m == 16 && (g.Nv & 3) == 0) {
-            float4 *d4 = reinterpret_cast<float4 *>(dst + c);
+      if (g.mode == 0) {
+        float *dst = g.y32 + off;
+        for (int c = 0; c < nvalid; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)c, v);
+          if (a < g.Nv) {
+            const int m = min(16, nvalid - c);
+            if (m == 16 && (g.Nv & 3) == 0) {
+              float4 *d4 = reinterpret_cast<float4 *>(dst + c);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          } else {
-            for (int q = 0; q < m; ++q) dst[c + q] = v[q];
+              for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+              for (int q = 0; q < m; ++q) dst[c + q] = v[q];
+            }
+          }
+        }
+      } else {
+        // every accumulator value is an integer below 2^24 (exact in fp32); the float64
+        // sum over levels is the only rounding step
+        double *dst = (terms_of(g, s) == 2 ? g.y64 : g.p64) + off;
+        const double scale = ldexp(1.0, g.es[s] + g.eF - 6 * g.level);
+        for (int c = 0; c < nvalid; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)c, v);
+          if (a < g.Nv) {
+            const int m = min(16, nvalid - c);
+            if (m == 16 && (g.Nv & 1) == 0) {
+              double2 *d2 = reinterpret_cast<double2 *>(dst + c);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                double2 o = g.first ? make_double2(0.0, 0.0) : d2[q];
+                o.x += (double)v[2 * q] * scale;
+                o.y += (double)v[2 * q + 1] * scale;
+                d2[q] = o;
+              }
+            } else {
+              for (int q = 0; q < m; ++q) dst[c + q] = (g.first ? 0.0 : dst[c + q]) + (double)v[q] * scale;
+            }
           }
         }
       }
@@ -270,6 +332,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
   if (threadIdx.x == 0 && fail) atomicOr(g.err, 1);
+}
+
+// Exact digit split of float64 slices (Ozaki-type splitting): with 2^e the smallest power
+// of two above 2 max |x_s|, z = x / 2^e lies in (-1/2, 1/2) and
+//     z = sum_{p>=1} d_p 64^-p,  d_p integers in [-32, 32]
+// by repeated rounding to the nearest integer; every d_p is exact in bf16 and every product
+// of two digits is an integer of magnitude <= 2^10.
+// Per-slice exponent: one CTA per slice, element (r, c) of slice s at s*sstride + r*ld + c.
+__global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int64_t sstride, int *es) {
+  __shared__ double red[32];
+  const double *X = x + blockIdx.x * sstride;
+  double m = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x)
+    m = fmax(m, fabs(X[(e / cols) * ld + e % cols]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (m > 0.0) frexp(m, &e);   // m = f 2^e with f in [0.5, 1): 2 max |x| < 2^(e+1)
+      es[blockIdx.x] = m > 0.0 ? e + 1 : 0;
+    }
+  }
+}
+
+// digits: out[p][s][r][c] (row pitch Nvp, pad columns zero), plane = S * rows * Nvp
+__global__ void k_digits(const double *x, int S, int rows, int cols, int Nvp, int64_t ld, int64_t sstride,
+                         const int *es, int P, __nv_bfloat16 *out) {
+  const int64_t plane = (int64_t)S * rows * Nvp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % Nvp);
+    const int64_t rs = e / Nvp;
+    const int r = (int)(rs % rows);
+    const int s = (int)(rs / rows);
+    double z = c < cols ? ldexp(x[s * sstride + r * ld + c], -es[s]) : 0.0;
+    for (int p = 0; p < P; ++p) {
+      const double t = z * 64.0;
+      const double d = rint(t);
+      z = t - d;                       // exact: d is the integer nearest to t
+      out[p * plane + e] = __float2bfloat16_rn((float)d);
+    }
+  }
 }
 
 // bf16 copies: dst[s][r][c] (row pitch Nvp) = src[s][r][c] (row pitch Nv); pad columns zero.
@@ -321,34 +430,27 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
 }
 }  // namespace
 
-// y[s][a][b] = sum_c xb[s][a][c] F[c][b] + sum_c F[a][c] xb[s][c][b]  for S slices (fp32 out).
-// xb: bf16 [S][Nv][Nvp], Fb: bf16 [Nv][Nvp], Nvp = Nv rounded up to 8 (16-byte row pitch).
-esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err) {
-  const int Nv = h->d.Nv;
-  const int Nvp = (Nv + 7) & ~7;
-  if (!get_encode()) { h->err = "cuTensorMapEncodeTiled unavailable"; return ESMP2_ERR_CUDA; }
+namespace {
+// Fills the tile geometry of `g` and launches k_virt.  xd: bf16 x planes [planes][S_plane][Nv][Nvp];
+// Fd: bf16 F planes [F_planes][Nv][Nvp]; Nvp = Nv rounded up to 8 (16-byte row pitch).
+const char *launch_virt(cudaStream_t st, const void *xd, int x_planes, const void *Fd, int F_planes, tc::Args &g) {
+  const int Nv = g.Nv, Nvp = (Nv + 7) & ~7;
+  if (!get_encode()) return "cuTensorMapEncodeTiled unavailable";
+  if (g.nslices <= 0) return nullptr;
   CUtensorMap mXa, mXb, mFa, mFb;
-  const uint64_t dX[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)S};
+  const uint64_t dX[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)g.S_plane * x_planes};
   const uint64_t sX[2] = {(uint64_t)Nvp * 2, (uint64_t)Nvp * Nv * 2};
-  const uint64_t dF[2] = {(uint64_t)Nvp, (uint64_t)Nv};
-  const uint64_t sF[1] = {(uint64_t)Nvp * 2};
-  tc::Args g;
-  g.Nv = Nv;
-  g.S = S;
+  const uint64_t dF[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)F_planes};
   g.a_tiles = (Nv + tc::BM - 1) / tc::BM;
   g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
   g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
   g.nk = (Nv + tc::BK - 1) / tc::BK;
-  g.tiles = (int64_t)S * g.a_tiles * g.b_tiles;
-  g.y = y;
-  g.err = err;
-  const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[2] = {64, 128};
-  const uint32_t boxFb[2] = {64, (uint32_t)g.bn};
-  if (!make_map(&mXa, xb, 3, dX, sX, boxXa) || !make_map(&mXb, xb, 3, dX, sX, boxXb) ||
-      !make_map(&mFa, Fb, 2, dF, sF, boxFa) || !make_map(&mFb, Fb, 2, dF, sF, boxFb)) {
-    h->err = "tensor map encoding failed";
-    return ESMP2_ERR_CUDA;
-  }
+  g.tiles = (int64_t)g.nslices * g.a_tiles * g.b_tiles;
+  const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[3] = {64, 128, 1};
+  const uint32_t boxFb[3] = {64, (uint32_t)g.bn, 1};
+  if (!make_map(&mXa, xd, 3, dX, sX, boxXa) || !make_map(&mXb, xd, 3, dX, sX, boxXb) ||
+      !make_map(&mFa, Fd, 3, dF, sX, boxFa) || !make_map(&mFb, Fd, 3, dF, sX, boxFb))
+    return "tensor map encoding failed";
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc::k_virt, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
@@ -358,9 +460,152 @@ esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, f
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(g.tiles, sms);
-  tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, h->stream>>>(mXa, mXb, mFa, mFb, g);
+  tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, st>>>(mXa, mXb, mFa, mFb, g);
+  return nullptr;
+}
+
+tc::Args plain_args(int Nv, int S, float *y, int *err) {
+  tc::Args g{};
+  g.Nv = Nv;
+  g.nslices = S;
+  g.slices = nullptr;
+  g.per_block = S;
+  g.sym = 0;
+  g.npairs = 1;
+  g.S_plane = S;
+  g.mode = 0;
+  g.y32 = y;
+  g.err = err;
+  return g;
+}
+}  // namespace
+
+// y[s][a][b] = sum_c xb[s][a][c] F[c][b] + sum_c F[a][c] xb[s][c][b]  for S slices (fp32 out).
+// xb: bf16 [S][Nv][Nvp], Fb: bf16 [Nv][Nvp], Nvp = Nv rounded up to 8 (16-byte row pitch).
+esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err) {
+  tc::Args g = plain_args(h->d.Nv, S, y, err);
+  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g)) { h->err = m; return ESMP2_ERR_CUDA; }
   h->launches += 1;
   return check_cuda(h, cudaGetLastError(), "virt_bf16");
+}
+
+// ---- float64-accurate virtual-index terms from exact digit products on the tensor cores.
+// x_s = 2^{e_s} sum_p d_p 64^-p and F_vv = 2^{e_F} sum_q f_q 64^-q (Lmax - 1 digits each);
+// level L = p + q collects every digit pair of that weight in one fp32 accumulator.  A
+// level-L sum over both terms and K = Nv is an integer of magnitude <= 2 Nv (L - 1) 2^10,
+// below 2^24 whenever Nv < 2^13 / (L - 1): fp32 accumulation is then exact and the float64
+// sum over levels 2 .. Lmax is the only rounding.  The x digits stop 2^{-6 (Lmax - 1) - 1}
+// below 2^{e_s}, and the dropped pairs (p + q > Lmax) weigh as little, so the result carries
+// a relative error of order 2^{-6 (Lmax - 1)} against the largest term of each slice.
+// sym = 1: T, X, Y slices (exactly antisymmetric) take only x F on i < j into p64 and the
+// caller forms y_ij = P_ij - P_ij^T; S and Z slices take x F + F x into y.
+// sym = 0: every slice takes both terms into y (any input).
+namespace {
+constexpr int kSplitMaxLevels = 10;
+
+__global__ void k_split_list(int No, int *list) {
+  // T, X, Y slices with i < j, then every S and Z slice
+  const int NN = No * No, half = No * (No - 1) / 2;
+  const int n = 3 * half + 2 * NN;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int s;
+    if (e < 3 * half) {
+      const int blk = e / half == 0 ? 0 : (e / half == 1 ? 2 : 3);
+      int k = e % half, i = 0;
+      while (k >= No - 1 - i) { k -= No - 1 - i; ++i; }
+      s = blk * NN + i * No + (i + 1 + k);
+    } else {
+      const int f = e - 3 * half;
+      s = (f < NN ? 1 : 4) * NN + f % NN;
+    }
+    list[e] = s;
+  }
+}
+}  // namespace
+
+int split_levels_for(double tol) {
+  // keep 2^{-6 (Lmax - 1)} at or below 1e-4 tol (refinement and energy stay float64-exact)
+  const double need = std::log2(1e4 / std::max(tol, 1e-300)) / 6.0;
+  return std::max(2, std::min(kSplitMaxLevels, (int)std::ceil(need) + 1));
+}
+
+bool split_supported(const esmp2_handle *h, int levels) {
+  if (levels < 2 || levels > kSplitMaxLevels) return false;
+  return 2LL * h->d.Nv * (levels - 1) * 1024 < (1LL << 24);
+}
+
+esmp2_status ensure_split(esmp2_handle *h) {
+  if (h->xdig) return ESMP2_OK;
+  const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, Nvp = (Nv + 7) & ~7;
+  const int S = 5 * No * No, P = kSplitMaxLevels - 1;
+  const int nl = 3 * (No * (No - 1) / 2) + 2 * No * No;
+  cudaError_t e = cudaMalloc(&h->xdig, sizeof(__nv_bfloat16) * (size_t)P * S * Nv * Nvp);
+  if (e == cudaSuccess) e = cudaMalloc(&h->Fdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp);
+  if (e == cudaSuccess) e = cudaMalloc(&h->es, sizeof(int) * (size_t)(S + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&h->slist, sizeof(int) * (size_t)nl);
+  if (e != cudaSuccess) {
+    cudaFree(h->xdig); cudaFree(h->Fdig); cudaFree(h->es); cudaFree(h->slist);
+    h->xdig = h->Fdig = nullptr; h->es = h->slist = nullptr;
+    return check_cuda(h, e, "split workspace");
+  }
+  h->nslist = nl;
+  if (!h->dflag) {
+    if ((e = cudaMalloc(&h->dflag, sizeof(int))) != cudaSuccess) return check_cuda(h, e, "split workspace");
+    cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+  }
+  k_split_list<<<(unsigned)cdiv(nl, 256), 256, 0, h->stream>>>(No, h->slist);
+  // digits of F_vv (the same block in the TOP and the semicanonical-occupied basis); the
+  // leading digits do not depend on how many are kept
+  const double *Fv = h->F + (int64_t)No * N + No;
+  tc::k_slice_exp<<<1, 256, 0, h->stream>>>(Fv, Nv, Nv, N, 0, h->es + S);
+  tc::k_digits<<<256, 256, 0, h->stream>>>(Fv, 1, Nv, Nv, Nvp, N, 0, h->es + S, P,
+                                           static_cast<__nv_bfloat16 *>(h->Fdig));
+  h->launches += 3;
+  e = cudaMemcpyAsync(&h->eF, h->es + S, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return check_cuda(h, e, "split setup");
+}
+
+esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64, int sym, int levels) {
+  if (!split_supported(h, levels)) { h->err = "digit-split contraction not exact for this Nv"; return ESMP2_ERR_UNSUPPORTED; }
+  esmp2_status s = ensure_split(h);
+  if (s) return s;
+  const int No = h->d.No, Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  const int S = 5 * No * No, P = kSplitMaxLevels - 1;
+  const int64_t NvNv = (int64_t)Nv * Nv;
+  tc::k_slice_exp<<<S, 256, 0, h->stream>>>(x, Nv, Nv, Nv, NvNv, h->es);
+  tc::k_digits<<<1216, 256, 0, h->stream>>>(x, S, Nv, Nv, Nvp, Nv, NvNv, h->es, levels - 1,
+                                            static_cast<__nv_bfloat16 *>(h->xdig));
+  h->launches += 2;
+  for (int L = 2; L <= levels; ++L) {
+    tc::Args g{};
+    g.Nv = Nv;
+    g.nslices = sym ? h->nslist : S;
+    g.slices = sym ? h->slist : nullptr;
+    g.per_block = No * No;
+    g.sym = sym;
+    g.S_plane = S;
+    g.npairs = 0;
+    for (int p = 1; p < L; ++p) {
+      g.dx[g.npairs] = p - 1;     // digit p of x with digit L - p of F
+      g.df[g.npairs] = L - p - 1;
+      ++g.npairs;
+    }
+    g.mode = 1;
+    g.y64 = y;
+    g.p64 = p64;
+    g.es = h->es;
+    g.eF = h->eF;
+    g.level = L;
+    g.first = (L == 2);
+    g.err = h->dflag;
+    if (const char *m = launch_virt(h->stream, h->xdig, P, h->Fdig, P, g)) {
+      h->err = m;
+      return ESMP2_ERR_CUDA;
+    }
+    h->launches += 1;
+  }
+  return check_cuda(h, cudaGetLastError(), "virt_split");
 }
 
 void to_bf16_f64(esmp2_handle *h, const double *src, void *dst, int64_t rows) {
@@ -436,31 +681,8 @@ extern "C" esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const
   cudaMemsetAsync(err, 0, sizeof(int), st);  // the array keeps the previous call's contents
   tc::k_fvv_bf16<<<256, 256, 0, st>>>(Fvv, 0, Nv, Nvp, Fb);
   tc::k_to_bf16<double><<<1216, 256, 0, st>>>(x, xb, (int64_t)S * Nv, Nv, Nvp);
-  CUtensorMap mXa, mXb, mFa, mFb;
-  const uint64_t dX[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)S};
-  const uint64_t sX[2] = {(uint64_t)Nvp * 2, (uint64_t)Nvp * Nv * 2};
-  const uint64_t dF[2] = {(uint64_t)Nvp, (uint64_t)Nv};
-  const uint64_t sF[1] = {(uint64_t)Nvp * 2};
-  tc::Args g;
-  g.Nv = Nv;
-  g.S = S;
-  g.a_tiles = (Nv + tc::BM - 1) / tc::BM;
-  g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
-  g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
-  g.nk = (Nv + tc::BK - 1) / tc::BK;
-  g.tiles = (int64_t)S * g.a_tiles * g.b_tiles;
-  g.y = y32;
-  g.err = err;
-  const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[2] = {64, 128};
-  const uint32_t boxFb[2] = {64, (uint32_t)g.bn};
-  if (!make_map(&mXa, xb, 3, dX, sX, boxXa) || !make_map(&mXb, xb, 3, dX, sX, boxXb) ||
-      !make_map(&mFa, Fb, 2, dF, sF, boxFa) || !make_map(&mFb, Fb, 2, dF, sF, boxFb))
-    return ESMP2_ERR_CUDA;
-  cudaFuncSetAttribute(tc::k_virt, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(g.tiles, sms);
-  tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, st>>>(mXa, mXb, mFa, mFb, g);
+  tc::Args g = plain_args(Nv, S, y32, err);
+  if (launch_virt(st, xb, 1, Fb, 1, g)) return ESMP2_ERR_CUDA;
   k_noalloc_f32_to_f64<<<1216, 256, 0, st>>>(y32, y, (int64_t)S * Nv * Nv);
   int flag = 0;
   cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);
