@@ -199,6 +199,35 @@ esmp2_status esmp2_grad(esmp2_handle *h, double *dF, double *dOVOV, int adjoint_
 /* Number of CUDA kernels this handle has launched since creation (for accounting). */
 int64_t esmp2_kernel_launches(const esmp2_handle *h);
 
+/* Process-wide timing of the kernel families of the hot path (measurement support; the
+ * paper has no counterpart).  While enabled, each launch of an instrumented family is
+ * bracketed by two CUDA events on the stream it runs on, and its work is recorded:
+ *   ESMP2_KT_CONTRACTION  tcgen05 virtual-index contraction (bf16 and digit-split launches);
+ *                         alg_units = algorithmic flops (unique amplitudes, per digit pair),
+ *                         exec_units = flops the tensor cores execute on stored slices
+ *   ESMP2_KT_COUPLING     element-wise coupling pass (five block launches); units = bytes of
+ *                         one read of x and one read and write of y
+ *   ESMP2_KT_GEMM64       float64 GEMM (transforms, float64 sigma); units = flops
+ *   ESMP2_KT_E2S          S-space energy sum; units = S-space elements
+ * esmp2_kernel_times synchronises the recorded events, fills out[ESMP2_KT_COUNT] with the
+ * totals since the last call and clears them ("launches" counts timed scopes: one coupling
+ * pass, one E2_S sector).  Enabling adds two event records per scope. */
+typedef enum {
+  ESMP2_KT_CONTRACTION = 0,
+  ESMP2_KT_COUPLING = 1,
+  ESMP2_KT_GEMM64 = 2,
+  ESMP2_KT_E2S = 3,
+  ESMP2_KT_COUNT = 4
+} esmp2_kernel_family;
+typedef struct {
+  int64_t launches;
+  double ms;          /* summed event-to-event device time */
+  double alg_units;
+  double exec_units;
+} esmp2_kernel_time;
+void esmp2_kernel_timing(int enable);
+esmp2_status esmp2_kernel_times(esmp2_kernel_time *out);
+
 /* Allocation-free bf16 virtual-index contraction (the paper has no counterpart; this is a
  * library service).  Computes, like esmp2_virtual_contraction(..., ESMP2_MIXED_BF16),
  *     y_s = X_s F + F X_s   for s = 0..S-1,  X_s = x[s] (Nv x Nv),  F = Fvv (Nv x Nv)

@@ -88,6 +88,8 @@ void gemm64(const Gemm64 &g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   const int mtiles = (int)cdiv(g.M, BM);
   const int64_t tiles = (int64_t)mtiles * cdiv(g.N, BN);
+  const double flops = 2.0 * g.M * (double)g.N * g.K * g.batch;
+  KScope ks(st, ESMP2_KT_GEMM64, flops, flops);
   for (int b0 = 0; b0 < g.batch; b0 += 65535) {
     Gemm64 gg = g;
     gg.batch = std::min(65535, g.batch - b0);

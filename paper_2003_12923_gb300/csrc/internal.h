@@ -150,4 +150,23 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
 void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Process-wide kernel timing (esmp2_kernel_timing): a scope records one event pair around
+// the launches it encloses when timing is on.
+class KScope {
+ public:
+  KScope(cudaStream_t st, int family, double alg_units, double exec_units);
+  ~KScope();
+  KScope(const KScope &) = delete;
+  KScope &operator=(const KScope &) = delete;
+ private:
+  cudaStream_t st_;
+  int fam_;
+  double alg_, exec_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+// unique D+L amplitudes of TOP(1) (spin-flip pairs counted once) and the algorithmic flops
+// of the virtual-index terms of one sigma build: 2 flops x 2 virtual sums of length Nv each
+double unique_amplitudes(int No, int Nv);
+inline double alg_virtual_flops(int No, int Nv) { return 4.0 * unique_amplitudes(No, Nv) * Nv; }
 }  // namespace esmp2

@@ -335,22 +335,46 @@ struct SCtx {
   }
 };
 
-// sector A: up-up-up, lowest pair u >= 1; block = (u, j, k), threads over b, loop c > b
+// 1 / D from a float seed and two Newton-Raphson steps (each squares the relative error:
+// 2^-24 -> 2^-48 -> below float64 rounding); D is a sum of orbital energies, far from the
+// float range limits.
+__device__ __forceinline__ double rcp64(double D) {
+  double r = (double)(1.0f / (float)D);
+  r = fma(r, fma(-D, r, 1.0), r);
+  r = fma(r, fma(-D, r, 1.0), r);
+  return r;
+}
+
+// In every sector the common case holds exactly one TOP pair (u, u'); then b_I is a single
+// antisymmetrised integral times lam_u and the term is evaluated inline.  Triples whose
+// other indices form a second TOP pair take the general P(k/ij)P(c/ab) form (s.term).
+// Sectors A and B: loop over c, threads over b < c (coalesced (kc|jb), (jc|kb) rows).
+
+// sector A: up-up-up, lowest pair u >= 1; block = (u, j, k)
 __global__ void k_e2s_a(SCtx s, double *red) {
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && j < k && j != u && k != u) {
-    for (int b = threadIdx.x; b < Nv; b += blockDim.x) {
-      if (b == u) continue;
-      for (int c = b + 1; c < Nv; ++c) {
-        if (c == u) continue;
-        const bool pj = (b == j || c == j), pk = (b == k || c == k);
-        if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
-        if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
-        const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
-        v[0] += s.term(ho, hs, po, ps);
+    const double lu = s.lam[u];
+    const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
+    for (int c = 1; c < Nv; ++c) {
+      if (c == u) continue;
+      const double Dc = Dh + s.Fv(c);
+      const bool cjk = (c == j || c == k);
+      for (int b = threadIdx.x; b < c; b += blockDim.x) {
+        if (b == u) continue;
+        if (cjk || b == j || b == k) {
+          const bool pj = (b == j || c == j), pk = (b == k || c == k);
+          if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
+          if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
+          const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
+          v[0] += s.term(ho, hs, po, ps);
+          continue;
+        }
+        const double bI = lu * (s.g(k, c, j, b) - s.g(j, c, k, b));
+        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(b));
       }
     }
   }
@@ -364,30 +388,52 @@ __global__ void k_e2s_b(SCtx s, double *red) {
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && j < k) {
-    for (int b = threadIdx.x; b < Nv; b += blockDim.x)
-      for (int c = b + 1; c < Nv; ++c) {
-        if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
-        const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
-        v[0] += s.term(ho, hs, po, ps);
+    const double lu = s.lam[u];
+    const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
+    for (int c = 1; c < Nv; ++c) {
+      const double Dc = Dh + s.Fv(c);
+      const bool cjk = (c == j || c == k);
+      for (int b = threadIdx.x; b < c; b += blockDim.x) {
+        if (cjk || b == j || b == k) {
+          if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
+          const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
+          v[0] += s.term(ho, hs, po, ps);
+          continue;
+        }
+        const double bI = lu * (s.g(k, c, j, b) - s.g(j, c, k, b));
+        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(b));
       }
+    }
   }
   block_partials<1>(v, red);
 }
 
-// sector C: up-down-down without an up pair; lowest down pair u >= 1; block = (u, i, k)
+// sector C: up-down-down without an up pair; lowest down pair u >= 1; block = (u, i, k),
+// threads over c (coalesced (ia|kc) rows), loop over a
 __global__ void k_e2s_c(SCtx s, double *red) {
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
   const int u = (int)(blk / ((int64_t)No * No)), i = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && k != u) {
-    for (int a = threadIdx.x; a < Nv; a += blockDim.x) {
-      if (a == i) continue;
-      for (int c = 0; c < Nv; ++c) {
-        if (c == u) continue;
-        if (c == k && (k < u || k == 0)) continue;
-        const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, c}, ps[3] = {0, 1, 1};
-        v[0] += s.term(ho, hs, po, ps);
+    const double lu = s.lam[u];
+    const double Dh = s.Fv(u) - s.Fo(i) - s.Fo(u) - s.Fo(k) - s.omega;
+    for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
+      if (c == u) continue;
+      if (c == k) {
+        if (k < u || k == 0) continue;
+        for (int a = 0; a < Nv; ++a) {
+          if (a == i) continue;
+          const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, c}, ps[3] = {0, 1, 1};
+          v[0] += s.term(ho, hs, po, ps);
+        }
+        continue;
+      }
+      const double Dc = Dh + s.Fv(c);
+      for (int a = 0; a < Nv; ++a) {
+        if (a == i) continue;
+        const double bI = lu * s.g(i, a, k, c);
+        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(a));
       }
     }
   }
@@ -519,9 +565,12 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
     const int nb = No * No * No;
     double tot = 0.0;
     for (int sector = 0; sector < 3; ++sector) {
-      if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, h->red);
-      else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, h->red);
-      else k_e2s_c<<<nb, 128, 0, st>>>(sc, h->red);
+      {
+        KScope ks(st, ESMP2_KT_E2S, 0.0, 0.0);
+        if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, h->red);
+        else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, h->red);
+        else k_e2s_c<<<nb, 128, 0, st>>>(sc, h->red);
+      }
       k_finalize<<<1, 256, 0, st>>>(h->red, nb, 1, h->red_out, 3);
       h->launches += 2;
       if ((s = read_slots(h, sl, 32))) return s;

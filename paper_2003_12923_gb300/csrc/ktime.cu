@@ -1,0 +1,76 @@
+// Process-wide timing of the kernel families of the hot path (esmp2_kernel_timing).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace esmp2 {
+namespace {
+struct Rec {
+  cudaEvent_t a, b;
+  int fam;
+  double alg, exec;
+};
+std::atomic<int> g_on{0};
+std::mutex g_mu;
+std::vector<Rec> g_recs;
+}  // namespace
+
+KScope::KScope(cudaStream_t st, int family, double alg_units, double exec_units)
+    : st_(st), fam_(family), alg_(alg_units), exec_(exec_units) {
+  if (!g_on.load(std::memory_order_relaxed)) return;
+  if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+    if (a_) cudaEventDestroy(a_);
+    a_ = b_ = nullptr;
+    return;
+  }
+  cudaEventRecord(a_, st_);
+}
+
+KScope::~KScope() {
+  if (!a_) return;
+  cudaEventRecord(b_, st_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back({a_, b_, fam_, alg_, exec_});
+}
+
+double unique_amplitudes(int No, int Nv) {
+  auto c2 = [](double n) { return n * (n - 1) / 2; };
+  const double T = c2(No) * c2(Nv), S = 0.5 * No * No * (double)Nv * Nv, X = c2(No - 1) * c2(Nv - 1),
+               Y = c2(No) * c2(Nv), Z = ((double)No * Nv - 1) * (No - 1) * (double)(Nv - 1);
+  return T + S + X + Y + Z;
+}
+}  // namespace esmp2
+
+extern "C" {
+
+void esmp2_kernel_timing(int enable) { esmp2::g_on.store(enable ? 1 : 0); }
+
+esmp2_status esmp2_kernel_times(esmp2_kernel_time *out) {
+  using namespace esmp2;
+  if (!out) return ESMP2_ERR_INVALID_ARG;
+  for (int k = 0; k < ESMP2_KT_COUNT; ++k) out[k] = esmp2_kernel_time{0, 0.0, 0.0, 0.0};
+  std::vector<Rec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    recs.swap(g_recs);
+  }
+  esmp2_status st = ESMP2_OK;
+  for (const Rec &r : recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      st = ESMP2_ERR_CUDA;
+    if (r.fam >= 0 && r.fam < ESMP2_KT_COUNT) {
+      out[r.fam].launches += 1;
+      out[r.fam].ms += ms;
+      out[r.fam].alg_units += r.alg;
+      out[r.fam].exec_units += r.exec;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  return st;
+}
+
+}  // extern "C"

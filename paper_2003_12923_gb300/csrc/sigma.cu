@@ -159,113 +159,200 @@ void launch_inter(esmp2_handle *h, const CtxT<CT> &c, const T *x, const Coupling
   h->launches += 4;
 }
 
+// Vector loads/stores of VW consecutive elements (16 bytes when VW * sizeof(T) == 16); the
+// address must be 16-byte aligned: only slice rows (Nv a multiple of VW) and the coupling
+// intermediates (separate allocations, rows of Nv) are read this way, never rows of F.
+template <int VW, typename T, typename CT>
+__device__ __forceinline__ void ldv(const T *p, CT (&o)[VW]) {
+  if constexpr (VW == 4 && sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = (CT)t.x; o[1] = (CT)t.y; o[2] = (CT)t.z; o[3] = (CT)t.w;
+  } else if constexpr (VW == 2 && sizeof(T) == 8) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = (CT)t.x; o[1] = (CT)t.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < VW; ++k) o[k] = (CT)p[k];
+  }
+}
+template <int VW, typename T, typename CT>
+__device__ __forceinline__ void stv(T *p, const CT (&v)[VW]) {
+  if constexpr (VW == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  } else if constexpr (VW == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2 *>(p) = make_double2((double)v[0], (double)v[1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VW; ++k) p[k] = (T)v[k];
+  }
+}
+
 // y += couplings - omega x (+ pair energy on L blocks); y = 0 on non-amplitude slots.
-// One CTA iteration per 32 x 32 tile (a, b) of one slice (blk, i, j): block, slice and tile
-// are uniform over the CTA, so every gather is either a coalesced row of a slice or a
-// broadcast; the one transposed operand (Z_ji^ba of the S block) goes through shared memory.
-template <typename TX, typename TY, typename CT>
-__global__ void __launch_bounds__(256, 4) k_couple(CtxT<CT> c, const TX *__restrict__ x, TY *__restrict__ y,
+// One launch per block; a CTA owns a 32-row strip of one slice (i, j) and walks its
+// 32 x (32 VW) tiles along b, each thread VW consecutive columns of four rows.  Block,
+// slice and strip are uniform over the CTA, so every gather is a coalesced (vector) row of
+// some slice or a broadcast, all slice pointers are formed once, and the element loop runs
+// on 32-bit offsets; the one transposed operand (Z_ji^ba of the S block) goes through
+// shared memory.
+template <int BLK, int VW, typename TX, typename TY, typename CT>
+__global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restrict__ x, TY *__restrict__ y,
                                                 CouplingsT<CT> cp) {
-  __shared__ CT zt[32][33];
-  const int No = c.No, Nv = c.Nv;
-  const int nt = (Nv + 31) >> 5;
-  const int64_t NvNv = (int64_t)Nv * Nv, NN = (int64_t)No * No;
-  const int64_t ntiles = 5 * NN * nt * nt;
+  constexpr int TW = 32 * VW;  // tile columns
+  __shared__ CT zt[TW][33];
+  const int No = c.No, Nv = c.Nv, nt = (Nv + TW - 1) / TW;
+  const int i = blockIdx.y / No, j = blockIdx.y % No;
+  const int a_base = blockIdx.x << 5;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const CT shift = c.Fv(0, 0) - c.Fo(0, 0);
-  const CT f00 = c.Fov(0, 0);
-  auto slice = [&](int bl, int ii, int jj) { return x + ((int64_t)bl * NN + (int64_t)ii * No + jj) * NvNv; };
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t f = t;
-    const int tb = (int)(f % nt); f /= nt;
-    const int ta = (int)(f % nt); f /= nt;
-    const int j = (int)(f % No); f /= No;
-    const int i = (int)(f % No);
-    const int blk = (int)(f / No);
-    const int a0 = ta << 5, b0 = tb << 5, b = b0 + tx;
-    const bool i0 = i == 0, j0 = j == 0, b0f = b == 0;
-    const TX *xs = slice(blk, i, j);
-    TY *ys = y + (xs - x);
-    if (blk == BS) {  // Z_ji[b][a] for the tile, read along a and used along b
+  const int64_t NvNv = (int64_t)Nv * Nv, NN = (int64_t)No * No;
+  auto S = [&](int bl, int ii, int jj) { return x + ((int64_t)bl * NN + (int64_t)ii * No + jj) * NvNv; };
+  const TX *xs = S(BLK, i, j);
+  TY *ys = y + (xs - x);
+  const bool i0 = i == 0, j0 = j == 0;
+  const CT om = c.omega, shift = c.Fv(0, 0) - c.Fo(0, 0), f00 = c.Fov(0, 0);
+  const CT fdiag = c.Fo(i, i) + c.Fo(j, j), foi = c.Fo(0, i), foj = c.Fo(0, j);
+  const CT fio = c.Fov(i, 0), fjo = c.Fov(j, 0);
+  const TX *A0j = S(BLK, 0, j), *Ai0 = S(BLK, i, 0);
+  const CT *OC1 = c.arrow ? cp.OC1 + ((int64_t)BLK * No + j) * NvNv : nullptr;
+  const CT *OC2 = c.arrow ? cp.OC2 + ((int64_t)BLK * No + i) * NvNv : nullptr;
+  const CT *Fo_i = c.F + (int64_t)i * c.N + No, *Fo_j = c.F + (int64_t)j * c.N + No, *Fo_0 = c.F + No;
+  for (int tb = 0; tb < nt; ++tb) {
+    const int b = tb * TW + tx * VW;  // first of this thread's VW columns
+    if constexpr (BLK == BS) {  // Z_ji[b][a] for the tile, read along a and used along b
       __syncthreads();
-      const TX *zji = slice(BZ, j, i);
-      for (int r = ty; r < 32; r += 8) {
-        const int bb = b0 + r, aa = a0 + tx;
-        zt[r][tx] = (bb < Nv && aa < Nv) ? (CT)zji[(int64_t)bb * Nv + aa] : CT(0);
+      const TX *zji = S(BZ, j, i);
+      for (int r = ty; r < TW; r += 8) {
+        const int bb = tb * TW + r, aa = a_base + tx;
+        zt[r][tx] = (bb < Nv && aa < Nv) ? (CT)zji[bb * Nv + aa] : CT(0);
       }
       __syncthreads();
     }
     if (b >= Nv) continue;
-    const CT foi = c.Fo(0, i), foj = c.Fo(0, j), fdiag = c.Fo(i, i) + c.Fo(j, j);
-    for (int r = ty; r < 32; r += 8) {
-      const int a = a0 + r;
+    CT fob_0[VW], fob_i[VW], fob_j[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {  // rows of F start at arbitrary offsets: scalar loads
+      fob_0[k] = Fo_0[b + k];
+      fob_i[k] = Fo_i[b + k];
+      fob_j[k] = Fo_j[b + k];
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr;
+      const int a = a_base + r;
       if (a >= Nv) break;
-      const int64_t ab = (int64_t)a * Nv + b;
-      if (!valid_elem(blk, i, j, a, b)) { ys[ab] = (TY)0; continue; }
+      const int ab = a * Nv + b;
       const bool a0f = a == 0;
-      const CT xe = (CT)xs[ab];
-      CT v = -c.omega * xe;
+      CT xe[VW], v[VW], t1[VW], t2[VW];
+      ldv<VW>(xs + ab, xe);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) v[k] = -om * xe[k];
       if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
-        v -= fdiag * xe;
-        v -= i0 ? cp.OC1[((int64_t)blk * No + j) * NvNv + ab] : foi * (CT)slice(blk, 0, j)[ab];
-        v -= j0 ? cp.OC2[((int64_t)blk * No + i) * NvNv + ab] : foj * (CT)slice(blk, i, 0)[ab];
+        if (i0) ldv<VW>(OC1 + ab, t1); else ldv<VW>(A0j + ab, t1);
+        if (j0) ldv<VW>(OC2 + ab, t2); else ldv<VW>(Ai0 + ab, t2);
+        const CT s1 = i0 ? CT(1) : foi, s2 = j0 ? CT(1) : foj;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] -= fdiag * xe[k] + s1 * t1[k] + s2 * t2[k];
       }
-      switch (blk) {
-        case BT: {
-          v += f00 * ((CT)slice(BX, i, j)[ab] + (CT)slice(BY, i, j)[ab]);
-          const int64_t ij = ((int64_t)i * No + j) * Nv;
-          if (a0f) v -= cp.VX[ij + b];
-          if (b0f) v += cp.VX[ij + a];
-          if (i0) v -= cp.OX[j * NvNv + ab];
-          if (j0) v += cp.OX[i * NvNv + ab];
-          if (i0 && a0f) v += cp.G[j * Nv + b];
-          if (j0 && a0f) v -= cp.G[i * Nv + b];
-          if (i0 && b0f) v -= cp.G[j * Nv + a];
-          if (j0 && b0f) v += cp.G[i * Nv + a];
-          break;
+      if constexpr (BLK == BT) {
+        ldv<VW>(S(BX, i, j) + ab, t1);
+        ldv<VW>(S(BY, i, j) + ab, t2);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] += f00 * (t1[k] + t2[k]);
+        const int ij = (i * No + j) * Nv;
+        if (a0f) { ldv<VW>(cp.VX + ij + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (i0) { ldv<VW>(cp.OX + j * NvNv + ab, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (j0) { ldv<VW>(cp.OX + i * NvNv + ab, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
+        if (i0 && a0f) { ldv<VW>(cp.G + j * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
+        if (j0 && a0f) { ldv<VW>(cp.G + i * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (b == 0) {  // column 0 is the first element of this thread's vector
+          v[0] += cp.VX[ij + a];
+          if (i0) v[0] -= cp.G[j * Nv + a];
+          if (j0) v[0] += cp.G[i * Nv + a];
         }
-        case BS: {
-          if (j0 && b0f) v += cp.H[i * Nv + a];
-          if (i0 && a0f) v += cp.H[j * Nv + b];
-          v += f00 * ((CT)slice(BZ, i, j)[ab] + zt[tx][r]);
-          if (b0f) v -= cp.WZ[((int64_t)i * No + j) * Nv + a];
-          if (a0f) v -= cp.WZ[((int64_t)j * No + i) * Nv + b];
-          if (j0) v -= cp.OZ[i * NvNv + ab];
-          if (i0) v -= cp.OZ[j * NvNv + (int64_t)b * Nv + a];
-          break;
+      } else if constexpr (BLK == BS) {
+        ldv<VW>(S(BZ, i, j) + ab, t1);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] += f00 * (t1[k] + zt[tx * VW + k][r]);
+        if (i0 && a0f) { ldv<VW>(cp.H + j * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
+        if (a0f) { ldv<VW>(cp.WZ + (j * No + i) * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (j0) { ldv<VW>(cp.OZ + i * NvNv + ab, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (i0) {
+#pragma unroll
+          for (int k = 0; k < VW; ++k) v[k] -= cp.OZ[j * NvNv + (b + k) * Nv + a];
         }
-        case BX: {
-          const TX *T = slice(BT, i, j), *T0j = slice(BT, 0, j), *T0i = slice(BT, 0, i);
-          v += shift * xe + f00 * (CT)T[ab];
-          v += -c.Fov(0, a) * (CT)T[b] + c.Fov(0, b) * (CT)T[a];
-          v += -c.Fov(i, 0) * (CT)T0j[ab] + c.Fov(j, 0) * (CT)T0i[ab];
-          v += c.Fov(i, a) * (CT)T0j[b] - c.Fov(j, a) * (CT)T0i[b] - c.Fov(i, b) * (CT)T0j[a] + c.Fov(j, b) * (CT)T0i[a];
-          break;
+        if (b == 0) {
+          if (j0) v[0] += cp.H[i * Nv + a];
+          v[0] -= cp.WZ[(i * No + j) * Nv + a];
         }
-        case BY: {
-          const TX *S0i = slice(BS, 0, i), *S0j = slice(BS, 0, j);
-          v += shift * xe + f00 * (CT)slice(BT, i, j)[ab];
-          v += c.Fov(j, b) * (CT)S0i[a] - c.Fov(i, b) * (CT)S0j[a] - c.Fov(j, a) * (CT)S0i[b] + c.Fov(i, a) * (CT)S0j[b];
-          if (i0 && a0f) v += cp.CYZ[j * Nv + b];
-          if (j0 && a0f) v -= cp.CYZ[i * Nv + b];
-          if (i0 && b0f) v -= cp.CYZ[j * Nv + a];
-          if (j0 && b0f) v += cp.CYZ[i * Nv + a];
-          break;
+      } else if constexpr (BLK == BX) {
+        const TX *T = S(BT, i, j), *T0j = S(BT, 0, j), *T0i = S(BT, 0, i);
+        const CT foa_0 = Fo_0[a], foa_i = Fo_i[a], foa_j = Fo_j[a];
+        const CT Ta = (CT)T[a], T0ja = (CT)T0j[a], T0ia = (CT)T0i[a];
+        CT Tab[VW], Tb[VW], T0jab[VW], T0iab[VW], T0jb[VW], T0ib[VW];
+        ldv<VW>(T + ab, Tab); ldv<VW>(T + b, Tb);
+        ldv<VW>(T0j + ab, T0jab); ldv<VW>(T0i + ab, T0iab);
+        ldv<VW>(T0j + b, T0jb); ldv<VW>(T0i + b, T0ib);
+#pragma unroll
+        for (int k = 0; k < VW; ++k)
+          v[k] += shift * xe[k] + f00 * Tab[k] - foa_0 * Tb[k] + fob_0[k] * Ta - fio * T0jab[k] + fjo * T0iab[k]
+                + foa_i * T0jb[k] - foa_j * T0ib[k] - fob_i[k] * T0ja + fob_j[k] * T0ia;
+      } else if constexpr (BLK == BY) {
+        const TX *S0i = S(BS, 0, i), *S0j = S(BS, 0, j);
+        const CT S0ia = (CT)S0i[a], S0ja = (CT)S0j[a], foa_i = Fo_i[a], foa_j = Fo_j[a];
+        CT Tab[VW], S0ib[VW], S0jb[VW];
+        ldv<VW>(S(BT, i, j) + ab, Tab); ldv<VW>(S0i + b, S0ib); ldv<VW>(S0j + b, S0jb);
+#pragma unroll
+        for (int k = 0; k < VW; ++k)
+          v[k] += shift * xe[k] + f00 * Tab[k] + fob_j[k] * S0ia - fob_i[k] * S0ja - foa_j * S0ib[k] + foa_i * S0jb[k];
+        if (i0 && a0f) { ldv<VW>(cp.CYZ + j * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
+        if (j0 && a0f) { ldv<VW>(cp.CYZ + i * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
+        if (b == 0) {
+          if (i0) v[0] -= cp.CYZ[j * Nv + a];
+          if (j0) v[0] += cp.CYZ[i * Nv + a];
         }
-        default: {  // BZ
-          const TX *Sij = slice(BS, i, j), *Si0 = slice(BS, i, 0);
-          v += shift * xe;
-          v += f00 * (CT)Sij[ab] - c.Fov(0, b) * (CT)Sij[(int64_t)a * Nv] - c.Fov(j, 0) * (CT)Si0[ab]
-             + c.Fov(j, b) * (CT)Si0[(int64_t)a * Nv] + c.Fov(i, a) * (CT)slice(BT, 0, j)[b];
-          const CT y0 = (CT)slice(BY, 0, j)[b];
-          if (i0) v += c.Fv(a, 0) * y0;
-          if (a0f) v -= foi * y0;
-          break;
+      } else {  // BZ
+        const TX *Sij = S(BS, i, j), *Si0 = S(BS, i, 0);
+        const CT Sija0 = (CT)Sij[a * Nv], Si0a0 = (CT)Si0[a * Nv], foa_i = Fo_i[a], fva = c.Fv(a, 0);
+        CT Sijab[VW], Si0ab[VW], T0jb[VW], Y0jb[VW];
+        ldv<VW>(Sij + ab, Sijab); ldv<VW>(Si0 + ab, Si0ab);
+        ldv<VW>(S(BT, 0, j) + b, T0jb); ldv<VW>(S(BY, 0, j) + b, Y0jb);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          v[k] += shift * xe[k] + f00 * Sijab[k] - fob_0[k] * Sija0 - fjo * Si0ab[k] + fob_j[k] * Si0a0
+                + foa_i * T0jb[k];
+          if (i0) v[k] += fva * Y0jb[k];
+          if (a0f) v[k] -= foi * Y0jb[k];
         }
       }
-      ys[ab] = (TY)((CT)ys[ab] + v);
+      CT yo[VW];
+      ldv<VW>(ys + ab, yo);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) yo[k] = valid_elem(BLK, i, j, a, b + k) ? yo[k] + v[k] : CT(0);
+      stv<VW>(ys + ab, yo);
     }
   }
+}
+
+template <int VW, typename TX, typename TY, typename CT>
+void launch_couple_vw(const CtxT<CT> &c, const TX *x, TY *y, const CouplingsT<CT> &cp, cudaStream_t st) {
+  const dim3 grid((unsigned)((c.Nv + 31) / 32), (unsigned)(c.No * c.No));
+  k_couple<BT, VW, TX, TY, CT><<<grid, 256, 0, st>>>(c, x, y, cp);
+  k_couple<BS, VW, TX, TY, CT><<<grid, 256, 0, st>>>(c, x, y, cp);
+  k_couple<BX, VW, TX, TY, CT><<<grid, 256, 0, st>>>(c, x, y, cp);
+  k_couple<BY, VW, TX, TY, CT><<<grid, 256, 0, st>>>(c, x, y, cp);
+  k_couple<BZ, VW, TX, TY, CT><<<grid, 256, 0, st>>>(c, x, y, cp);
+}
+
+// 16-byte vectors when every row of a slice starts on a 16-byte boundary
+template <typename TX, typename TY, typename CT>
+void launch_couple(const CtxT<CT> &c, const TX *x, TY *y, const CouplingsT<CT> &cp, cudaStream_t st) {
+  constexpr int VW = 16 / sizeof(TX);
+  const double bytes = 5.0 * c.B * (sizeof(TX) + 2.0 * sizeof(TY));
+  KScope ks(st, ESMP2_KT_COUPLING, bytes, bytes);
+  const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+  if (aligned && c.Nv % VW == 0 && sizeof(TX) == sizeof(TY) && sizeof(TX) == sizeof(CT))
+    launch_couple_vw<VW>(c, x, y, cp, st);
+  else
+    launch_couple_vw<1>(c, x, y, cp, st);
 }
 
 }  // namespace
@@ -283,8 +370,8 @@ void launch_intermediates64(esmp2_handle *h, const double *F, int arrow, const d
 }
 
 void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *x, double *y) {
-  k_couple<double, double, double><<<1216, 256, 0, h->stream>>>(make_ctx<double>(h, F, arrow), x, y, h->cp);
-  h->launches += 1;
+  launch_couple<double, double, double>(make_ctx<double>(h, F, arrow), x, y, h->cp, h->stream);
+  h->launches += 5;
 }
 
 // float coupling + arrow occupied pass of the inner (low-precision) sigma: float arithmetic
@@ -292,8 +379,8 @@ void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *
 void couple32(esmp2_handle *h, const float *F32, const float *x, float *y) {
   const CtxT<float> c = make_ctx<float>(h, F32, 1);
   launch_inter<float, float>(h, c, x, h->cp32);
-  k_couple<float, float, float><<<1216, 256, 0, h->stream>>>(c, x, y, h->cp32);
-  h->launches += 1;
+  launch_couple<float, float, float>(c, x, y, h->cp32, h->stream);
+  h->launches += 5;
 }
 
 // Part (1) in float64: four strided batched GEMM passes over all five blocks.

@@ -433,7 +433,8 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
 namespace {
 // Fills the tile geometry of `g` and launches k_virt.  xd: bf16 x planes [planes][S_plane][Nv][Nvp];
 // Fd: bf16 F planes [F_planes][Nv][Nvp]; Nvp = Nv rounded up to 8 (16-byte row pitch).
-const char *launch_virt(cudaStream_t st, const void *xd, int x_planes, const void *Fd, int F_planes, tc::Args &g) {
+const char *launch_virt(cudaStream_t st, const void *xd, int x_planes, const void *Fd, int F_planes, tc::Args &g,
+                        double alg_flops, double exec_flops) {
   const int Nv = g.Nv, Nvp = (Nv + 7) & ~7;
   if (!get_encode()) return "cuTensorMapEncodeTiled unavailable";
   if (g.nslices <= 0) return nullptr;
@@ -460,6 +461,7 @@ const char *launch_virt(cudaStream_t st, const void *xd, int x_planes, const voi
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(g.tiles, sms);
+  KScope ks(st, ESMP2_KT_CONTRACTION, alg_flops, exec_flops);
   tc::k_virt<<<grid, tc::NTHREADS, tc::SMEM_BYTES, st>>>(mXa, mXb, mFa, mFb, g);
   return nullptr;
 }
@@ -484,7 +486,9 @@ tc::Args plain_args(int Nv, int S, float *y, int *err) {
 // xb: bf16 [S][Nv][Nvp], Fb: bf16 [Nv][Nvp], Nvp = Nv rounded up to 8 (16-byte row pitch).
 esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err) {
   tc::Args g = plain_args(h->d.Nv, S, y, err);
-  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g)) { h->err = m; return ESMP2_ERR_CUDA; }
+  const double nv = h->d.Nv, exec = 4.0 * nv * nv * nv * S;
+  const double alg = S == 5 * h->d.No * h->d.No ? alg_virtual_flops(h->d.No, h->d.Nv) : exec;
+  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g, alg, exec)) { h->err = m; return ESMP2_ERR_CUDA; }
   h->launches += 1;
   return check_cuda(h, cudaGetLastError(), "virt_bf16");
 }
@@ -599,7 +603,10 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
     g.level = L;
     g.first = (L == 2);
     g.err = h->dflag;
-    if (const char *m = launch_virt(h->stream, h->xdig, P, h->Fdig, P, g)) {
+    const double nv3 = (double)Nv * Nv * Nv;
+    const double per_pair = sym ? 3.0 * (No * (No - 1) / 2) * 2.0 * nv3 + 2.0 * No * No * 4.0 * nv3 : 4.0 * nv3 * S;
+    const double alg_pair = sym ? alg_virtual_flops(No, Nv) : per_pair;
+    if (const char *m = launch_virt(h->stream, h->xdig, P, h->Fdig, P, g, g.npairs * alg_pair, g.npairs * per_pair)) {
       h->err = m;
       return ESMP2_ERR_CUDA;
     }
@@ -682,7 +689,8 @@ extern "C" esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const
   tc::k_fvv_bf16<<<256, 256, 0, st>>>(Fvv, 0, Nv, Nvp, Fb);
   tc::k_to_bf16<double><<<1216, 256, 0, st>>>(x, xb, (int64_t)S * Nv, Nv, Nvp);
   tc::Args g = plain_args(Nv, S, y32, err);
-  if (launch_virt(st, xb, 1, Fb, 1, g)) return ESMP2_ERR_CUDA;
+  const double exec = 4.0 * (double)Nv * Nv * Nv * S;
+  if (launch_virt(st, xb, 1, Fb, 1, g, exec, exec)) return ESMP2_ERR_CUDA;
   k_noalloc_f32_to_f64<<<1216, 256, 0, st>>>(y32, y, (int64_t)S * Nv * Nv);
   int flag = 0;
   cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -51,6 +51,11 @@ class EnergyParts(ctypes.Structure):
                 ("E2_S", ctypes.c_double)]
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("alg_units", ctypes.c_double),
+                ("exec_units", ctypes.c_double)]
+
+
 class BatchResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("e2", EnergyParts), ("info", SolveInfo),
                 ("kernel_launches", ctypes.c_int64), ("message", ctypes.c_char * 160)]
@@ -59,7 +64,8 @@ class BatchResult(ctypes.Structure):
 EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_stream", "esmp2_layout",
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
            "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma",
-           "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc", "esmp2_batch_solve", "esmp2_grad")
+           "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc", "esmp2_batch_solve", "esmp2_grad",
+           "esmp2_kernel_timing", "esmp2_kernel_times")
 MIXED_READY = True
 
 
@@ -114,12 +120,33 @@ def load(path: str | None = None):
         L.esmp2_grad.argtypes = [P, P, P, I, P]
         L.esmp2_kernel_launches.restype = I64
         L.esmp2_kernel_launches.argtypes = [P]
+        L.esmp2_kernel_timing.restype = None
+        L.esmp2_kernel_timing.argtypes = [I]
+        L.esmp2_kernel_times.restype = I
+        L.esmp2_kernel_times.argtypes = [ctypes.POINTER(KernelTime)]
         if path is None:
             _lib = L
         return L
 
 
 NOALLOC_MAX_BYTES = 64 << 20
+
+KERNEL_FAMILIES = ("contraction", "coupling", "gemm64", "e2s")
+
+
+def kernel_timing(enable: bool):
+    """Switch the process-wide event timing of the kernel families on or off."""
+    load().esmp2_kernel_timing(1 if enable else 0)
+
+
+def kernel_times():
+    """Totals per kernel family since the last call (see esmp2_kernel_times)."""
+    out = (KernelTime * len(KERNEL_FAMILIES))()
+    st = load().esmp2_kernel_times(out)
+    if st != OK:
+        raise Esmp2Error(st, "esmp2_kernel_times failed")
+    return {name: {"launches": int(t.launches), "ms": float(t.ms), "alg_units": float(t.alg_units),
+                   "exec_units": float(t.exec_units)} for name, t in zip(KERNEL_FAMILIES, out)}
 
 
 def batch_solve(instances, tol: float = 1e-8, maxit: int = 2000, precision: int = FP64, concurrency: int = 2):

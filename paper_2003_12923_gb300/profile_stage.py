@@ -12,6 +12,7 @@ Stages:
     sigma-fp64    float64 sigma build
     sigma-fp64tc  float64 sigma build with the tensor-core virtual-index terms
     sigma-mixed   sigma with bf16 virtual-index terms, float64 elsewhere
+    sigma-inner   the inner (float32 vector) sigma of the mixed solve, per-stage timed
     solve-mixed   a mixed-precision solve to --tol (create excluded)
 """
 from __future__ import annotations
@@ -32,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--sigma-off", type=float, default=1e-3)
     ap.add_argument("--stage", default="virt-bf16",
                     choices=["virt-bf16", "virt-fp64tc", "virt-fp64", "sigma-fp64", "sigma-fp64tc", "sigma-mixed",
-                             "solve-mixed"])
+                             "sigma-inner", "solve-mixed"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
     args = ap.parse_args(argv)
@@ -50,6 +51,9 @@ def main(argv=None):
     if args.stage == "solve-mixed":
         info = h.solve(tol=args.tol, maxit=3000, precision=esmp2.MIXED_BF16)
         print("solve", info)
+    elif args.stage == "sigma-inner":
+        ms = h.profile_sigma(x, precision=esmp2.MIXED_BF16, reps=args.reps)
+        print("inner sigma stage ms (to bf16, virtual, -, couplings, total):", [round(float(v), 3) for v in ms[:5]])
     else:
         out = torch.empty_like(x)
         for _ in range(args.reps):
