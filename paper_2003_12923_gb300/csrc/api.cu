@@ -32,9 +32,10 @@ void free_handle(esmp2_handle *h) {
                   h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
                   h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
-                  h->xdig, h->Fdig, h->es, h->slist};
+                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (h->inner_graph) cudaGraphExecDestroy(h->inner_graph);
   if (h->hred) cudaFreeHost(h->hred);
 }
 

@@ -116,7 +116,11 @@ struct esmp2_handle {
   int *es = nullptr;        // per-slice exponents (5 No^2) and that of F_vv (last entry)
   int *slist = nullptr;     // slices of the symmetric form (T, X, Y with i < j; all S, Z)
   int nslist = 0, eF = 0;
+  void *Rdig = nullptr;     // digit planes of W_v^T (integral transforms on the tensor cores)
+  int eR = 0;
   int last_precision = 0;   // precision of the last solve (the energy's sigma follows it)
+  cudaGraphExec_t inner_graph = nullptr;  // one inner PCG iteration of the mixed solve
+  int64_t inner_graph_launches = 0, inner_graph_launches_pending = 0;
 };
 
 namespace esmp2 {
@@ -138,7 +142,7 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
 esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
-esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q);
+esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready = false);
 esmp2_status check_device_flag(esmp2_handle *h);
 void antisym_project(esmp2_handle *h, double *v);
 void combine_sym(esmp2_handle *h, double *y);
@@ -146,7 +150,9 @@ constexpr int kFp64TcLevels = 10;  // digit levels of the float64-exact tensor-c
 int split_levels_for(double tol);
 bool split_supported(const esmp2_handle *h, int levels);
 esmp2_status ensure_split(esmp2_handle *h);
+esmp2_status ensure_slist(esmp2_handle *h);
 esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64, int sym, int levels);
+esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y);
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
 void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace esmp2 {
@@ -199,6 +201,7 @@ __global__ void kt_p(VCtx c, const double *slots, const T *r, T *p) {
 struct ICtx {
   int64_t B;
   const float *dinv;
+  __nv_bfloat16 *pb;  // bf16 copy of p for the tensor-core operand (nullptr: not kept here)
 };
 __device__ __forceinline__ float blk_weight(int blk) { return blk == 1 ? 1.f : (blk == 4 ? 2.f : 0.5f); }
 
@@ -212,6 +215,7 @@ __global__ void ki_init(ICtx c, const double *r64, float *r, float *p, float *d,
       const float ri = (float)r64[e], z = c.dinv[e] * ri;
       r[e] = ri;
       p[e] = z;
+      if (c.pb) c.pb[e] = __float2bfloat16_rn(z);
       d[e] = 0.f;
       s0 += ri * z;
       s1 += ri * ri;
@@ -258,8 +262,11 @@ __global__ void ki_update(ICtx c, const double *slots, float *d, float *r, const
 
 __global__ void ki_p(ICtx c, const double *slots, const float *r, float *p) {
   const float beta = (float)slots[5];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
-    p[e] = c.dinv[e] * r[e] + beta * p[e];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const float pn = c.dinv[e] * r[e] + beta * p[e];
+    p[e] = pn;
+    if (c.pb) c.pb[e] = __float2bfloat16_rn(pn);
+  }
 }
 
 // Jacobi preconditioner as a float vector (computed once per basis, in float64)
@@ -470,7 +477,7 @@ double dot_w(esmp2_handle *h, const double *u, const double *v) {
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc) {
   auto t0 = std::chrono::steady_clock::now();
   if (h->x_semi) {  // the plain fp64 solve works in the TOP basis
-    rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
+    if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
     h->x_semi = 0;
   }
   const VCtx c = vctx(h);
@@ -597,7 +604,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
   if (!h->x_semi) {
-    rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);
+    if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);  // zero in every basis
     h->x_semi = 1;
   }
   cudaStream_t st = h->stream;
@@ -612,6 +619,16 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   ICtx ic;
   ic.B = h->d.B;
   ic.dinv = h->dinv32;
+  // rows of the bf16 operand are padded to a multiple of 8; without padding the PCG update
+  // writes it directly
+  const bool fused_bf16 = (h->d.Nv % 8) == 0;
+  ic.pb = fused_bf16 ? static_cast<__nv_bfloat16 *>(h->xlp) : nullptr;
+  // small instances are launch-bound: replay the inner iteration as a CUDA graph
+  bool use_graph = h->d.n <= (64LL << 20) && st != nullptr;
+  if (h->inner_graph && !use_graph) {
+    cudaGraphExecDestroy(h->inner_graph);
+    h->inner_graph = nullptr;
+  }
   double *x = h->s64.x, *r = h->s64.r, *q = h->s64.q;
   float *r32 = h->r32, *p32 = h->p32, *q32 = h->q32, *d32 = h->x32;
   int outer = 0, inner_total = 0, nsig64 = 0, nsiglow = 0;
@@ -641,7 +658,9 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d\n", outer, relres, inner_total);
     if (relres <= tol) { result = ESMP2_OK; break; }
     if (inner_total >= maxit) break;
-    // inner PCG on A d = r
+    // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
+    // contracts the slices i < j and mirrors them)
+    antisym_project(h, r);
     ki_init<<<kRedBlocks, kRedThreads, 0, st>>>(ic, r, r32, p32, d32, h->red);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 0);
     h->launches += 2;
@@ -650,15 +669,48 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     const double target = std::max(eta * r0, 0.25 * tol * bn);
     int inner = 0, since_best = 0;
     double best = r0;
-    while (inner_total < maxit) {
-      if ((s = sigma_inner(h, p32, q32))) return s;
-      ++nsiglow;
+    // one inner iteration: q = A p, alpha, x/r update, beta, p update (device scalars only)
+    auto inner_step = [&]() -> esmp2_status {
+      const int64_t l0 = h->launches;
+      esmp2_status s2 = sigma_inner(h, p32, q32, fused_bf16);
+      if (s2) return s2;
       ki_dot<<<kRedBlocks, kRedThreads, 0, st>>>(ic, p32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
       ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, d32, r32, p32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
       ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32);
       h->launches += 5;
+      h->inner_graph_launches_pending = h->launches - l0;
+      return check_cuda(h, cudaGetLastError(), "inner step");
+    };
+    while (inner_total < maxit) {
+      if (h->inner_graph) {
+        if ((s = check_cuda(h, cudaGraphLaunch(h->inner_graph, st), "inner graph"))) return s;
+        h->launches += h->inner_graph_launches;
+      } else if (use_graph && inner_total > 0) {
+        // capture one iteration (every pointer it touches belongs to the handle) and replay it
+        const int64_t l0 = h->launches;
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) ok = inner_step() == ESMP2_OK;
+        if (cudaStreamEndCapture(st, &g) != cudaSuccess || !g) ok = false;
+        if (ok) ok = cudaGraphInstantiate(&h->inner_graph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->launches = l0;
+        if (ok) {
+          h->inner_graph_launches = h->inner_graph_launches_pending;
+          if ((s = check_cuda(h, cudaGraphLaunch(h->inner_graph, st), "inner graph"))) return s;
+          h->launches += h->inner_graph_launches;
+        } else {
+          h->inner_graph = nullptr;
+          use_graph = false;
+          if ((s = inner_step())) return s;
+        }
+      } else {
+        if ((s = inner_step())) return s;
+      }
+      ++nsiglow;
       if ((s = read_slots(h, sl, 32))) return s;
       ++inner;
       ++inner_total;

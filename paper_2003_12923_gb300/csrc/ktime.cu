@@ -20,6 +20,8 @@ std::vector<Rec> g_recs;
 KScope::KScope(cudaStream_t st, int family, double alg_units, double exec_units)
     : st_(st), fam_(family), alg_(alg_units), exec_(exec_units) {
   if (!g_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;  // graph capture
   if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
     if (a_) cudaEventDestroy(a_);
     a_ = b_ = nullptr;

@@ -16,6 +16,7 @@
 namespace esmp2 {
 
 esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err);
+esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err);
 void to_bf16_f64(esmp2_handle *h, const double *src, void *dst, int64_t rows);
 void to_bf16_f32(esmp2_handle *h, const float *src, void *dst, int64_t rows);
 void fvv_bf16(esmp2_handle *h, const double *F, void *dst);
@@ -50,6 +51,64 @@ __global__ void k_build_rot(const double *V, int No, int Nv, double *R, double *
   }
 }
 
+// out[p][k'][q] = sum_k R[k][k'] in[p][k][q] for K <= 32 in double-float arithmetic: every
+// float64 operand is split into two floats (hi + lo); products are formed with the exact
+// product error (fma) and summed with Knuth's two-sum, so the float32 pipes do the work at
+// about 2^-46 relative accuracy; the float64 result is hi + lo.  The orbital rotations have
+// only No multiply-adds per element, which on this part would otherwise be float64-bound.
+constexpr int kDfK = 32;
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
+  const float ph = ah * bh;
+  const float pe = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
+  const float t = sh + ph;
+  const float bv = t - sh;
+  const float err = (sh - (t - bv)) + (ph - bv);
+  const float lo = sl + err + pe;
+  sh = t + lo;                 // renormalise (fast two-sum)
+  sl = lo - (sh - t);
+}
+
+__global__ void __launch_bounds__(256) k_mode_df(const double *in, double *out, int64_t P, int K, int64_t Q,
+                                                 const double *R) {
+  __shared__ float Rh[kDfK * kDfK], Rl[kDfK * kDfK];
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const double r = R[e];
+    const float hi = (float)r;
+    Rh[e] = hi;
+    Rl[e] = (float)(r - (double)hi);
+  }
+  __syncthreads();
+  const int64_t n = P * Q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / Q, q = e % Q;
+    const double *src = in + p * K * Q + q;
+    double *dst = out + p * K * Q + q;
+    float xh[kDfK], xl[kDfK];
+#pragma unroll
+    for (int k = 0; k < kDfK; ++k) {
+      if (k < K) {
+        const double v = src[k * Q];
+        xh[k] = (float)v;
+        xl[k] = (float)(v - (double)xh[k]);
+      }
+    }
+    for (int k2 = 0; k2 < K; k2 += 4) {
+      float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < kDfK; ++k) {
+        if (k < K) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (k2 + c < K) df_fma(sh[c], sl[c], Rh[k * K + k2 + c], Rl[k * K + k2 + c], xh[k], xl[k]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (k2 + c < K) dst[(k2 + c) * Q] = (double)sh[c] + (double)sl[c];
+    }
+  }
+}
+
 }  // namespace
 
 // in/out: block vectors; new occupied index i' = sum_i R[i][i'] (old i) (to_semi), or back.
@@ -61,8 +120,14 @@ void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, boo
   }
   const int dims[4] = {5, No, No, Nv * Nv};
   const double *R = to_semi ? h->Rocc : h->Rocct;
-  mode_product(in, tmp, dims, 1, R, No, No, h->stream);
-  mode_product(tmp, out, dims, 2, R, No, No, h->stream);
+  if (No <= kDfK) {
+    const int64_t NvNv = (int64_t)Nv * Nv;
+    k_mode_df<<<1216, 256, 0, h->stream>>>(in, tmp, 5, No, (int64_t)No * NvNv, R);
+    k_mode_df<<<1216, 256, 0, h->stream>>>(tmp, out, 5LL * No, No, NvNv, R);
+  } else {
+    mode_product(in, tmp, dims, 1, R, No, No, h->stream);
+    mode_product(tmp, out, dims, 2, R, No, No, h->stream);
+  }
   h->launches += 2;
 }
 
@@ -77,7 +142,7 @@ static esmp2_status alloc_mixed_buffers(esmp2_handle *h) {
   A(&h->xlp, sizeof(__nv_bfloat16) * (size_t)5 * No * No * Nv * Nvp);
   A(&h->Fvlp, sizeof(__nv_bfloat16) * (size_t)Nv * Nvp);
   A(reinterpret_cast<void **>(&h->ylp), sizeof(float) * n);
-  A(reinterpret_cast<void **>(&h->dflag), sizeof(int));
+  if (!h->dflag) A(reinterpret_cast<void **>(&h->dflag), sizeof(int));
   A(reinterpret_cast<void **>(&h->cp.OC1), sizeof(double) * (size_t)5 * No * Nv * Nv);
   A(reinterpret_cast<void **>(&h->cp.OC2), sizeof(double) * (size_t)5 * No * Nv * Nv);
   if (e != cudaSuccess) return check_cuda(h, e, "mixed buffers");
@@ -155,12 +220,14 @@ esmp2_status check_device_flag(esmp2_handle *h) {
 }
 
 // Inner (low-precision) sigma in the semicanonical-occupied basis: q = A p with the
-// virtual-index terms from bf16 operands on tcgen05 and everything else in fp32/fp64.
-esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q) {
+// virtual-index terms from bf16 operands on tcgen05 and everything else in float32.
+// p_bf16_ready: the PCG update already wrote bf16(p) into the operand buffer.  The T, X, Y
+// slices j > i are filled from i < j (antisymmetry), so p is taken as antisymmetric.
+esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready) {
   const int No = h->d.No, Nv = h->d.Nv;
   const int64_t rows = (int64_t)5 * No * No * Nv;
-  to_bf16_f32(h, p, h->xlp, rows);
-  esmp2_status s = virt_bf16(h, h->xlp, h->Fvlp, 5 * No * No, q, h->dflag);
+  if (!p_bf16_ready) to_bf16_f32(h, p, h->xlp, rows);
+  esmp2_status s = virt_bf16_sym(h, h->xlp, h->Fvlp, q, h->dflag);
   if (s) return s;
   couple32(h, h->F32, p, q);
   return check_cuda(h, cudaGetLastError(), "sigma_inner");

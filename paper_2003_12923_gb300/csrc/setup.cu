@@ -438,19 +438,129 @@ esmp2_status setup_top_basis(esmp2_handle *h) {
 
 // Integral transforms (in place on the handle's copies) + f0 + right-hand side.
 // ovov_in / ooov_in / ovvv_in are device copies of the inputs; ovvv_in is consumed.
+namespace {
+// out[o0][o1][o2][o3] = in[...] with input axis ax[k] running along output axis k
+__global__ void k_permute4(const double *in, double *out, int d0, int d1, int d2, int d3, int a0, int a1, int a2,
+                           int a3) {
+  const int d[4] = {d0, d1, d2, d3}, ax[4] = {a0, a1, a2, a3};
+  int64_t st[4];
+  st[3] = 1; st[2] = d3; st[1] = (int64_t)d2 * d3; st[0] = (int64_t)d1 * d2 * d3;
+  const int D0 = d[ax[0]], D1 = d[ax[1]], D2 = d[ax[2]], D3 = d[ax[3]];
+  const int64_t n = (int64_t)D0 * D1 * D2 * D3;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t f = e;
+    const int o3 = (int)(f % D3); f /= D3;
+    const int o2 = (int)(f % D2); f /= D2;
+    const int o1 = (int)(f % D1);
+    const int o0 = (int)(f / D1);
+    out[e] = in[o0 * st[ax[0]] + o1 * st[ax[1]] + o2 * st[ax[2]] + o3 * st[ax[3]]];
+  }
+}
+
+void permute4(esmp2_handle *h, const double *in, double *out, const int d[4], int a0, int a1, int a2, int a3) {
+  k_permute4<<<1216, 256, 0, h->stream>>>(in, out, d[0], d[1], d[2], d[3], a0, a1, a2, a3);
+  h->launches += 1;
+}
+
+// Double-float arithmetic (two floats hi + lo per float64 value): products with their exact
+// fma error, sums by Knuth's two-sum, renormalised after every step; about 2^-46 relative.
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
+  const float ph = ah * bh;
+  const float pe = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
+  const float t = sh + ph;
+  const float bv = t - sh;
+  const float err = (sh - (t - bv)) + (ph - bv);
+  const float lo = sl + err + pe;
+  sh = t + lo;
+  sl = lo - (sh - t);
+}
+__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
+  const float t = sh + bh;
+  const float bv = t - sh;
+  const float err = (sh - (t - bv)) + (bh - bv);
+  const float lo = sl + bl + err;
+  sh = t + lo;
+  sl = lo - (sh - t);
+}
+
+// out[m][n] = sum_k in[m][k] R[k][n] for n < N <= 32 (a tall matrix times a narrow right
+// factor held in shared memory), one warp per row, double-float accumulation.  The
+// contraction of the last OVVV index with the TOP virtuals: No multiply-adds per input
+// element, float64-bound on this part in plain float64.
+constexpr int kXrN = 32;
+__global__ void __launch_bounds__(256) k_xr_df(const double *in, double *out, int64_t M, int K, int N, const double *R,
+                                               int64_t ldR) {
+  extern __shared__ float sR[];           // [K][N + 1] hi, then [K][N + 1] lo
+  const int ldS = N + 1;
+  float *Rh = sR, *Rl = sR + (size_t)K * ldS;
+  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
+    const int k = e / N, n = e % N;
+    const double r = R[(int64_t)k * ldR + n];
+    const float hi = (float)r;
+    Rh[k * ldS + n] = hi;
+    Rl[k * ldS + n] = (float)(r - (double)hi);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t m = w0; m < M; m += nw) {
+    float ah[kXrN], al[kXrN];
+#pragma unroll
+    for (int n = 0; n < kXrN; ++n) { ah[n] = 0.f; al[n] = 0.f; }
+    const double *row = in + m * K;
+    for (int k = lane; k < K; k += 32) {
+      const double v = row[k];
+      const float xh = (float)v, xl = (float)(v - (double)xh);
+#pragma unroll
+      for (int n = 0; n < kXrN; ++n)
+        if (n < N) df_fma(ah[n], al[n], Rh[k * ldS + n], Rl[k * ldS + n], xh, xl);
+    }
+    double mine = 0.0;
+#pragma unroll
+    for (int n = 0; n < kXrN; ++n) {
+      if (n < N) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, ah[n], o), ol = __shfl_xor_sync(0xffffffffu, al[n], o);
+          df_add(ah[n], al[n], oh, ol);
+        }
+        if (lane == n) mine = (double)ah[n] + (double)al[n];
+      }
+    }
+    if (lane < N) out[m * N + lane] = mine;
+  }
+}
+}  // namespace
+
+// The N^5 integral transforms of step a1.  Rotations by the occupied U (No x No) are float64
+// GEMMs; rotations by W_v (Nv x Nv) run as X W_v on the tensor cores from exact digit
+// products (float64 accuracy), after moving the rotated index last.  The contraction of
+// the last OVVV index with the TOP virtuals (Nv -> No columns) stays a float64 GEMM.
 esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, double *ovvv_in, double *scratch) {
   const int No = h->d.No, Nv = h->d.Nv;
   cudaStream_t st = h->stream;
+  const bool tc = (int64_t)9 * Nv * 1024 < (1LL << 24);   // exact ten-level digit sums (one term)
+  esmp2_status s = ESMP2_OK;
   {
     const int dims[4] = {No, Nv, No, Nv};
-    double *src = ovov_in, *dst = scratch;
-    const double *R[4] = {h->U, h->Wv, h->U, h->Wv};
-    const int K[4] = {No, Nv, No, Nv};
-    for (int m = 0; m < 4; ++m) {
-      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
-      double *t = src; src = dst; dst = t;
+    if (tc) {
+      mode_product(ovov_in, scratch, dims, 0, h->U, No, No, st);
+      mode_product(scratch, ovov_in, dims, 2, h->U, No, No, st);
+      if ((s = xwv_split(h, ovov_in, (int64_t)No * Nv * No, scratch))) return s;   // b
+      permute4(h, scratch, ovov_in, dims, 0, 2, 3, 1);                              // [i][j][b][a]
+      if ((s = xwv_split(h, ovov_in, (int64_t)No * No * Nv, scratch))) return s;   // a
+      const int d2[4] = {No, No, Nv, Nv};
+      permute4(h, scratch, h->ovov, d2, 0, 3, 1, 2);                                // [i][a][j][b]
+    } else {
+      double *src = ovov_in, *dst = scratch;
+      const double *R[4] = {h->U, h->Wv, h->U, h->Wv};
+      const int K[4] = {No, Nv, No, Nv};
+      for (int m = 0; m < 4; ++m) {
+        mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+        double *t = src; src = dst; dst = t;
+      }
+      cudaMemcpyAsync(h->ovov, src, sizeof(double) * h->d.B, cudaMemcpyDeviceToDevice, st);
     }
-    cudaMemcpyAsync(h->ovov, src, sizeof(double) * h->d.B, cudaMemcpyDeviceToDevice, st);
   }
   {
     const int dims[4] = {No, No, No, Nv};
@@ -465,16 +575,37 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
   }
   {
     int dims[4] = {No, Nv, Nv, Nv};
-    mode_product(ovvv_in, scratch, dims, 3, h->Wv, No, Nv, st);  // c -> u' (first No columns of Wv)
-    dims[3] = No;
-    double *src = scratch, *dst = ovvv_in;
-    const double *R[3] = {h->U, h->Wv, h->Wv};
-    const int K[3] = {No, Nv, Nv};
-    for (int m = 0; m < 3; ++m) {
-      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
-      double *t = src; src = dst; dst = t;
+    const size_t smem = sizeof(float) * 2 * (size_t)Nv * (No + 1);
+    if (No <= kXrN && smem <= 200 * 1024) {  // c -> u' (first No columns of Wv)
+      static size_t attr = 0;
+      if (smem > attr) {
+        cudaFuncSetAttribute(k_xr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+      }
+      k_xr_df<<<1216, 256, smem, st>>>(ovvv_in, scratch, (int64_t)No * Nv * Nv, Nv, No, h->Wv, Nv);
+      h->launches += 1;
+    } else {
+      mode_product(ovvv_in, scratch, dims, 3, h->Wv, No, Nv, st);
     }
-    cudaMemcpyAsync(h->ovvt, src, sizeof(double) * (size_t)No * Nv * Nv * No, cudaMemcpyDeviceToDevice, st);
+    dims[3] = No;
+    if (tc) {
+      mode_product(scratch, ovvv_in, dims, 0, h->U, No, No, st);                    // [i][a][b][u]
+      permute4(h, ovvv_in, scratch, dims, 0, 3, 1, 2);                             // [i][u][a][b]
+      if ((s = xwv_split(h, scratch, (int64_t)No * No * Nv, ovvv_in))) return s;  // b
+      const int d2[4] = {No, No, Nv, Nv};
+      permute4(h, ovvv_in, scratch, d2, 0, 1, 3, 2);                               // [i][u][b][a]
+      if ((s = xwv_split(h, scratch, (int64_t)No * No * Nv, ovvv_in))) return s;  // a
+      permute4(h, ovvv_in, h->ovvt, d2, 0, 3, 2, 1);                               // [i][a][b][u]
+    } else {
+      double *src = scratch, *dst = ovvv_in;
+      const double *R[3] = {h->U, h->Wv, h->Wv};
+      const int K[3] = {No, Nv, Nv};
+      for (int m = 0; m < 3; ++m) {
+        mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+        double *t = src; src = dst; dst = t;
+      }
+      cudaMemcpyAsync(h->ovvt, src, sizeof(double) * (size_t)No * Nv * Nv * No, cudaMemcpyDeviceToDevice, st);
+    }
   }
   k_f0vo<<<(unsigned)cdiv((int64_t)No * Nv, 256), 256, 0, st>>>(h->F, h->lam, h->ooov, h->ovvt, h->f0vo, No, Nv);
   k_rhs<<<1216, 256, 0, st>>>(h->lam, h->f0vo, h->ovov, h->ooov, h->ovvt, h->b, No, Nv);

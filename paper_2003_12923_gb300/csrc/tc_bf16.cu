@@ -133,7 +133,7 @@ struct Args {
   int nslices;       // slices of this launch
   const int *slices; // global slice index of each launched slice (nullptr: 0 .. nslices-1)
   int per_block;     // slices per amplitude block (No^2); block of slice s = s / per_block
-  int sym;           // 1: slices of T, X, Y take only the term x F (antisymmetric slices)
+  int sym;           // 1: slices of T, X, Y take only the term x F (antisymmetric slices); 2: every slice
   int a_tiles;       // ceil(Nv / 128)
   int b_tiles;       // column tiles per slice
   int bn;            // columns of a full column tile (multiple of 16, <= 256)
@@ -148,6 +148,8 @@ struct Args {
   double *p64;       // [S][Nv][Nv] (one-term slices in mode 1)
   const int *es;     // per-slice binary exponent of the x digits
   int eF, level, first;
+  int mirror;        // mode 0: slices of T, X, Y (i < j listed) also write -y into slice (j, i)
+  int No;
   int *err;          // error flag (device)
 };
 
@@ -156,6 +158,7 @@ __device__ __forceinline__ int slice_of(const Args &g, int64_t li) {
 }
 __device__ __forceinline__ int terms_of(const Args &g, int s) {
   if (!g.sym) return 2;
+  if (g.sym == 2) return 1;                // x F only on every slice (general right factor)
   const int blk = s / g.per_block;
   return (blk == 1 || blk == 4) ? 2 : 1;   // S and Z blocks keep both terms
 }
@@ -281,6 +284,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * BN_MAX);
       if (g.mode == 0) {
         float *dst = g.y32 + off;
+        float *dmr = nullptr;   // mirror slice (j, i) of an antisymmetric block
+        if (g.mirror) {
+          const int blk = s / g.per_block, ij = s % g.per_block;
+          if (blk == 0 || blk == 2 || blk == 3) {
+            const int sm = blk * g.per_block + (ij % g.No) * g.No + ij / g.No;
+            dmr = g.y32 + ((int64_t)sm * g.Nv + a) * g.Nv + b0;
+          }
+        }
         for (int c = 0; c < nvalid; c += 16) {
           float v[16];
           tmem_ld16(taddr + (uint32_t)c, v);
@@ -290,8 +301,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               float4 *d4 = reinterpret_cast<float4 *>(dst + c);
 #pragma unroll
               for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              if (dmr) {
+                float4 *m4 = reinterpret_cast<float4 *>(dmr + c);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  m4[q] = make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]);
+              }
             } else {
               for (int q = 0; q < m; ++q) dst[c + q] = v[q];
+              if (dmr)
+                for (int q = 0; q < m; ++q) dmr[c + q] = -v[q];
             }
           }
         }
@@ -335,17 +354,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // Exact digit split of float64 slices (Ozaki-type splitting): with 2^e the smallest power
-// of two above 2 max |x_s|, z = x / 2^e lies in (-1/2, 1/2) and
-//     z = sum_{p>=1} d_p 64^-p,  d_p integers in [-32, 32]
-// by repeated rounding to the nearest integer; every d_p is exact in bf16 and every product
-// of two digits is an integer of magnitude <= 2^10.
-// Per-slice exponent: one CTA per slice, element (r, c) of slice s at s*sstride + r*ld + c.
-__global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int64_t sstride, int *es) {
+// of two above 2 max |x_s|, z = x / 2^e lies in (-1/2, 1/2); Z = round(z 64^P) is an integer
+// of magnitude <= 2^(6P-1) (exact in int64 for P <= 9), and its balanced base-64 digits
+//     Z = sum_{p=1..P} d_p 64^(P-p),  d_p in [-32, 31] for p >= 2, d_1 in [-32, 32]
+// give z = sum_p d_p 64^-p to within 64^-P / 2.  Every d_p is exact in bf16 and every
+// product of two digits is an integer of magnitude <= 2^10.
+// Per-slice exponent: one CTA per slice, element (r, c) of slice s at s*sstride + r*ld + c*cs.
+__global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int64_t sstride, int *es,
+                            int64_t cs = 1) {
   __shared__ double red[32];
   const double *X = x + blockIdx.x * sstride;
   double m = 0.0;
   for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x)
-    m = fmax(m, fabs(X[(e / cols) * ld + e % cols]));
+    m = fmax(m, fabs(X[(e / cols) * ld + (e % cols) * cs]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -362,21 +383,25 @@ __global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int
   }
 }
 
-// digits: out[p][s][r][c] (row pitch Nvp, pad columns zero), plane = S * rows * Nvp
+// digits: out[p][s][r][c] (row pitch Nvp, pad columns zero), plane = S * rows * Nvp.
+// One CTA iteration per row; one float64 multiply and one conversion per element, the rest
+// is integer arithmetic.
 __global__ void k_digits(const double *x, int S, int rows, int cols, int Nvp, int64_t ld, int64_t sstride,
-                         const int *es, int P, __nv_bfloat16 *out) {
+                         const int *es, int P, __nv_bfloat16 *out, int64_t cs = 1) {
   const int64_t plane = (int64_t)S * rows * Nvp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % Nvp);
-    const int64_t rs = e / Nvp;
-    const int r = (int)(rs % rows);
-    const int s = (int)(rs / rows);
-    double z = c < cols ? ldexp(x[s * sstride + r * ld + c], -es[s]) : 0.0;
-    for (int p = 0; p < P; ++p) {
-      const double t = z * 64.0;
-      const double d = rint(t);
-      z = t - d;                       // exact: d is the integer nearest to t
-      out[p * plane + e] = __float2bfloat16_rn((float)d);
+  for (int64_t row = blockIdx.x; row < (int64_t)S * rows; row += gridDim.x) {
+    const int s = (int)(row / rows), r = (int)(row % rows);
+    const double scale = ldexp(1.0, 6 * P - es[s]);
+    const double *src = x + s * sstride + r * ld;
+    __nv_bfloat16 *dst = out + row * Nvp;
+    for (int c = threadIdx.x; c < Nvp; c += blockDim.x) {
+      long long Z = c < cols ? __double2ll_rn(src[c * cs] * scale) : 0;
+      for (int p = P - 1; p > 0; --p) {   // least significant digit first
+        const long long d = ((Z + 32) & 63) - 32;
+        Z = (Z - d) >> 6;                 // exact: Z - d is a multiple of 64
+        dst[p * plane + c] = __int2bfloat16_rn((int)d);
+      }
+      dst[c] = __int2bfloat16_rn((int)Z);  // leading digit, |Z| <= 32
     }
   }
 }
@@ -482,6 +507,26 @@ tc::Args plain_args(int Nv, int S, float *y, int *err) {
 }
 }  // namespace
 
+// Inner-solve form: only T, X, Y slices with i < j and every S, Z slice are contracted; the
+// slice (j, i) of T, X, Y receives -y_ij (the blocks are antisymmetric under i <-> j).
+esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err) {
+  if (esmp2_status s0 = ensure_slist(h)) return s0;
+  const int No = h->d.No, S = 5 * No * No;
+  tc::Args g = plain_args(h->d.Nv, S, y, err);
+  g.nslices = h->nslist;
+  g.slices = h->slist;
+  g.per_block = No * No;
+  g.No = No;
+  g.mirror = 1;
+  const double nv = h->d.Nv, exec = 4.0 * nv * nv * nv * h->nslist;
+  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g, alg_virtual_flops(No, h->d.Nv), exec)) {
+    h->err = m;
+    return ESMP2_ERR_CUDA;
+  }
+  h->launches += 1;
+  return check_cuda(h, cudaGetLastError(), "virt_bf16_sym");
+}
+
 // y[s][a][b] = sum_c xb[s][a][c] F[c][b] + sum_c F[a][c] xb[s][c][b]  for S slices (fp32 out).
 // xb: bf16 [S][Nv][Nvp], Fb: bf16 [Nv][Nvp], Nvp = Nv rounded up to 8 (16-byte row pitch).
 esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, float *y, int *err) {
@@ -538,26 +583,35 @@ bool split_supported(const esmp2_handle *h, int levels) {
   return 2LL * h->d.Nv * (levels - 1) * 1024 < (1LL << 24);
 }
 
+esmp2_status ensure_slist(esmp2_handle *h) {
+  if (h->slist) return ESMP2_OK;
+  const int No = h->d.No;
+  const int nl = 3 * (No * (No - 1) / 2) + 2 * No * No;
+  cudaError_t e = cudaMalloc(&h->slist, sizeof(int) * (size_t)nl);
+  if (e != cudaSuccess) { h->slist = nullptr; return check_cuda(h, e, "slice list"); }
+  h->nslist = nl;
+  k_split_list<<<(unsigned)cdiv(nl, 256), 256, 0, h->stream>>>(No, h->slist);
+  h->launches += 1;
+  return check_cuda(h, cudaGetLastError(), "slice list");
+}
+
 esmp2_status ensure_split(esmp2_handle *h) {
   if (h->xdig) return ESMP2_OK;
+  if (esmp2_status s0 = ensure_slist(h)) return s0;
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, Nvp = (Nv + 7) & ~7;
   const int S = 5 * No * No, P = kSplitMaxLevels - 1;
-  const int nl = 3 * (No * (No - 1) / 2) + 2 * No * No;
   cudaError_t e = cudaMalloc(&h->xdig, sizeof(__nv_bfloat16) * (size_t)P * S * Nv * Nvp);
   if (e == cudaSuccess) e = cudaMalloc(&h->Fdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp);
-  if (e == cudaSuccess) e = cudaMalloc(&h->es, sizeof(int) * (size_t)(S + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&h->slist, sizeof(int) * (size_t)nl);
+  if (e == cudaSuccess) e = cudaMalloc(&h->es, sizeof(int) * (size_t)(S + 2));  // slices, F_vv, W_v^T
   if (e != cudaSuccess) {
-    cudaFree(h->xdig); cudaFree(h->Fdig); cudaFree(h->es); cudaFree(h->slist);
-    h->xdig = h->Fdig = nullptr; h->es = h->slist = nullptr;
+    cudaFree(h->xdig); cudaFree(h->Fdig); cudaFree(h->es);
+    h->xdig = h->Fdig = nullptr; h->es = nullptr;
     return check_cuda(h, e, "split workspace");
   }
-  h->nslist = nl;
   if (!h->dflag) {
     if ((e = cudaMalloc(&h->dflag, sizeof(int))) != cudaSuccess) return check_cuda(h, e, "split workspace");
     cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
   }
-  k_split_list<<<(unsigned)cdiv(nl, 256), 256, 0, h->stream>>>(No, h->slist);
   // digits of F_vv (the same block in the TOP and the semicanonical-occupied basis); the
   // leading digits do not depend on how many are kept
   const double *Fv = h->F + (int64_t)No * N + No;
@@ -613,6 +667,67 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
     h->launches += 1;
   }
   return check_cuda(h, cudaGetLastError(), "virt_split");
+}
+
+// Y = X W_v (rows x Nv times Nv x Nv, rows a multiple of Nv) in float64 accuracy from exact
+// digit products on the tensor cores (ten levels), the right-factor form of the orbital
+// rotations of the integral transforms.  X is read as rows/Nv slices of Nv x Nv.
+esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y) {
+  esmp2_status s = ensure_split(h);
+  if (s) return s;
+  const int No = h->d.No, Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  const int S = (int)(rows / Nv), P = kSplitMaxLevels - 1, levels = kSplitMaxLevels;
+  if (rows % Nv != 0 || S > 5 * No * No || (int64_t)(levels - 1) * Nv * 1024 >= (1LL << 24)) {
+    h->err = "xwv_split: unsupported shape";
+    return ESMP2_ERR_UNSUPPORTED;
+  }
+  const int64_t NvNv = (int64_t)Nv * Nv;
+  if (!h->Rdig) {  // digits of W_v^T: row b' holds column b' of W_v (the K-major right operand)
+    cudaError_t e = cudaMalloc(&h->Rdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp);
+    if (e != cudaSuccess) return check_cuda(h, e, "rotation digits");
+    int *eR = h->es + 5 * No * No + 1;
+    tc::k_slice_exp<<<1, 256, 0, h->stream>>>(h->Wv, Nv, Nv, 1, 0, eR, Nv);
+    tc::k_digits<<<256, 256, 0, h->stream>>>(h->Wv, 1, Nv, Nv, Nvp, 1, 0, eR, P,
+                                             static_cast<__nv_bfloat16 *>(h->Rdig), Nv);
+    e = cudaMemcpyAsync(&h->eR, eR, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->launches += 2;
+    if (e != cudaSuccess) return check_cuda(h, e, "rotation digits");
+  }
+  tc::k_slice_exp<<<S, 256, 0, h->stream>>>(X, Nv, Nv, Nv, NvNv, h->es);
+  tc::k_digits<<<1216, 256, 0, h->stream>>>(X, S, Nv, Nv, Nvp, Nv, NvNv, h->es, P,
+                                            static_cast<__nv_bfloat16 *>(h->xdig));
+  h->launches += 2;
+  for (int L = 2; L <= levels; ++L) {
+    tc::Args g{};
+    g.Nv = Nv;
+    g.nslices = S;
+    g.slices = nullptr;
+    g.per_block = S;
+    g.sym = 2;
+    g.S_plane = S;
+    g.npairs = 0;
+    for (int p = 1; p < L; ++p) {
+      g.dx[g.npairs] = p - 1;
+      g.df[g.npairs] = L - p - 1;
+      ++g.npairs;
+    }
+    g.mode = 1;
+    g.y64 = nullptr;
+    g.p64 = Y;
+    g.es = h->es;
+    g.eF = h->eR;
+    g.level = L;
+    g.first = (L == 2);
+    g.err = h->dflag;
+    const double fl = 2.0 * g.npairs * (double)rows * Nv * Nv;
+    if (const char *m = launch_virt(h->stream, h->xdig, P, h->Rdig, P, g, fl, fl)) {
+      h->err = m;
+      return ESMP2_ERR_CUDA;
+    }
+    h->launches += 1;
+  }
+  return check_cuda(h, cudaGetLastError(), "xwv_split");
 }
 
 void to_bf16_f64(esmp2_handle *h, const double *src, void *dst, int64_t rows) {
