@@ -1,5 +1,6 @@
 // Internal declarations of the ESMP2 GB300 library (not part of the C ABI).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -89,7 +90,7 @@ struct esmp2_handle {
   esmp2::Couplings cp{};
   esmp2::CouplingsT<float> cp32{};
   float *F32 = nullptr;     // float copy of Fsemi (inner solve)
-  float *dinv32 = nullptr;  // Jacobi preconditioner in that basis (n floats)
+  __half *dinv32 = nullptr; // Jacobi preconditioner in that basis (n halves)
   double *P64 = nullptr;    // x F for the T, S, X, Y blocks (float64 sigma workspace, 4 blocks)
   double *red = nullptr;    // reduction partials
   double *red_out = nullptr;// reduction results (device)

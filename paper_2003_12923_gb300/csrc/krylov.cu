@@ -13,6 +13,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 
@@ -197,13 +198,31 @@ __global__ void kt_p(VCtx c, const double *slots, const T *r, T *p) {
 }
 
 // ---- float inner PCG: block-by-block streaming, float arithmetic, the Jacobi preconditioner
-// read from a float vector (dinv), per-thread float partial sums combined in float64.
+// read from a half-precision vector (a fixed diagonal SPD preconditioner: rounding it only
+// perturbs the preconditioner), per-thread float partial sums combined in float64.  With
+// B a multiple of 4 every block starts on a 16-byte boundary and the streams move four
+// elements per access.  The correction d is advanced in the p update (d += alpha p before p
+// changes), so the residual update reads only r, q and M^-1.
 struct ICtx {
   int64_t B;
-  const float *dinv;
+  const __half *dinv;
   __nv_bfloat16 *pb;  // bf16 copy of p for the tensor-core operand (nullptr: not kept here)
+  int vec;            // B % 4 == 0
 };
 __device__ __forceinline__ float blk_weight(int blk) { return blk == 1 ? 1.f : (blk == 4 ? 2.f : 0.5f); }
+__device__ __forceinline__ float4 ld_h4(const __half *p4) {
+  const uint2 u = *reinterpret_cast<const uint2 *>(p4);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_b4(__nv_bfloat16 *p4, float4 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t *>(&a);
+  u.y = *reinterpret_cast<uint32_t *>(&b);
+  *reinterpret_cast<uint2 *>(p4) = u;
+}
 
 __global__ void ki_init(ICtx c, const double *r64, float *r, float *p, float *d, double *red) {
   float a0 = 0.f, a1 = 0.f;
@@ -212,7 +231,7 @@ __global__ void ki_init(ICtx c, const double *r64, float *r, float *p, float *d,
     const float w = blk_weight(blk);
     float s0 = 0.f, s1 = 0.f;
     for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
-      const float ri = (float)r64[e], z = c.dinv[e] * ri;
+      const float ri = (float)r64[e], z = __half2float(c.dinv[e]) * ri;
       r[e] = ri;
       p[e] = z;
       if (c.pb) c.pb[e] = __float2bfloat16_rn(z);
@@ -232,25 +251,49 @@ __global__ void ki_dot(ICtx c, const float *u, const float *q, double *red) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int blk = 0; blk < 5; ++blk) {
     float s = 0.f;
-    for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) s += u[e] * q[e];
+    if (c.vec) {
+      const int64_t n4 = c.B >> 2;
+      const float4 *u4 = reinterpret_cast<const float4 *>(u + blk * c.B), *q4 = reinterpret_cast<const float4 *>(q + blk * c.B);
+      for (int64_t e = t0; e < n4; e += stride) {
+        const float4 a4 = u4[e], b4 = q4[e];
+        s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
+      }
+    } else {
+      for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) s += u[e] * q[e];
+    }
     a += blk_weight(blk) * s;
   }
   double v[1] = {(double)a};
   block_partials<1>(v, red);
 }
 
-__global__ void ki_update(ICtx c, const double *slots, float *d, float *r, const float *p, const float *q, double *red) {
+// r -= alpha q; partials <r, M^-1 r>, <r, r>
+__global__ void ki_update(ICtx c, const double *slots, float *r, const float *q, double *red) {
   const float alpha = (float)slots[4];
   float a0 = 0.f, a1 = 0.f;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int blk = 0; blk < 5; ++blk) {
     float s0 = 0.f, s1 = 0.f;
-    for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
-      d[e] += alpha * p[e];
-      const float ri = r[e] - alpha * q[e];
-      r[e] = ri;
-      s0 += ri * c.dinv[e] * ri;
-      s1 += ri * ri;
+    if (c.vec) {
+      const int64_t n4 = c.B >> 2;
+      float4 *r4 = reinterpret_cast<float4 *>(r + blk * c.B);
+      const float4 *q4 = reinterpret_cast<const float4 *>(q + blk * c.B);
+      const __half *dv = c.dinv + blk * c.B;
+      for (int64_t e = t0; e < n4; e += stride) {
+        float4 rv = r4[e];
+        const float4 qv = q4[e], m = ld_h4(dv + 4 * e);
+        rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+        r4[e] = rv;
+        s0 += rv.x * m.x * rv.x + rv.y * m.y * rv.y + rv.z * m.z * rv.z + rv.w * m.w * rv.w;
+        s1 += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+      }
+    } else {
+      for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
+        const float ri = r[e] - alpha * q[e];
+        r[e] = ri;
+        s0 += ri * __half2float(c.dinv[e]) * ri;
+        s1 += ri * ri;
+      }
     }
     const float w = blk_weight(blk);
     a0 += w * s0;
@@ -260,19 +303,39 @@ __global__ void ki_update(ICtx c, const double *slots, float *d, float *r, const
   block_partials<2>(v, red);
 }
 
-__global__ void ki_p(ICtx c, const double *slots, const float *r, float *p) {
-  const float beta = (float)slots[5];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
-    const float pn = c.dinv[e] * r[e] + beta * p[e];
-    p[e] = pn;
-    if (c.pb) c.pb[e] = __float2bfloat16_rn(pn);
+// d += alpha p; p = M^-1 r + beta p (and its bf16 copy)
+__global__ void ki_p(ICtx c, const double *slots, const float *r, float *p, float *d) {
+  const float alpha = (float)slots[4], beta = (float)slots[5];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c.vec) {
+    const int64_t n4 = (5 * c.B) >> 2;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+    float4 *p4 = reinterpret_cast<float4 *>(p), *d4 = reinterpret_cast<float4 *>(d);
+    for (int64_t e = t0; e < n4; e += stride) {
+      const float4 pv = p4[e], rv = r4[e], m = ld_h4(c.dinv + 4 * e);
+      float4 dv = d4[e];
+      dv.x += alpha * pv.x; dv.y += alpha * pv.y; dv.z += alpha * pv.z; dv.w += alpha * pv.w;
+      d4[e] = dv;
+      const float4 pn = make_float4(m.x * rv.x + beta * pv.x, m.y * rv.y + beta * pv.y, m.z * rv.z + beta * pv.z,
+                                    m.w * rv.w + beta * pv.w);
+      p4[e] = pn;
+      if (c.pb) st_b4(c.pb + 4 * e, pn);
+    }
+  } else {
+    for (int64_t e = t0; e < 5 * c.B; e += stride) {
+      const float pv = p[e];
+      d[e] += alpha * pv;
+      const float pn = __half2float(c.dinv[e]) * r[e] + beta * pv;
+      p[e] = pn;
+      if (c.pb) c.pb[e] = __float2bfloat16_rn(pn);
+    }
   }
 }
 
-// Jacobi preconditioner as a float vector (computed once per basis, in float64)
-__global__ void k_dinv32(VCtx c, float *dinv) {
+// Jacobi preconditioner as a half vector (computed once per basis, in float64)
+__global__ void k_dinv32(VCtx c, __half *dinv) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
-    dinv[e] = (float)c.dinv(e);
+    dinv[e] = __float2half_rn((float)c.dinv(e));
 }
 
 // r = -b - q (fp64 true residual); partials <r,r>, <b,b>
@@ -611,7 +674,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   antisym_project(h, h->s64.x);
   const VCtx c = vctx(h, h->Fsemi);
   if (!h->dinv32) {
-    cudaError_t e = cudaMalloc(&h->dinv32, sizeof(float) * (size_t)h->d.n);
+    cudaError_t e = cudaMalloc(&h->dinv32, sizeof(__half) * (size_t)h->d.n);
     if (e != cudaSuccess) return check_cuda(h, e, "preconditioner");
     k_dinv32<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->dinv32);
     h->launches += 1;
@@ -623,6 +686,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // writes it directly
   const bool fused_bf16 = (h->d.Nv % 8) == 0;
   ic.pb = fused_bf16 ? static_cast<__nv_bfloat16 *>(h->xlp) : nullptr;
+  ic.vec = (h->d.B % 4) == 0;
   // small instances are launch-bound: replay the inner iteration as a CUDA graph
   bool use_graph = h->d.n <= (64LL << 20) && st != nullptr;
   if (h->inner_graph && !use_graph) {
@@ -676,9 +740,9 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
       if (s2) return s2;
       ki_dot<<<kRedBlocks, kRedThreads, 0, st>>>(ic, p32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
-      ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, d32, r32, p32, q32, h->red);
+      ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
-      ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32);
+      ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32, d32);
       h->launches += 5;
       h->inner_graph_launches_pending = h->launches - l0;
       return check_cuda(h, cudaGetLastError(), "inner step");

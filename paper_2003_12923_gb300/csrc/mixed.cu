@@ -289,7 +289,7 @@ esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps
     cudaEventRecord(ev[0], h->stream);
     to_bf16_f32(h, h->p32, h->xlp, rows);
     cudaEventRecord(ev[1], h->stream);
-    if ((s = virt_bf16(h, h->xlp, h->Fvlp, 5 * No * No, h->q32, h->dflag))) return s;
+    if ((s = virt_bf16_sym(h, h->xlp, h->Fvlp, h->q32, h->dflag))) return s;
     cudaEventRecord(ev[2], h->stream);
     couple32(h, h->F32, h->p32, h->q32);
     cudaEventRecord(ev[3], h->stream);

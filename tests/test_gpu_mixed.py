@@ -80,3 +80,30 @@ def test_solve_mixed_matches_oracle(No, Nv, seed):
     # the plain fp64 solve continues from the mixed solution (basis handled by the library)
     info2 = h.solve(tol=1e-11, maxit=50)
     assert info2["iterations"] <= 2
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(4, 9, 12), (6, 30, 0), (5, 64, 14)])
+def test_solve_mixed_graph_replay_matches_oracle(No, Nv, seed):
+    """On a non-default stream the inner PCG iteration is captured once and replayed as a
+    CUDA graph; the result must not change."""
+    import torch
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        t = {k: torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")}
+        h = esmp2.Handle(t["F"], t["ovov"], t["ooov"], t["ovvv"], t["C"], stream=st)
+        info = h.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
+        e = h.energy()
+        # a second solve from zero on the same handle replays the cached graph
+        h.set_solution(torch.zeros(h.shape, dtype=torch.float64, device="cuda"))
+        info2 = h.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
+        e2 = h.energy()
+    st.synchronize()
+    ref = o2.solve(top.prepare(inst), tol=1e-12)
+    assert info["rel_residual"] <= 1e-11 and info2["rel_residual"] <= 1e-11
+    assert abs(e["E2"] - ref["E2"]) < 1e-10
+    assert abs(e2["E2"] - ref["E2"]) < 1e-10
+    plain = handle_for(inst)
+    info3 = plain.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
+    assert info3["iterations"] == info["iterations"]
