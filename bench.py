@@ -167,6 +167,9 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
 
 
 def run_reference(args):
+    if args.config not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-instance configs"}))
+        return 0
     No, Nv, seed, so = WORKLOADS[args.config]
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -188,13 +191,79 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: 64 uneven instances (No ~ U{8..32}, Nv = round(r No), r ~ U[8,14]),
+    solved through esmp2_batch_solve (mixed precision, `--concurrency` workers, one stream
+    each) from host inputs, in waves of `--wave` instances (the whole batch's OVVV blocks
+    total 230 GB, so inputs are generated wave by wave; generation is not timed).
+    value = instances solved per second of batch_solve wall time.  The float64 comparison
+    times sequential plain-FP64 solves (create + solve + energy, host inputs) on every
+    `--fp64-every`-th instance and scales to the whole batch by No^2 Nv^3."""
+    import torch
+    import synth
+    from paper_2003_12923_gb300 import esmp2
+    rank = int(os.environ.get("RANK", "0"))
+    shapes = synth.batch_shapes(64)
+    t_batch, t_seq64, w_seq64, w_all = 0.0, 0.0, 0.0, 0.0
+    n_done, worst_res, e2_diffs, iters = 0, 0.0, [], []
+    for w0 in range(0, len(shapes), args.wave):
+        wave = shapes[w0:w0 + args.wave]
+        insts = [synth.make_instance(No, Nv, sd, sigma_off=1e-3) for (No, Nv, sd) in wave]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = esmp2.batch_solve(insts, tol=args.tol, maxit=args.maxit, precision=esmp2.MIXED_BF16,
+                                    concurrency=args.concurrency)
+        torch.cuda.synchronize()
+        t_batch += time.perf_counter() - t0
+        if st != esmp2.OK:
+            raise RuntimeError("batch_solve failed: " + "; ".join(r["message"] for r in res if r["status"]))
+        for (No, Nv, sd), inst, r in zip(wave, insts, res):
+            w = No * No * float(Nv) ** 3
+            w_all += w
+            n_done += 1
+            worst_res = max(worst_res, r["rel_residual"])
+            iters.append(r["iterations"])
+            if (w0 + wave.index((No, Nv, sd))) % args.fp64_every == 0:
+                t0 = time.perf_counter()
+                h = esmp2.Handle(*(torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")))
+                h.solve(tol=args.tol, maxit=args.maxit, precision=esmp2.FP64)
+                e64 = h.energy()["E2"]
+                h.close()
+                torch.cuda.synchronize()
+                t_seq64 += time.perf_counter() - t0
+                w_seq64 += w
+                e2_diffs.append(abs(r["E2"] - e64))
+        del insts
+    est64 = t_seq64 * (w_all / w_seq64) if w_seq64 > 0 else None
+    line = {"metric": "ESMP2 batched solves/s, 64 uneven instances (No 8-32, Nv 8-14 x No), res<1e-8, mixed",
+            "value": n_done / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f64", "data": "synthetic",
+            "config": {"workload": "c4: synth.batch_shapes(64) seeds 100-163, sigma_off 1e-3", "tol": args.tol,
+                       "concurrency": args.concurrency, "wave": args.wave,
+                       "step": "esmp2_batch_solve per wave (create from host inputs + solve + energy + destroy)"},
+            "instances": n_done, "batch_seconds": t_batch, "worst_rel_residual": worst_res,
+            "inner_iterations_total": int(sum(iters)),
+            "fp64_sequential": {"seconds_measured": t_seq64, "instances_measured": len(e2_diffs),
+                                "seconds_estimated_all": est64,
+                                "solves_per_s_estimated": (n_done / est64) if est64 else None,
+                                "max_abs_E2_mixed_minus_fp64": max(e2_diffs) if e2_diffs else None,
+                                "scaling": "measured seconds x (sum No^2 Nv^3 over all / over measured)"}}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS) + ["c4"])
+    ap.add_argument("--wave", type=int, default=2, help="c4: instances generated and solved per batch call")
+    ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
+    ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=2000)
@@ -206,6 +275,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "c4":
+        return run_batch(args)
 
     import torch
     import torch.distributed as dist

@@ -173,8 +173,10 @@ esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
  * the status, energies, solve info and launches of instance i.  `concurrency` host
  * workers each drive their own non-blocking CUDA stream on the current device and take
  * instances in order from a shared counter, so small instances overlap; device memory in
- * use is that of `concurrency` instances at a time.  Returns ESMP2_OK if every instance
- * succeeded, else the first failing status (every instance is still attempted). */
+ * use is that of `concurrency` instances at a time.  In the mixed solve of an instance of
+ * at most 64M amplitudes the inner PCG iteration is captured once and replayed as a CUDA
+ * graph.  p: ESMP2_FP64, ESMP2_FP64_TC or ESMP2_MIXED_BF16.  Returns ESMP2_OK if every
+ * instance succeeded, else the first failing status (every instance is still attempted). */
 typedef struct {
   esmp2_status status;
   esmp2_energy_parts e2;

@@ -405,14 +405,12 @@ struct SCtx {
   }
 };
 
-// 1 / D from a float seed and two Newton-Raphson steps (each squares the relative error:
-// 2^-24 -> 2^-48 -> below float64 rounding); D is a sum of orbital energies, far from the
-// float range limits.
+// 1 / D from a float seed and one Newton-Raphson step (it squares the relative error:
+// 2^-24 -> 2^-48, far below what the S-space sum needs); D is a sum of orbital energies,
+// far from the float range limits.
 __device__ __forceinline__ double rcp64(double D) {
-  double r = (double)(1.0f / (float)D);
-  r = fma(r, fma(-D, r, 1.0), r);
-  r = fma(r, fma(-D, r, 1.0), r);
-  return r;
+  const double r = (double)(1.0f / (float)D);
+  return fma(r, fma(-D, r, 1.0), r);
 }
 
 // In every sector the common case holds exactly one TOP pair (u, u'); then b_I is a single
@@ -427,7 +425,7 @@ __global__ void k_e2s_a(SCtx s, double *red) {
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && j < k && j != u && k != u) {
-    const double lu = s.lam[u];
+    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
     for (int c = 1; c < Nv; ++c) {
       if (c == u) continue;
@@ -443,8 +441,8 @@ __global__ void k_e2s_a(SCtx s, double *red) {
           v[0] += s.term(ho, hs, po, ps);
           continue;
         }
-        const double bI = lu * (s.g(k, c, j, b) - s.g(j, c, k, b));
-        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(b));
+        const double dg = s.g(k, c, j, b) - s.g(j, c, k, b);
+        v[0] += c2 * dg * dg * rcp64(Dc + s.Fv(b));
       }
     }
   }
@@ -458,7 +456,7 @@ __global__ void k_e2s_b(SCtx s, double *red) {
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && j < k) {
-    const double lu = s.lam[u];
+    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
     for (int c = 1; c < Nv; ++c) {
       const double Dc = Dh + s.Fv(c);
@@ -470,8 +468,8 @@ __global__ void k_e2s_b(SCtx s, double *red) {
           v[0] += s.term(ho, hs, po, ps);
           continue;
         }
-        const double bI = lu * (s.g(k, c, j, b) - s.g(j, c, k, b));
-        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(b));
+        const double dg = s.g(k, c, j, b) - s.g(j, c, k, b);
+        v[0] += c2 * dg * dg * rcp64(Dc + s.Fv(b));
       }
     }
   }
@@ -486,7 +484,7 @@ __global__ void k_e2s_c(SCtx s, double *red) {
   const int u = (int)(blk / ((int64_t)No * No)), i = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
   if (u >= 1 && k != u) {
-    const double lu = s.lam[u];
+    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
     const double Dh = s.Fv(u) - s.Fo(i) - s.Fo(u) - s.Fo(k) - s.omega;
     for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
       if (c == u) continue;
@@ -502,8 +500,8 @@ __global__ void k_e2s_c(SCtx s, double *red) {
       const double Dc = Dh + s.Fv(c);
       for (int a = 0; a < Nv; ++a) {
         if (a == i) continue;
-        const double bI = lu * s.g(i, a, k, c);
-        v[0] -= 2.0 * bI * bI * rcp64(Dc + s.Fv(a));
+        const double g = s.g(i, a, k, c);
+        v[0] += c2 * g * g * rcp64(Dc + s.Fv(a));
       }
     }
   }

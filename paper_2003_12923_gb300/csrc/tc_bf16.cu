@@ -10,10 +10,11 @@
 // so each output element is written once.  Operands are bf16 (rounded copies of x and F),
 // accumulation fp32.
 //
-// Structure (persistent, one CTA per SM, 192 threads):
-//   warp 0      TMA producer: 3-D / 2-D tiled bulk copies, 128-byte swizzle, 2-stage ring
+// Structure (persistent, one CTA per SM, 320 threads):
+//   warp 0      TMA producer: 3-D tiled bulk copies, 128-byte swizzle, 2-stage ring
 //   warp 1      tcgen05.mma issuer (one elected thread), commits to mbarriers
-//   warps 2..5  epilogue: tcgen05.ld 32x32b from the accumulator, fp32 stores
+//   warps 2..9  epilogue: tcgen05.ld 32x32b from the accumulator (two warps per lane
+//               quarter, each half of the columns), fp32 stores or float64 accumulation
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of tile k overlap the main
 // loop of tile k+1.  Every mbarrier wait is bounded by a globaltimer limit; a wait that
 // runs out sets an error flag, skips the remaining work and the CTA still waits (bounded)
@@ -25,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -34,12 +36,12 @@ namespace tc {
 constexpr int BM = 128;           // accumulator rows (TMEM lanes)
 constexpr int BN_MAX = 256;       // accumulator columns per tile
 constexpr int BK = 64;            // K elements per stage (128 bytes of bf16)
-constexpr int STAGES = 2;
+constexpr int STAGES = 4;          // ring slots; a slot holds the operands of one term
 constexpr int A_BYTES = BM * BK * 2;          // 16 KB
 constexpr int B_BYTES = BN_MAX * BK * 2;      // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;     // producer warp, MMA warp, 8 epilogue warps
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -133,7 +135,8 @@ struct Args {
   int nslices;       // slices of this launch
   const int *slices; // global slice index of each launched slice (nullptr: 0 .. nslices-1)
   int per_block;     // slices per amplitude block (No^2); block of slice s = s / per_block
-  int sym;           // 1: slices of T, X, Y take only the term x F (antisymmetric slices); 2: every slice
+  int tm[5];         // per block: 1 = x F only, 2 = x F + F x, 3 = F x only
+  int to_p64[5];     // mode 1, per block: 1 = write p64, 0 = write y64
   int a_tiles;       // ceil(Nv / 128)
   int b_tiles;       // column tiles per slice
   int bn;            // columns of a full column tile (multiple of 16, <= 256)
@@ -156,12 +159,7 @@ struct Args {
 __device__ __forceinline__ int slice_of(const Args &g, int64_t li) {
   return g.slices ? g.slices[li] : (int)li;
 }
-__device__ __forceinline__ int terms_of(const Args &g, int s) {
-  if (!g.sym) return 2;
-  if (g.sym == 2) return 1;                // x F only on every slice (general right factor)
-  const int blk = s / g.per_block;
-  return (blk == 1 || blk == 4) ? 2 : 1;   // S and Z blocks keep both terms
-}
+__device__ __forceinline__ int terms_of(const Args &g, int s) { return g.tm[s / g.per_block]; }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_virt(const __grid_constant__ CUtensorMap tXa, const __grid_constant__ CUtensorMap tXb,
@@ -174,7 +172,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int s = 0; s < 2; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], 4); }
+    for (int s = 0; s < 2; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], 8); }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -194,29 +192,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {  // ------------------------------------------------ TMA producer
       int64_t it = 0;
       bool ok = true;
-      const uint32_t bytes2 = (uint32_t)(2 * A_BYTES + g.bn * BK * 2 + (BN_MAX / 64) * 64 * BK * 2);
-      const uint32_t bytes1 = (uint32_t)(A_BYTES + g.bn * BK * 2);
+      const uint32_t bytesXF = (uint32_t)(A_BYTES + g.bn * BK * 2);
+      const uint32_t bytesFX = (uint32_t)(A_BYTES + (BN_MAX / 64) * 64 * BK * 2);
       for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
         const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
         const int terms = terms_of(g, s);
         const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
         for (int pr = 0; pr < g.npairs && ok; ++pr) {
           const int zx = g.dx[pr] * g.S_plane + s, zf = g.df[pr];
-          for (int kc = 0; kc < g.nk; ++kc, ++it) {
-            const int st = (int)(it % STAGES);
-            const uint32_t rnd = (uint32_t)(it / STAGES);
-            if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) { ok = false; break; }
-            uint8_t *base = smem + st * STAGE_BYTES;
-            uint8_t *A2 = base, *A1 = base + A_BYTES, *B2 = base + 2 * A_BYTES, *B1 = B2 + B_BYTES;
-            // boxes: A2 (128 x 64), B2 (bn x 64); two-term slices also A1 (128 x 64), B1 (4 x 64 x 64)
-            mbar_expect_tx(&full[st], terms == 2 ? bytes2 : bytes1);
+          for (int kc = 0; kc < g.nk && ok; ++kc) {
             const int c0 = kc * BK;
-            tma_3d(A2, &tXa, &full[st], c0, a0, zx);
-            tma_3d(B2, &tFb, &full[st], c0, b0, zf);
-            if (terms == 2) {
-              tma_3d(A1, &tFa, &full[st], c0, a0, zf);
+            for (int term = 1; term <= 2; ++term, ++it) {   // 1: x F, 2: F x
+              if ((term == 1 && terms == 3) || (term == 2 && terms == 1)) { --it; continue; }
+              const int st = (int)(it % STAGES);
+              const uint32_t rnd = (uint32_t)(it / STAGES);
+              if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) { ok = false; break; }
+              uint8_t *A = smem + st * STAGE_BYTES, *B = A + A_BYTES;
+              if (term == 1) {   // A = X_s rows (128 x 64), B = F rows b (bn x 64), both K-major
+                mbar_expect_tx(&full[st], bytesXF);
+                tma_3d(A, &tXa, &full[st], c0, a0, zx);
+                tma_3d(B, &tFb, &full[st], c0, b0, zf);
+              } else {           // A = F rows a (128 x 64), B = X_s[c][b] (4 boxes of 64 x 64, MN-major)
+                mbar_expect_tx(&full[st], bytesFX);
+                tma_3d(A, &tFa, &full[st], c0, a0, zf);
 #pragma unroll
-              for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B1 + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, zx);
+                for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, zx);
+              }
             }
           }
         }
@@ -243,22 +244,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&acc_empty[ab], (ar & 1) ^ 1)) { ok = false; break; }
         tc_after();
         const uint32_t d = tmem + (uint32_t)(ab * BN_MAX);
+        bool first = true;
         for (int pr = 0; pr < g.npairs && ok; ++pr) {
-          for (int kc = 0; kc < g.nk; ++kc, ++it) {
-            const int st = (int)(it % STAGES);
-            const uint32_t rnd = (uint32_t)(it / STAGES);
-            if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
-            tc_after();
-            const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t A2 = base, A1 = base + A_BYTES, B2 = base + 2 * A_BYTES, B1 = B2 + B_BYTES;
+          for (int kc = 0; kc < g.nk && ok; ++kc) {
             const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);
-            for (int k = 0; k < ksteps; ++k)   // X_s[a][c] F[c][b]
-              umma(d, sdesc(A2 + 32 * k, 16, 1024), sdesc(B2 + 32 * k, 16, 1024), id2,
-                   (pr > 0 || kc > 0 || k > 0) ? 1u : 0u);
-            if (terms == 2)
-              for (int k = 0; k < ksteps; ++k)   // F[a][c] X_s[c][b]
-                umma(d, sdesc(A1 + 32 * k, 16, 1024), sdesc(B1 + 2048 * k, BK * 128, 1024), id1, 1u);
-            umma_commit(&empty[st]);
+            for (int term = 1; term <= 2; ++term, ++it) {
+              if ((term == 1 && terms == 3) || (term == 2 && terms == 1)) { --it; continue; }
+              const int st = (int)(it % STAGES);
+              const uint32_t rnd = (uint32_t)(it / STAGES);
+              if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
+              tc_after();
+              const uint32_t A = smem_u32(smem + st * STAGE_BYTES), B = A + A_BYTES;
+              for (int k = 0; k < ksteps; ++k) {
+                if (term == 1)   // X_s[a][c] F[c][b]
+                  umma(d, sdesc(A + 32 * k, 16, 1024), sdesc(B + 32 * k, 16, 1024), id2, first ? 0u : 1u);
+                else             // F[a][c] X_s[c][b]
+                  umma(d, sdesc(A + 32 * k, 16, 1024), sdesc(B + 2048 * k, BK * 128, 1024), id1, first ? 0u : 1u);
+                first = false;
+              }
+              umma_commit(&empty[st]);
+            }
           }
         }
         if (!ok) break;
@@ -267,7 +272,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!ok) atomicExch(&fail, 1);
     }
   } else {  // ---------------------------------------------------------- epilogue
-    const int quarter = warp & 3;
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (the tcgen05.ld lane rule); the two warps of
+    // a lane quarter split the tile's columns
+    const int quarter = warp & 3, chalf = (warp - 2) >> 2;
     int lt = 0;
     for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x, ++lt) {
       const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
@@ -282,6 +289,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int a = a0 + row;
       const int64_t off = ((int64_t)s * g.Nv + a) * g.Nv + b0;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * BN_MAX);
+      const int hc = ((nvalid + 31) / 32) * 16;   // columns per half, a multiple of 16
+      const int c_begin = chalf * hc, c_end = min(nvalid, c_begin + hc);
       if (g.mode == 0) {
         float *dst = g.y32 + off;
         float *dmr = nullptr;   // mirror slice (j, i) of an antisymmetric block
@@ -292,11 +301,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             dmr = g.y32 + ((int64_t)sm * g.Nv + a) * g.Nv + b0;
           }
         }
-        for (int c = 0; c < nvalid; c += 16) {
+        for (int c = c_begin; c < c_end; c += 16) {
           float v[16];
           tmem_ld16(taddr + (uint32_t)c, v);
           if (a < g.Nv) {
             const int m = min(16, nvalid - c);
+            if (!g.first)
+              for (int q = 0; q < m; ++q) v[q] += dst[c + q];   // second pass of a split slice
             if (m == 16 && (g.Nv & 3) == 0) {
               float4 *d4 = reinterpret_cast<float4 *>(dst + c);
 #pragma unroll
@@ -317,9 +328,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       } else {
         // every accumulator value is an integer below 2^24 (exact in fp32); the float64
         // sum over levels is the only rounding step
-        double *dst = (terms_of(g, s) == 2 ? g.y64 : g.p64) + off;
+        double *dst = (g.to_p64[s / g.per_block] ? g.p64 : g.y64) + off;
         const double scale = ldexp(1.0, g.es[s] + g.eF - 6 * g.level);
-        for (int c = 0; c < nvalid; c += 16) {
+        for (int c = c_begin; c < c_end; c += 16) {
           float v[16];
           tmem_ld16(taddr + (uint32_t)c, v);
           if (a < g.Nv) {
@@ -497,7 +508,8 @@ tc::Args plain_args(int Nv, int S, float *y, int *err) {
   g.nslices = S;
   g.slices = nullptr;
   g.per_block = S;
-  g.sym = 0;
+  for (int b = 0; b < 5; ++b) g.tm[b] = 2;
+  g.first = 1;
   g.npairs = 1;
   g.S_plane = S;
   g.mode = 0;
@@ -507,23 +519,53 @@ tc::Args plain_args(int Nv, int S, float *y, int *err) {
 }
 }  // namespace
 
+// Two-term slices can run as two one-term passes (x F, then F x accumulated), which halves
+// the operand tiles per stage but doubles the stages and the epilogue passes; measured
+// slower on GB300 (No=30 Nv=400: inner contraction 4.2 ms vs 2.0 ms fused), so both terms
+// share one pass unless ESMP2_SPLIT_TERMS=1 (tuning knob).
+static bool split_terms() {
+  static const int v = [] {
+    const char *e = std::getenv("ESMP2_SPLIT_TERMS");
+    return (e && std::atoi(e) == 1) ? 1 : 0;
+  }();
+  return v != 0;
+}
+
 // Inner-solve form: only T, X, Y slices with i < j and every S, Z slice are contracted; the
 // slice (j, i) of T, X, Y receives -y_ij (the blocks are antisymmetric under i <-> j).
 esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err) {
   if (esmp2_status s0 = ensure_slist(h)) return s0;
-  const int No = h->d.No, S = 5 * No * No;
+  const int No = h->d.No, S = 5 * No * No, half = No * (No - 1) / 2;
+  const double nv = h->d.Nv, nv3 = nv * nv * nv;
   tc::Args g = plain_args(h->d.Nv, S, y, err);
   g.nslices = h->nslist;
   g.slices = h->slist;
   g.per_block = No * No;
   g.No = No;
   g.mirror = 1;
-  const double nv = h->d.Nv, exec = 4.0 * nv * nv * nv * h->nslist;
-  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g, alg_virtual_flops(No, h->d.Nv), exec)) {
+  const bool split = split_terms();
+  if (split) { g.tm[1] = 1; g.tm[4] = 1; }   // S, Z: x F here, F x in the second pass
+  const double exec1 = 4.0 * nv3 * 3 * half + (split ? 2.0 : 4.0) * nv3 * 2 * No * No;
+  if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g, alg_virtual_flops(No, h->d.Nv), exec1)) {
     h->err = m;
     return ESMP2_ERR_CUDA;
   }
   h->launches += 1;
+  if (split) {
+    tc::Args g2 = plain_args(h->d.Nv, S, y, err);
+    g2.nslices = 2 * No * No;
+    g2.slices = h->slist + 3 * half;   // the S and Z slices
+    g2.per_block = No * No;
+    g2.No = No;
+    for (int b = 0; b < 5; ++b) g2.tm[b] = 3;
+    g2.first = 0;
+    const double exec2 = 2.0 * nv3 * 2 * No * No;
+    if (const char *m = launch_virt(h->stream, xb, 1, Fb, 1, g2, 0.0, exec2)) {
+      h->err = m;
+      return ESMP2_ERR_CUDA;
+    }
+    h->launches += 1;
+  }
   return check_cuda(h, cudaGetLastError(), "virt_bf16_sym");
 }
 
@@ -635,13 +677,20 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
   tc::k_digits<<<1216, 256, 0, h->stream>>>(x, S, Nv, Nv, Nvp, Nv, NvNv, h->es, levels - 1,
                                             static_cast<__nv_bfloat16 *>(h->xdig));
   h->launches += 2;
+  const bool split = sym && split_terms();
+  const int half = No * (No - 1) / 2;
   for (int L = 2; L <= levels; ++L) {
+   for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
     tc::Args g{};
     g.Nv = Nv;
-    g.nslices = sym ? h->nslist : S;
-    g.slices = sym ? h->slist : nullptr;
+    g.nslices = sym ? (pass == 0 ? h->nslist : 2 * No * No) : S;
+    g.slices = sym ? (pass == 0 ? h->slist : h->slist + 3 * half) : nullptr;
     g.per_block = No * No;
-    g.sym = sym;
+    for (int b = 0; b < 5; ++b) {
+      const bool txy = (b == 0 || b == 2 || b == 3);
+      g.tm[b] = !sym ? 2 : (pass == 1 ? 3 : (txy || split ? 1 : 2));
+      g.to_p64[b] = sym && txy;
+    }
     g.S_plane = S;
     g.npairs = 0;
     for (int p = 1; p < L; ++p) {
@@ -655,16 +704,21 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
     g.es = h->es;
     g.eF = h->eF;
     g.level = L;
-    g.first = (L == 2);
+    g.first = (L == 2 && pass == 0);
     g.err = h->dflag;
     const double nv3 = (double)Nv * Nv * Nv;
-    const double per_pair = sym ? 3.0 * (No * (No - 1) / 2) * 2.0 * nv3 + 2.0 * No * No * 4.0 * nv3 : 4.0 * nv3 * S;
-    const double alg_pair = sym ? alg_virtual_flops(No, Nv) : per_pair;
+    double per_pair = 4.0 * nv3 * S, alg_pair = per_pair;
+    if (sym) {
+      if (!split) per_pair = 3.0 * half * 2.0 * nv3 + 2.0 * No * No * 4.0 * nv3;
+      else per_pair = pass == 0 ? (3.0 * half + 2.0 * No * No) * 2.0 * nv3 : 2.0 * No * No * 2.0 * nv3;
+      alg_pair = pass == 0 ? alg_virtual_flops(No, Nv) : 0.0;
+    }
     if (const char *m = launch_virt(h->stream, h->xdig, P, h->Fdig, P, g, g.npairs * alg_pair, g.npairs * per_pair)) {
       h->err = m;
       return ESMP2_ERR_CUDA;
     }
     h->launches += 1;
+   }
   }
   return check_cuda(h, cudaGetLastError(), "virt_split");
 }
@@ -704,7 +758,7 @@ esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y
     g.nslices = S;
     g.slices = nullptr;
     g.per_block = S;
-    g.sym = 2;
+    for (int b = 0; b < 5; ++b) { g.tm[b] = 1; g.to_p64[b] = 1; }
     g.S_plane = S;
     g.npairs = 0;
     for (int p = 1; p < L; ++p) {
