@@ -16,8 +16,8 @@ using namespace esmp2;
 namespace {
 
 template <typename T>
-cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+cudaError_t dalloc(T **p, size_t count, cudaStream_t st) {
+  return dmalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1), st);
 }
 
 bool finite_host(const double *p, size_t n) {
@@ -34,7 +34,8 @@ void free_handle(esmp2_handle *h) {
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
                   h->xdig, h->Fdig, h->es, h->slist, h->Rdig};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) dfree(p, h->stream);
+  cudaStreamSynchronize(h->stream);
   if (h->inner_graph) cudaGraphExecDestroy(h->inner_graph);
   if (h->hred) cudaFreeHost(h->hred);
 }
@@ -63,6 +64,7 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   if (!h) return ESMP2_ERR_OOM;
   *out = h;
   h->stream = stream;
+  debug_phase(h, "create: begin");
   const int No = d->No, Nv = d->Nv;
   if (No < 1 || No > 64 || Nv < No || Nv > 4096) {
     h->err = "require 1 <= No <= 64 and No <= Nv <= 4096";
@@ -87,7 +89,7 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
         }
   }
   cudaError_t ce = cudaSuccess;
-#define ALLOC(ptr, cnt) if ((ce = dalloc(&(ptr), (cnt))) != cudaSuccess) { esmp2_status s = check_cuda(h, ce, "alloc " #ptr); return s; }
+#define ALLOC(ptr, cnt) if ((ce = dalloc(&(ptr), (cnt), h->stream)) != cudaSuccess) { esmp2_status s = check_cuda(h, ce, "alloc " #ptr); return s; }
   ALLOC(h->C, nC); ALLOC(h->U, (size_t)No * No); ALLOC(h->lam, (size_t)No); ALLOC(h->Wv, (size_t)Nv * Nv);
   ALLOC(h->W, nF); ALLOC(h->F, nF); ALLOC(h->f0vo, nC); ALLOC(h->scal, (size_t)8);
   ALLOC(h->ovov, nOVOV); ALLOC(h->ooov, nOOOV); ALLOC(h->ovvt, nOVVT);
@@ -104,13 +106,15 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   ALLOC(h->red_out, (size_t)32);
   if ((ce = cudaMallocHost(reinterpret_cast<void **>(&h->hred), sizeof(double) * 32)) != cudaSuccess)
     return check_cuda(h, ce, "pinned alloc");
+  debug_phase(h, "create: allocations");
   // inputs -> device
   const cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   double *ovov_in = nullptr, *ooov_in = nullptr, *ovvv_in = nullptr, *scratch = nullptr;
   const size_t nscr = std::max(nOVOV, std::max(nOOOV, nOVVT));
-  if ((ce = dalloc(&ovov_in, nOVOV)) != cudaSuccess || (ce = dalloc(&ooov_in, nOOOV)) != cudaSuccess ||
-      (ce = dalloc(&ovvv_in, std::max(nOVVV, nOVVT))) != cudaSuccess || (ce = dalloc(&scratch, nscr)) != cudaSuccess) {
-    cudaFree(ovov_in); cudaFree(ooov_in); cudaFree(ovvv_in); cudaFree(scratch);
+  if ((ce = dalloc(&ovov_in, nOVOV, h->stream)) != cudaSuccess || (ce = dalloc(&ooov_in, nOOOV, h->stream)) != cudaSuccess ||
+      (ce = dalloc(&ovvv_in, std::max(nOVVV, nOVVT), h->stream)) != cudaSuccess ||
+      (ce = dalloc(&scratch, nscr, h->stream)) != cudaSuccess) {
+    dfree(ovov_in, h->stream); dfree(ooov_in, h->stream); dfree(ovvv_in, h->stream); dfree(scratch, h->stream);
     return check_cuda(h, ce, "input staging");
   }
   cudaMemcpyAsync(h->F, d->F, sizeof(double) * nF, kind, h->stream);
@@ -120,13 +124,16 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
   ce = cudaGetLastError();
   esmp2_status s = check_cuda(h, ce, "input copy");
+  debug_phase(h, "create: input copies");
   if (!s) s = setup_top_basis(h);
+  debug_phase(h, "create: TOP basis");
   if (!s) s = setup_rhs_from(h, ovov_in, ooov_in, ovvv_in, scratch);
+  debug_phase(h, "create: transforms + rhs");
   if (!s) {
     cudaMemsetAsync(h->s64.x, 0, sizeof(double) * h->d.n, h->stream);
     s = check_cuda(h, cudaStreamSynchronize(h->stream), "create");
   }
-  cudaFree(ovov_in); cudaFree(ooov_in); cudaFree(ovvv_in); cudaFree(scratch);
+  dfree(ovov_in, h->stream); dfree(ooov_in, h->stream); dfree(ovvv_in, h->stream); dfree(scratch, h->stream);
   if (!s && !std::isfinite(h->omega)) { h->err = "non-finite Fock matrix in the TOP basis"; s = ESMP2_ERR_INVALID_ARG; }
   return s;
 #undef ALLOC
@@ -229,6 +236,7 @@ esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
   cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
   h->x_semi = 0;
   h->x_zero = false;
+  h->r_true = false;
   return check_cuda(h, cudaGetLastError(), "set_solution");
 }
 

@@ -402,6 +402,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
     cudaMemcpyAsync(xs, h->s64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(h->s64.x, 0, sizeof(double) * n, st);
     h->x_zero = true;
+    h->r_true = false;
     esmp2_solve_info info{};
     esmp2_status s = solve64(h, 1e-12, 5000, &info);
     if (s != ESMP2_OK && s != ESMP2_ERR_NOT_CONVERGED) { cudaFree(xs); return s; }
@@ -414,6 +415,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
     if (adj_diff) *adj_diff = xx > 0 ? std::sqrt(dd / xx) : 0.0;
     cudaMemcpyAsync(h->s64.x, xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     h->x_zero = false;
+    h->r_true = false;
     cudaStreamSynchronize(st);
     cudaFree(xs);
   }

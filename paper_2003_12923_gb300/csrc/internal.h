@@ -111,6 +111,7 @@ struct esmp2_handle {
   double *bsemi = nullptr;  // right-hand side in that basis (n)
   int x_semi = 0;           // 1: s64.x is stored in that basis
   bool x_zero = true;       // s64.x is known to be zero (its sigma is zero, no build needed)
+  bool r_true = false;      // s64.r holds the true residual -b - A x of s64.x (same basis)
   // float64-accurate virtual-index terms from exact bf16 digit products (tcgen05)
   void *xdig = nullptr;     // digit planes of x [levels-1][5 No^2][Nv][Nvp] bf16
   void *Fdig = nullptr;     // digit planes of F_vv [levels-1][Nv][Nvp] bf16
@@ -155,8 +156,21 @@ esmp2_status ensure_slist(esmp2_handle *h);
 esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64, int sym, int levels);
 esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y);
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
+void mode_product_small(const double *in, double *out, int64_t P, int K, int64_t Q, const double *R,
+                        cudaStream_t st);
 void eigvecs_block(esmp2_handle *h, const double *F, int off, int m, double *V, double *work);
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device memory owned by handles: stream-ordered allocations from the device's default
+// memory pool, which keeps up to a third of the device memory cached after frees, so a
+// handle created after another one reuses its memory without a synchronising
+// cudaMalloc/cudaFree pair.  dfree releases in stream order (after the stream's work).
+cudaError_t dmalloc(void **p, size_t bytes, cudaStream_t st);
+void dfree(void *p, cudaStream_t st);
+
+// ESMP2_DEBUG=1: synchronise the handle's stream and print the host time since the last
+// phase mark (set-up breakdowns; no effect otherwise).
+void debug_phase(esmp2_handle *h, const char *name);
 
 // Process-wide kernel timing (esmp2_kernel_timing): a scope records one event pair around
 // the launches it encloses when timing is on.

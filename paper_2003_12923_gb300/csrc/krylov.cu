@@ -332,10 +332,30 @@ __global__ void ki_p(ICtx c, const double *slots, const float *r, float *p, floa
   }
 }
 
-// Jacobi preconditioner as a half vector (computed once per basis, in float64)
+// Jacobi preconditioner as a half vector (once per basis): one CTA iteration per row
+// (blk, i, j, a), float arithmetic (the value is stored in half precision anyway)
 __global__ void k_dinv32(VCtx c, __half *dinv) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
-    dinv[e] = __float2half_rn((float)c.dinv(e));
+  const int No = c.No, Nv = c.Nv, N = c.N;
+  const int64_t rows = 5LL * No * No * Nv;
+  const float shift = (float)(c.F[(int64_t)No * N + No] - c.F[0]), om = (float)c.omega;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    int64_t f = row;
+    const int a = (int)(f % Nv); f /= Nv;
+    const int j = (int)(f % No); f /= No;
+    const int i = (int)(f % No);
+    const int blk = (int)(f / No);
+    const float base = (float)c.F[(int64_t)(No + a) * N + No + a] - (float)c.F[(int64_t)i * N + i] -
+                       (float)c.F[(int64_t)j * N + j] - om + (blk >= BX ? shift : 0.f);
+    __half *out = dinv + row * Nv;
+    for (int b = threadIdx.x; b < Nv; b += blockDim.x) {
+      bool zero = false;
+      if ((blk == BT || blk == BX || blk == BY) && (i == j || a == b)) zero = true;
+      if (blk == BX && (i == 0 || j == 0 || a == 0 || b == 0)) zero = true;
+      if (blk == BZ && (j == 0 || b == 0 || (i == 0 && a == 0))) zero = true;
+      const float d = base + (float)c.F[(int64_t)(No + b) * N + No + b];
+      out[b] = __float2half_rn(zero ? 0.f : 1.f / d);
+    }
+  }
 }
 
 // r = -b - q (fp64 true residual); partials <r,r>, <b,b>
@@ -356,14 +376,16 @@ __global__ void kt_accumulate(VCtx c, double *x, const T *d) {
     x[e] += (double)d[e];
 }
 
-// per-block <b,x> and <x,Ax> for the Hylleraas functional (10 partial sums)
-__global__ void k_hylleraas(VCtx c, const double *b, const double *x, const double *q, double *red) {
+// per-block <b,x> and <x,Ax> for the Hylleraas functional (10 partial sums); q = A x, or
+// from_r: q = -b - r with r the true residual of the current x
+__global__ void k_hylleraas(VCtx c, const double *b, const double *x, const double *q, int from_r, double *red) {
   double v[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) v[k] = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
     const int blk = (int)(e / c.B);
-    const double xb = x[e] * b[e], xq = x[e] * q[e];
+    const double qe = from_r ? -b[e] - q[e] : q[e];
+    const double xb = x[e] * b[e], xq = x[e] * qe;
 #pragma unroll
     for (int k = 0; k < 5; ++k)
       if (k == blk) { v[2 * k] += xb; v[2 * k + 1] += xq; }
@@ -545,6 +567,7 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
   double *x = h->s64.x, *r = h->s64.r, *p = h->s64.p, *q = h->s64.q;
   cudaStream_t st = h->stream;
   h->last_precision = virt_tc ? ESMP2_FP64_TC : ESMP2_FP64;
+  h->r_true = false;
   const int lv = virt_tc ? kFp64TcLevels : 0;
   antisym_project(h, x);
   esmp2_status s = ESMP2_OK;
@@ -567,7 +590,7 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
   int it = 0;
   esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
   double relres = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
-  if (bnorm == 0.0) result = ESMP2_OK;
+  if (bnorm == 0.0) { result = ESMP2_OK; h->r_true = true; }
   while (result != ESMP2_OK && it < maxit) {
     if (std::sqrt(rr) <= tol * bnorm) {  // confirm with the true residual
       if ((s = sigma64(h, x, q, lv))) return s;
@@ -579,7 +602,7 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
       if ((s = read_slots(h, sl, 32))) return s;
       rr = sl[1];
       relres = std::sqrt(rr) / bnorm;
-      if (relres <= tol) { result = ESMP2_OK; break; }
+      if (relres <= tol) { result = ESMP2_OK; h->r_true = true; break; }
     }
     if ((s = sigma64(h, p, q, lv))) return s;
     if (virt_tc && (s = check_device_flag(h))) return s;
@@ -615,11 +638,16 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   cudaStream_t st = h->stream;
   const double *F = h->x_semi ? h->Fsemi : h->F;
   const double *bb = h->x_semi ? h->bsemi : h->b;
-  // after a tensor-core solve the Hylleraas sigma uses the float64-exact digit levels
-  const int lv = (h->last_precision != ESMP2_FP64 && split_supported(h, kFp64TcLevels)) ? kFp64TcLevels : 0;
-  esmp2_status s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q, lv);
-  if (s) return s;
-  k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.q, h->red);
+  esmp2_status s = ESMP2_OK;
+  if (h->r_true) {
+    // the solve ended on a true residual r = -b - A x of this x: A x = -b - r, no sigma build
+    k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.r, 1, h->red);
+  } else {
+    // after a tensor-core solve the Hylleraas sigma uses the float64-exact digit levels
+    const int lv = (h->last_precision != ESMP2_FP64 && split_supported(h, kFp64TcLevels)) ? kFp64TcLevels : 0;
+    if ((s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q, lv))) return s;
+    k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.q, 0, h->red);
+  }
   k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 10, h->red_out, 3);
   h->launches += 2;
   double sl[32];
@@ -662,8 +690,10 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
 // (the solution is rotated back to the TOP basis on request).
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
   auto t0 = std::chrono::steady_clock::now();
+  debug_phase(h, "solve: start");
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
+  debug_phase(h, "solve: semicanonical set-up");
   if (!h->x_semi) {
     if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);  // zero in every basis
     h->x_semi = 1;
@@ -671,12 +701,14 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   cudaStream_t st = h->stream;
   antisym_project(h, h->s64.x);
   const VCtx c = vctx(h, h->Fsemi);
+  debug_phase(h, "solve: x rotation + projection");
   if (!h->dinv32) {
-    cudaError_t e = cudaMalloc(&h->dinv32, sizeof(__half) * (size_t)h->d.n);
+    cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->dinv32), sizeof(__half) * (size_t)h->d.n, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "preconditioner");
-    k_dinv32<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->dinv32);
+    k_dinv32<<<2432, 128, 0, st>>>(c, h->dinv32);
     h->launches += 1;
   }
+  debug_phase(h, "solve: preconditioner");
   ICtx ic;
   ic.B = h->d.B;
   ic.dinv = h->dinv32;
@@ -702,6 +734,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // the tensor cores when that is exact for this Nv, else from float64 GEMMs
   const int lv = split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
   h->last_precision = ESMP2_MIXED_BF16;
+  h->r_true = false;
   double eta = 1e-2;
   if (const char *ev = std::getenv("ESMP2_INNER_ETA")) eta = std::max(1e-12, std::atof(ev));
   while (true) {
@@ -718,7 +751,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     const double rn = std::sqrt(sl[8]), bn = std::sqrt(sl[9]);
     relres = bn > 0 ? rn / bn : 0.0;
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d\n", outer, relres, inner_total);
-    if (relres <= tol) { result = ESMP2_OK; break; }
+    if (relres <= tol) { result = ESMP2_OK; h->r_true = true; break; }
     if (inner_total >= maxit) break;
     // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
     // contracts the slices i < j and mirrors them)

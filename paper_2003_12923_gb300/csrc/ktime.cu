@@ -1,5 +1,8 @@
 // Process-wide timing of the kernel families of the hot path (esmp2_kernel_timing).
 #include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -35,6 +38,47 @@ KScope::~KScope() {
   cudaEventRecord(b_, st_);
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.push_back({a_, b_, fam_, alg_, exec_});
+}
+
+void debug_phase(esmp2_handle *h, const char *name) {
+  static const bool on = std::getenv("ESMP2_DEBUG") != nullptr;
+  if (!on) return;
+  static thread_local auto last = std::chrono::steady_clock::now();
+  cudaStreamSynchronize(h->stream);
+  const auto now = std::chrono::steady_clock::now();
+  std::fprintf(stderr, "esmp2 phase %-28s %9.3f ms\n", name, std::chrono::duration<double, std::milli>(now - last).count());
+  last = now;
+}
+
+cudaError_t dmalloc(void **p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static bool ready[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  const bool have_pool = dev >= 0 && dev < 64 && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess;
+  if (have_pool) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      uint64_t keep = tot / 3;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      ready[dev] = true;
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, st);
+  if (e == cudaErrorMemoryAllocation && have_pool) {  // give cached memory back and retry once
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocAsync(p, bytes ? bytes : 1, st);
+  }
+  return e;
+}
+
+void dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
 }
 
 double unique_amplitudes(int No, int Nv) {

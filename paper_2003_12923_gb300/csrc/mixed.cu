@@ -57,25 +57,14 @@ __global__ void k_build_rot(const double *V, int No, int Nv, double *R, double *
 // about 2^-46 relative accuracy; the float64 result is hi + lo.  The orbital rotations have
 // only No multiply-adds per element, which on this part would otherwise be float64-bound.
 constexpr int kDfK = 32;
-__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
-  const float ph = ah * bh;
-  const float pe = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
-  const float t = sh + ph;
-  const float bv = t - sh;
-  const float err = (sh - (t - bv)) + (ph - bv);
-  const float lo = sl + err + pe;
-  sh = t + lo;                 // renormalise (fast two-sum)
-  sl = lo - (sh - t);
-}
 
 __global__ void __launch_bounds__(256) k_mode_df(const double *in, double *out, int64_t P, int K, int64_t Q,
                                                  const double *R) {
-  __shared__ float Rh[kDfK * kDfK], Rl[kDfK * kDfK];
+  __shared__ float2 R2[kDfK * kDfK];      // (hi, lo) pairs: one 8-byte broadcast load per product
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const double r = R[e];
     const float hi = (float)r;
-    Rh[e] = hi;
-    Rl[e] = (float)(r - (double)hi);
+    R2[e] = make_float2(hi, (float)(r - (double)hi));
   }
   __syncthreads();
   const int64_t n = P * Q;
@@ -98,8 +87,17 @@ __global__ void __launch_bounds__(256) k_mode_df(const double *in, double *out, 
       for (int k = 0; k < kDfK; ++k) {
         if (k < K) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (k2 + c < K) df_fma(sh[c], sl[c], Rh[k * K + k2 + c], Rl[k * K + k2 + c], xh[k], xl[k]);
+          for (int c = 0; c < 4; ++c) {
+            if (k2 + c < K) {   // exact leading product, two-sum; renormalised once at the end
+              const float2 r = R2[k * K + k2 + c];
+              const float ph = r.x * xh[k];
+              const float pe = fmaf(r.x, xh[k], -ph) + fmaf(r.x, xl[k], r.y * xh[k]);
+              const float t = sh[c] + ph;
+              const float bv = t - sh[c];
+              sl[c] += ((sh[c] - (t - bv)) + (ph - bv)) + pe;
+              sh[c] = t;
+            }
+          }
         }
       }
 #pragma unroll
@@ -110,6 +108,23 @@ __global__ void __launch_bounds__(256) k_mode_df(const double *in, double *out, 
 }
 
 }  // namespace
+
+// out[p][k'][q] = sum_k R[k][k'] in[p][k][q] (R: K x K, row pitch K) in double-float
+// arithmetic when K <= 32, else as a float64 GEMM.
+void mode_product_small(const double *in, double *out, int64_t P, int K, int64_t Q, const double *R,
+                        cudaStream_t st) {
+  if (K <= kDfK) {
+    k_mode_df<<<1216, 256, 0, st>>>(in, out, P, K, Q, R);
+    return;
+  }
+  Gemm64 g{};
+  g.alpha = 1.0; g.beta = 0.0;
+  g.M = K; g.N = (int)Q; g.K = K; g.batch = (int)P;
+  g.A = R; g.sAm = 1; g.sAk = K; g.sAb = 0;
+  g.B = in; g.sBk = Q; g.sBn = 1; g.sBb = (int64_t)K * Q;
+  g.C = out; g.sCm = Q; g.sCn = 1; g.sCb = (int64_t)K * Q;
+  gemm64(g, st);
+}
 
 // in/out: block vectors; new occupied index i' = sum_i R[i][i'] (old i) (to_semi), or back.
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi) {
@@ -137,7 +152,7 @@ static esmp2_status alloc_mixed_buffers(esmp2_handle *h) {
   const size_t n = (size_t)h->d.n;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 1, h->stream);
   };
   A(&h->xlp, sizeof(__nv_bfloat16) * (size_t)5 * No * No * Nv * Nvp);
   A(&h->Fvlp, sizeof(__nv_bfloat16) * (size_t)Nv * Nvp);
@@ -158,7 +173,7 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   const size_t n = (size_t)h->d.n;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 1, h->stream);
   };
   A(reinterpret_cast<void **>(&h->Rocc), sizeof(double) * No * No);
   A(reinterpret_cast<void **>(&h->Rocct), sizeof(double) * No * No);
@@ -185,9 +200,10 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   A(reinterpret_cast<void **>(&W2), sizeof(double) * (size_t)N * N);
   A(reinterpret_cast<void **>(&T1), sizeof(double) * (size_t)N * N);
   if (e != cudaSuccess) {
-    cudaFree(V); cudaFree(work); cudaFree(W2); cudaFree(T1);
+    dfree(V, h->stream); dfree(work, h->stream); dfree(W2, h->stream); dfree(T1, h->stream);
     return check_cuda(h, e, "mixed set-up");
   }
+  debug_phase(h, "  mixed: allocations");
   if (m >= 1) eigvecs_block(h, h->F, 1, m, V, work);
   k_build_rot<<<64, 256, 0, h->stream>>>(V, No, Nv, h->Rocc, h->Rocct, W2);
   Gemm64 g{};
@@ -197,11 +213,12 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   g.A = W2; g.sAm = 1; g.sAk = N; g.B = T1; g.sBk = N; g.sBn = 1; g.C = h->Fsemi; g.sCm = N; g.sCn = 1;
   gemm64(g, h->stream);
   h->launches += 3;
+  debug_phase(h, "  mixed: basis (eigenvectors, F)");
   rotate_occ(h, h->b, h->bsemi, h->s64.w ? h->s64.w : h->s64.p, true);
+  debug_phase(h, "  mixed: rhs rotation");
   k_f64_to_f32<<<64, 256, 0, h->stream>>>(h->Fsemi, h->F32, (int64_t)N * N);
   h->launches += 1;
-  cudaStreamSynchronize(h->stream);
-  cudaFree(V); cudaFree(work); cudaFree(W2); cudaFree(T1);
+  dfree(V, h->stream); dfree(work, h->stream); dfree(W2, h->stream); dfree(T1, h->stream);
   h->mixed_ready = true;
   return check_cuda(h, cudaGetLastError(), "mixed set-up");
 }

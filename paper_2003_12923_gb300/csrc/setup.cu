@@ -490,15 +490,13 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl)
 constexpr int kXrN = 32;
 __global__ void __launch_bounds__(256) k_xr_df(const double *in, double *out, int64_t M, int K, int N, const double *R,
                                                int64_t ldR) {
-  extern __shared__ float sR[];           // [K][N + 1] hi, then [K][N + 1] lo
+  extern __shared__ float2 sR2[];         // [K][N + 1] (hi, lo) pairs: one 8-byte load per product
   const int ldS = N + 1;
-  float *Rh = sR, *Rl = sR + (size_t)K * ldS;
   for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
     const int k = e / N, n = e % N;
     const double r = R[(int64_t)k * ldR + n];
     const float hi = (float)r;
-    Rh[k * ldS + n] = hi;
-    Rl[k * ldS + n] = (float)(r - (double)hi);
+    sR2[k * ldS + n] = make_float2(hi, (float)(r - (double)hi));
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -511,20 +509,32 @@ __global__ void __launch_bounds__(256) k_xr_df(const double *in, double *out, in
     for (int k = lane; k < K; k += 32) {
       const double v = row[k];
       const float xh = (float)v, xl = (float)(v - (double)xh);
+      const float2 *rk = sR2 + k * ldS;
 #pragma unroll
-      for (int n = 0; n < kXrN; ++n)
-        if (n < N) df_fma(ah[n], al[n], Rh[k * ldS + n], Rl[k * ldS + n], xh, xl);
+      for (int n = 0; n < kXrN; ++n) {
+        if (n < N) {   // (ah, al) += (xh + xl)(rh + rl): exact leading product, two-sum, no renormalisation
+          const float2 r = rk[n];
+          const float ph = xh * r.x;
+          const float pe = fmaf(xh, r.x, -ph) + fmaf(xh, r.y, xl * r.x);
+          const float t = ah[n] + ph;
+          const float bv = t - ah[n];
+          al[n] += ((ah[n] - (t - bv)) + (ph - bv)) + pe;
+          ah[n] = t;
+        }
+      }
     }
     double mine = 0.0;
 #pragma unroll
     for (int n = 0; n < kXrN; ++n) {
       if (n < N) {
+        float sh = ah[n] + al[n];          // renormalise once
+        float sl = al[n] - (sh - ah[n]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, ah[n], o), ol = __shfl_xor_sync(0xffffffffu, al[n], o);
-          df_add(ah[n], al[n], oh, ol);
+          const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+          df_add(sh, sl, oh, ol);
         }
-        if (lane == n) mine = (double)ah[n] + (double)al[n];
+        if (lane == n) mine = (double)sh + (double)sl;
       }
     }
     if (lane < N) out[m * N + lane] = mine;
@@ -544,8 +554,9 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
   {
     const int dims[4] = {No, Nv, No, Nv};
     if (tc) {
-      mode_product(ovov_in, scratch, dims, 0, h->U, No, No, st);
-      mode_product(scratch, ovov_in, dims, 2, h->U, No, No, st);
+      mode_product_small(ovov_in, scratch, 1, No, (int64_t)Nv * No * Nv, h->U, st);   // i
+      mode_product_small(scratch, ovov_in, (int64_t)No * Nv, No, Nv, h->U, st);       // j
+      h->launches += 2;
       if ((s = xwv_split(h, ovov_in, (int64_t)No * Nv * No, scratch))) return s;   // b
       permute4(h, scratch, ovov_in, dims, 0, 2, 3, 1);                              // [i][j][b][a]
       if ((s = xwv_split(h, ovov_in, (int64_t)No * No * Nv, scratch))) return s;   // a
@@ -562,20 +573,30 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
       cudaMemcpyAsync(h->ovov, src, sizeof(double) * h->d.B, cudaMemcpyDeviceToDevice, st);
     }
   }
+  debug_phase(h, "  ovov transform");
   {
     const int dims[4] = {No, No, No, Nv};
     double *src = ooov_in, *dst = scratch;
     const double *R[4] = {h->U, h->U, h->U, h->Wv};
     const int K[4] = {No, No, No, Nv};
     for (int m = 0; m < 4; ++m) {
-      mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+      if (m < 3) {
+        int64_t P = 1, Q = 1;
+        for (int k = 0; k < m; ++k) P *= dims[k];
+        for (int k = m + 1; k < 4; ++k) Q *= dims[k];
+        mode_product_small(src, dst, P, No, Q, h->U, st);
+        h->launches += 1;
+      } else {
+        mode_product(src, dst, dims, m, R[m], K[m], K[m], st);
+      }
       double *t = src; src = dst; dst = t;
     }
     cudaMemcpyAsync(h->ooov, src, sizeof(double) * (size_t)No * No * No * Nv, cudaMemcpyDeviceToDevice, st);
   }
   {
+    debug_phase(h, "  ooov transform");
     int dims[4] = {No, Nv, Nv, Nv};
-    const size_t smem = sizeof(float) * 2 * (size_t)Nv * (No + 1);
+    const size_t smem = sizeof(float2) * (size_t)Nv * (No + 1);
     if (No <= kXrN && smem <= 200 * 1024) {  // c -> u' (first No columns of Wv)
       static size_t attr = 0;
       if (smem > attr) {
@@ -588,8 +609,10 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
       mode_product(ovvv_in, scratch, dims, 3, h->Wv, No, Nv, st);
     }
     dims[3] = No;
+    debug_phase(h, "  ovvv last index -> u'");
     if (tc) {
-      mode_product(scratch, ovvv_in, dims, 0, h->U, No, No, st);                    // [i][a][b][u]
+      mode_product_small(scratch, ovvv_in, 1, No, (int64_t)Nv * Nv * No, h->U, st);  // [i][a][b][u]
+      h->launches += 1;
       permute4(h, ovvv_in, scratch, dims, 0, 3, 1, 2);                             // [i][u][a][b]
       if ((s = xwv_split(h, scratch, (int64_t)No * No * Nv, ovvv_in))) return s;  // b
       const int d2[4] = {No, No, Nv, Nv};
@@ -607,6 +630,7 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
       cudaMemcpyAsync(h->ovvt, src, sizeof(double) * (size_t)No * Nv * Nv * No, cudaMemcpyDeviceToDevice, st);
     }
   }
+  debug_phase(h, "  ovvt rotations");
   k_f0vo<<<(unsigned)cdiv((int64_t)No * Nv, 256), 256, 0, st>>>(h->F, h->lam, h->ooov, h->ovvt, h->f0vo, No, Nv);
   k_rhs<<<1216, 256, 0, st>>>(h->lam, h->f0vo, h->ovov, h->ooov, h->ovvt, h->b, No, Nv);
   h->launches += 2;

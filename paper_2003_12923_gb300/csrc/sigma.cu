@@ -435,7 +435,7 @@ esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, do
   double acc[5] = {0, 0, 0, 0, 0};
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(ev[0], h->stream);
-    if (!h->P64) cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
+    if (!h->P64) dmalloc(reinterpret_cast<void **>(&h->P64), sizeof(double) * 4 * (size_t)h->d.B, h->stream);
     if (tc_levels) {
       esmp2_status s = virt_split(h, x, y, h->P64, 1, tc_levels);
       if (s) return s;
@@ -628,7 +628,7 @@ void combine_sym(esmp2_handle *h, double *y) {
 // cores, digit levels 2 .. tc_levels (F_vv of the handle); 0: float64 GEMMs with F.
 esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels) {
   if (!h->P64) {
-    cudaError_t e = cudaMalloc(&h->P64, sizeof(double) * 4 * (size_t)h->d.B);
+    cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->P64), sizeof(double) * 4 * (size_t)h->d.B, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "sigma64 workspace");
   }
   if (tc_levels) {

@@ -26,6 +26,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <vector>
+#include <mutex>
+#include <map>
 #include <cstdlib>
 
 #include "internal.h"
@@ -193,7 +196,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t it = 0;
       bool ok = true;
       const uint32_t bytesXF = (uint32_t)(A_BYTES + g.bn * BK * 2);
-      const uint32_t bytesFX = (uint32_t)(A_BYTES + (BN_MAX / 64) * 64 * BK * 2);
+      const int nb1 = (g.bn + 63) / 64;   // 64-column boxes of the MN-major X tile
+      const uint32_t bytesFX = (uint32_t)(A_BYTES + nb1 * 64 * BK * 2);
       for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
         const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
         const int terms = terms_of(g, s);
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_expect_tx(&full[st], bytesFX);
                 tma_3d(A, &tFa, &full[st], c0, a0, zf);
 #pragma unroll
-                for (int q = 0; q < BN_MAX / 64; ++q) tma_3d(B + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, zx);
+                for (int q = 0; q < nb1; ++q) tma_3d(B + q * (BK * 128), &tXb, &full[st], b0 + 64 * q, c0, zx);
               }
             }
           }
@@ -479,8 +483,12 @@ const char *launch_virt(cudaStream_t st, const void *xd, int x_planes, const voi
   const uint64_t sX[2] = {(uint64_t)Nvp * 2, (uint64_t)Nvp * Nv * 2};
   const uint64_t dF[3] = {(uint64_t)Nvp, (uint64_t)Nv, (uint64_t)F_planes};
   g.a_tiles = (Nv + tc::BM - 1) / tc::BM;
-  g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
-  g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
+  if (g.bn <= 0 || g.bn > tc::BN_MAX || (g.bn & 15)) {   // default column tile: fewest tiles of <= 256
+    g.b_tiles = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
+    g.bn = ((Nv + g.b_tiles - 1) / g.b_tiles + 15) & ~15;
+  } else {
+    g.b_tiles = (Nv + g.bn - 1) / g.bn;
+  }
   g.nk = (Nv + tc::BK - 1) / tc::BK;
   g.tiles = (int64_t)g.nslices * g.a_tiles * g.b_tiles;
   const uint32_t boxXa[3] = {64, 128, 1}, boxXb[3] = {64, 64, 1}, boxFa[3] = {64, 128, 1};
@@ -533,11 +541,13 @@ static bool split_terms() {
 
 // Inner-solve form: only T, X, Y slices with i < j and every S, Z slice are contracted; the
 // slice (j, i) of T, X, Y receives -y_ij (the blocks are antisymmetric under i <-> j).
-esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err) {
+// bn: column tile width (0 = the default, fewest tiles of at most 256 columns).
+static esmp2_status virt_bf16_sym_bn(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err, int bn) {
   if (esmp2_status s0 = ensure_slist(h)) return s0;
   const int No = h->d.No, S = 5 * No * No, half = No * (No - 1) / 2;
   const double nv = h->d.Nv, nv3 = nv * nv * nv;
   tc::Args g = plain_args(h->d.Nv, S, y, err);
+  g.bn = bn;
   g.nslices = h->nslist;
   g.slices = h->slist;
   g.per_block = No * No;
@@ -553,6 +563,7 @@ esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, floa
   h->launches += 1;
   if (split) {
     tc::Args g2 = plain_args(h->d.Nv, S, y, err);
+    g2.bn = bn;
     g2.nslices = 2 * No * No;
     g2.slices = h->slist + 3 * half;   // the S and Z slices
     g2.per_block = No * No;
@@ -567,6 +578,56 @@ esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, floa
     h->launches += 1;
   }
   return check_cuda(h, cudaGetLastError(), "virt_bf16_sym");
+}
+
+// Tile table keyed by (No, Nv): on the first inner contraction of a shape in this process,
+// the candidate column tile widths are timed on the handle's own operands (CUDA events,
+// one warm-up and one timed launch each) and the fastest is kept for every later call.
+// Candidates: the default, half of it, and 256 when Nv > 256.
+namespace {
+std::mutex g_tile_mu;
+std::map<std::pair<int, int>, int> g_tile_table;
+}  // namespace
+
+int tuned_column_tile(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err) {
+  const std::pair<int, int> key(h->d.No, h->d.Nv);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_table.find(key);
+    if (it != g_tile_table.end()) return it->second;
+  }
+  const int Nv = h->d.Nv;
+  const int nt = (Nv + tc::BN_MAX - 1) / tc::BN_MAX;
+  const int def = ((Nv + nt - 1) / nt + 15) & ~15;
+  std::vector<int> cand = {def};
+  const int halfw = ((def / 2) + 15) & ~15;
+  if (halfw >= 32 && halfw != def) cand.push_back(halfw);
+  if (Nv > tc::BN_MAX && def != tc::BN_MAX) cand.push_back(tc::BN_MAX);
+  int best = def;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cand.size() > 1 && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    for (int bn : cand) {
+      if (virt_bf16_sym_bn(h, xb, Fb, y, err, bn)) continue;
+      cudaEventRecord(e0, h->stream);
+      if (virt_bf16_sym_bn(h, xb, Fb, y, err, bn)) continue;
+      cudaEventRecord(e1, h->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = bn;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tile_table[key] = best;
+  return best;
+}
+
+esmp2_status virt_bf16_sym(esmp2_handle *h, const void *xb, const void *Fb, float *y, int *err) {
+  return virt_bf16_sym_bn(h, xb, Fb, y, err, tuned_column_tile(h, xb, Fb, y, err));
 }
 
 // y[s][a][b] = sum_c xb[s][a][c] F[c][b] + sum_c F[a][c] xb[s][c][b]  for S slices (fp32 out).
@@ -629,7 +690,7 @@ esmp2_status ensure_slist(esmp2_handle *h) {
   if (h->slist) return ESMP2_OK;
   const int No = h->d.No;
   const int nl = 3 * (No * (No - 1) / 2) + 2 * No * No;
-  cudaError_t e = cudaMalloc(&h->slist, sizeof(int) * (size_t)nl);
+  cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->slist), sizeof(int) * (size_t)nl, h->stream);
   if (e != cudaSuccess) { h->slist = nullptr; return check_cuda(h, e, "slice list"); }
   h->nslist = nl;
   k_split_list<<<(unsigned)cdiv(nl, 256), 256, 0, h->stream>>>(No, h->slist);
@@ -642,16 +703,17 @@ esmp2_status ensure_split(esmp2_handle *h) {
   if (esmp2_status s0 = ensure_slist(h)) return s0;
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, Nvp = (Nv + 7) & ~7;
   const int S = 5 * No * No, P = kSplitMaxLevels - 1;
-  cudaError_t e = cudaMalloc(&h->xdig, sizeof(__nv_bfloat16) * (size_t)P * S * Nv * Nvp);
-  if (e == cudaSuccess) e = cudaMalloc(&h->Fdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp);
-  if (e == cudaSuccess) e = cudaMalloc(&h->es, sizeof(int) * (size_t)(S + 2));  // slices, F_vv, W_v^T
+  cudaError_t e = dmalloc(&h->xdig, sizeof(__nv_bfloat16) * (size_t)P * S * Nv * Nvp, h->stream);
+  if (e == cudaSuccess) e = dmalloc(&h->Fdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp, h->stream);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&h->es), sizeof(int) * (size_t)(S + 2), h->stream);
   if (e != cudaSuccess) {
-    cudaFree(h->xdig); cudaFree(h->Fdig); cudaFree(h->es);
+    dfree(h->xdig, h->stream); dfree(h->Fdig, h->stream); dfree(h->es, h->stream);
     h->xdig = h->Fdig = nullptr; h->es = nullptr;
     return check_cuda(h, e, "split workspace");
   }
   if (!h->dflag) {
-    if ((e = cudaMalloc(&h->dflag, sizeof(int))) != cudaSuccess) return check_cuda(h, e, "split workspace");
+    if ((e = dmalloc(reinterpret_cast<void **>(&h->dflag), sizeof(int), h->stream)) != cudaSuccess)
+      return check_cuda(h, e, "split workspace");
     cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
   }
   // digits of F_vv (the same block in the TOP and the semicanonical-occupied basis); the
@@ -737,7 +799,7 @@ esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y
   }
   const int64_t NvNv = (int64_t)Nv * Nv;
   if (!h->Rdig) {  // digits of W_v^T: row b' holds column b' of W_v (the K-major right operand)
-    cudaError_t e = cudaMalloc(&h->Rdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp);
+    cudaError_t e = dmalloc(&h->Rdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "rotation digits");
     int *eR = h->es + 5 * No * No + 1;
     tc::k_slice_exp<<<1, 256, 0, h->stream>>>(h->Wv, Nv, Nv, 1, 0, eR, Nv);
