@@ -437,21 +437,89 @@ __device__ __forceinline__ double rcp64(double D) {
 
 // In every sector the common case holds exactly one TOP pair (u, u'); then b_I is a single
 // antisymmetrised integral times lam_u and the term is evaluated inline.  Triples whose
-// other indices form a second TOP pair take the general P(k/ij)P(c/ab) form (s.term).
-// Sectors A and B: loop over c, threads over b < c (coalesced (kc|jb), (jc|kb) rows).
+// other indices form a second TOP pair take the general P(k/ij)P(c/ab) form (s.term, in
+// float64).  The inline terms run in double-float arithmetic (value = hi + lo, two floats;
+// Dekker products, Knuth sums, one Newton-corrected quotient; about 2^-46 relative), which
+// moves the S-space sum from the float64 pipe to the float32 pipes: the integrals are kept
+// as (hi, lo) pairs (esmp2 keeps one copy per handle) and the orbital energies as pairs in
+// shared memory.
+struct dflt {
+  float h, l;
+};
+__device__ __forceinline__ dflt df_of(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const float s = a.h + b.h, bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ dflt df_neg(dflt a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e += a.h * b.l + a.l * b.h;
+  const float h = p + e;
+  return {h, e - (h - p)};
+}
+__device__ __forceinline__ dflt df_div(dflt a, dflt b) {
+  const float q1 = a.h / b.h;
+  // remainder a - q1 b with the leading product exact
+  const float p = q1 * b.h;
+  const float pe = fmaf(q1, b.h, -p);
+  const float r = ((a.h - p) - pe) + (a.l - q1 * b.l);
+  const float q2 = r / b.h;
+  const float h = q1 + q2;
+  return {h, q2 - (h - q1)};
+}
+__device__ __forceinline__ double df_to_double(dflt a) { return (double)a.h + (double)a.l; }
+
+// integrals as (hi, lo) pairs: same index as SCtx::g
+__global__ void k_ovov_df(const double *g, float2 *gdf, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = g[e];
+    const float h = (float)v;
+    gdf[e] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+struct SDf {
+  const float2 *g;  // (ia|jb) pairs
+  __device__ __forceinline__ dflt at(int No, int Nv, int i, int a, int j, int b) const {
+    const float2 v = g[(((int64_t)i * Nv + a) * No + j) * Nv + b];
+    return {v.x, v.y};
+  }
+};
+
+// shared-memory copy of the virtual orbital energies F_aa as pairs (Nv <= 4096)
+__device__ __forceinline__ void load_fv(const SCtx &s, float2 *fv) {
+  for (int a = threadIdx.x; a < s.Nv; a += blockDim.x) {
+    const dflt d = df_of(s.Fv(a));
+    fv[a] = make_float2(d.h, d.l);
+  }
+  __syncthreads();
+}
 
 // sector A: up-up-up, lowest pair u >= 1; block = (u, j, k)
-__global__ void k_e2s_a(SCtx s, double *red) {
+__global__ void k_e2s_a(SCtx s, SDf gd, double *red) {
+  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
-  if (u >= 1 && j < k && j != u && k != u) {
-    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
+  const bool active = u >= 1 && j < k && j != u && k != u;
+  if (active) load_fv(s, fv);
+  if (active) {
+    const double lu = s.lam[u];
+    const dflt c2 = df_of(-2.0 * lu * lu);
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
+    dflt acc = {0.f, 0.f};
     for (int c = 1; c < Nv; ++c) {
       if (c == u) continue;
-      const double Dc = Dh + s.Fv(c);
+      const dflt Dc = df_of(Dh + s.Fv(c));
       const bool cjk = (c == j || c == k);
       for (int b = threadIdx.x; b < c; b += blockDim.x) {
         if (b == u) continue;
@@ -463,25 +531,32 @@ __global__ void k_e2s_a(SCtx s, double *red) {
           v[0] += s.term(ho, hs, po, ps);
           continue;
         }
-        const double dg = s.g(k, c, j, b) - s.g(j, c, k, b);
-        v[0] += c2 * dg * dg * rcp64(Dc + s.Fv(b));
+        const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
+        const float2 f = fv[b];
+        acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
       }
     }
+    v[0] += df_to_double(acc);
   }
   block_partials<1>(v, red);
 }
 
 // sector B: up-down-down with the up pair u -> u' (u >= 1), any down-down double
-__global__ void k_e2s_b(SCtx s, double *red) {
+__global__ void k_e2s_b(SCtx s, SDf gd, double *red) {
+  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
   const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
-  if (u >= 1 && j < k) {
-    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
+  const bool active = u >= 1 && j < k;
+  if (active) load_fv(s, fv);
+  if (active) {
+    const double lu = s.lam[u];
+    const dflt c2 = df_of(-2.0 * lu * lu);
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
+    dflt acc = {0.f, 0.f};
     for (int c = 1; c < Nv; ++c) {
-      const double Dc = Dh + s.Fv(c);
+      const dflt Dc = df_of(Dh + s.Fv(c));
       const bool cjk = (c == j || c == k);
       for (int b = threadIdx.x; b < c; b += blockDim.x) {
         if (cjk || b == j || b == k) {
@@ -490,24 +565,31 @@ __global__ void k_e2s_b(SCtx s, double *red) {
           v[0] += s.term(ho, hs, po, ps);
           continue;
         }
-        const double dg = s.g(k, c, j, b) - s.g(j, c, k, b);
-        v[0] += c2 * dg * dg * rcp64(Dc + s.Fv(b));
+        const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
+        const float2 f = fv[b];
+        acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
       }
     }
+    v[0] += df_to_double(acc);
   }
   block_partials<1>(v, red);
 }
 
 // sector C: up-down-down without an up pair; lowest down pair u >= 1; block = (u, i, k),
 // threads over c (coalesced (ia|kc) rows), loop over a
-__global__ void k_e2s_c(SCtx s, double *red) {
+__global__ void k_e2s_c(SCtx s, SDf gd, double *red) {
+  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
   const int u = (int)(blk / ((int64_t)No * No)), i = (int)((blk / No) % No), k = (int)(blk % No);
   double v[1] = {0.0};
-  if (u >= 1 && k != u) {
-    const double lu = s.lam[u], c2 = -2.0 * lu * lu;
+  const bool active = u >= 1 && k != u;
+  if (active) load_fv(s, fv);
+  if (active) {
+    const double lu = s.lam[u];
+    const dflt c2 = df_of(-2.0 * lu * lu);
     const double Dh = s.Fv(u) - s.Fo(i) - s.Fo(u) - s.Fo(k) - s.omega;
+    dflt acc = {0.f, 0.f};
     for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
       if (c == u) continue;
       if (c == k) {
@@ -519,13 +601,15 @@ __global__ void k_e2s_c(SCtx s, double *red) {
         }
         continue;
       }
-      const double Dc = Dh + s.Fv(c);
+      const dflt Dc = df_of(Dh + s.Fv(c));
       for (int a = 0; a < Nv; ++a) {
         if (a == i) continue;
-        const double g = s.g(i, a, k, c);
-        v[0] += c2 * g * g * rcp64(Dc + s.Fv(a));
+        const dflt g = gd.at(No, Nv, i, a, k, c);
+        const float2 f = fv[a];
+        acc = df_add(acc, df_div(df_mul(c2, df_mul(g, g)), df_add(Dc, {f.x, f.y})));
       }
     }
+    v[0] += df_to_double(acc);
   }
   block_partials<1>(v, red);
 }
@@ -659,19 +743,28 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
     SCtx sc;
     sc.No = No; sc.Nv = h->d.Nv; sc.N = h->d.N; sc.F = h->F; sc.lam = h->lam; sc.ovov = h->ovov; sc.omega = h->omega;
     const int nb = No * No * No;
+    const int64_t ng = (int64_t)No * h->d.Nv * No * h->d.Nv;
+    float2 *gdf = nullptr;
+    cudaError_t ce = dmalloc(reinterpret_cast<void **>(&gdf), sizeof(float2) * (size_t)ng, st);
+    if (ce != cudaSuccess) return check_cuda(h, ce, "S-space integrals");
+    k_ovov_df<<<1216, 256, 0, st>>>(h->ovov, gdf, ng);
+    h->launches += 1;
+    SDf gd{gdf};
     double tot = 0.0;
     for (int sector = 0; sector < 3; ++sector) {
       {
         KScope ks(st, ESMP2_KT_E2S, 0.0, 0.0);
-        if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, h->red);
-        else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, h->red);
-        else k_e2s_c<<<nb, 128, 0, st>>>(sc, h->red);
+        if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, gd, h->red);
+        else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, gd, h->red);
+        else k_e2s_c<<<nb, 128, 0, st>>>(sc, gd, h->red);
       }
       k_finalize<<<1, 256, 0, st>>>(h->red, nb, 1, h->red_out, 3);
       h->launches += 2;
-      if ((s = read_slots(h, sl, 32))) return s;
+      if ((s = read_slots(h, sl, 32))) break;
       tot += sl[8];
     }
+    dfree(gdf, st);
+    if (s) return s;
     h->e2s = tot;
     h->e2s_done = true;
   }
