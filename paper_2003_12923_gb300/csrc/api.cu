@@ -8,7 +8,8 @@
 #include "internal.h"
 
 namespace esmp2 {
-esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, double *ovvv_in, double *scratch);
+esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovov_in, double *ooov_in,
+                            const double *ovvv_src, double *ovvv_in, double *scratch);
 }
 
 using namespace esmp2;
@@ -100,34 +101,40 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   ALLOC(h->cp.OZ, (size_t)No * Nv * Nv); ALLOC(h->cp.G, nC);
   ALLOC(h->cp.GP, (size_t)No * No * Nv); ALLOC(h->cp.HP, (size_t)No * No * Nv); ALLOC(h->cp.H, nC); ALLOC(h->cp.CYZ, nC);
   {
-    const size_t nred = std::max<size_t>((size_t)16 * 1216, (size_t)No * No * No);
+    const size_t nred = std::max<size_t>(std::max<size_t>((size_t)16 * 1216, (size_t)No * No * No),
+                                         (size_t)couple_dot_parts(h));
     ALLOC(h->red, nred);
   }
   ALLOC(h->red_out, (size_t)32);
   if ((ce = cudaMallocHost(reinterpret_cast<void **>(&h->hred), sizeof(double) * 32)) != cudaSuccess)
     return check_cuda(h, ce, "pinned alloc");
   debug_phase(h, "create: allocations");
-  // inputs -> device
-  const cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // inputs -> device; device-resident OVOV and OVVV are read in place by the first pass of
+  // their transforms (no staging copy), host inputs are staged in the work buffers
+  const bool dev = d->inputs_on_device != 0;
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   double *ovov_in = nullptr, *ooov_in = nullptr, *ovvv_in = nullptr, *scratch = nullptr;
   const size_t nscr = std::max(nOVOV, std::max(nOOOV, nOVVT));
   if ((ce = dalloc(&ovov_in, nOVOV, h->stream)) != cudaSuccess || (ce = dalloc(&ooov_in, nOOOV, h->stream)) != cudaSuccess ||
-      (ce = dalloc(&ovvv_in, std::max(nOVVV, nOVVT), h->stream)) != cudaSuccess ||
+      (ce = dalloc(&ovvv_in, dev ? nOVVT : std::max(nOVVV, nOVVT), h->stream)) != cudaSuccess ||
       (ce = dalloc(&scratch, nscr, h->stream)) != cudaSuccess) {
     dfree(ovov_in, h->stream); dfree(ooov_in, h->stream); dfree(ovvv_in, h->stream); dfree(scratch, h->stream);
     return check_cuda(h, ce, "input staging");
   }
   cudaMemcpyAsync(h->F, d->F, sizeof(double) * nF, kind, h->stream);
   cudaMemcpyAsync(h->C, d->C, sizeof(double) * nC, kind, h->stream);
-  cudaMemcpyAsync(ovov_in, d->ovov, sizeof(double) * nOVOV, kind, h->stream);
   cudaMemcpyAsync(ooov_in, d->ooov, sizeof(double) * nOOOV, kind, h->stream);
-  cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
+  if (!dev) {
+    cudaMemcpyAsync(ovov_in, d->ovov, sizeof(double) * nOVOV, kind, h->stream);
+    cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
+  }
+  const double *ovov_src = dev ? d->ovov : ovov_in, *ovvv_src = dev ? d->ovvv : ovvv_in;
   ce = cudaGetLastError();
   esmp2_status s = check_cuda(h, ce, "input copy");
   debug_phase(h, "create: input copies");
   if (!s) s = setup_top_basis(h);
   debug_phase(h, "create: TOP basis");
-  if (!s) s = setup_rhs_from(h, ovov_in, ooov_in, ovvv_in, scratch);
+  if (!s) s = setup_rhs_from(h, ovov_src, ovov_in, ooov_in, ovvv_src, ovvv_in, scratch);
   debug_phase(h, "create: transforms + rhs");
   if (!s) {
     cudaMemsetAsync(h->s64.x, 0, sizeof(double) * h->d.n, h->stream);

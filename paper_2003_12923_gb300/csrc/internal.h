@@ -134,7 +134,9 @@ esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
 esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int mode);
 void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);
-void couple32(esmp2_handle *h, const float *F32, const float *x, float *y);
+// dot (optional, couple_dot_parts(h) doubles): per-CTA partials of the weighted <x, y>
+void couple32(esmp2_handle *h, const float *F32, const float *x, float *y, double *dot = nullptr);
+int64_t couple_dot_parts(const esmp2_handle *h);
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels = 0);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
@@ -144,7 +146,7 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
 esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
-esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready = false);
+esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready = false, double *dot = nullptr);
 esmp2_status check_device_flag(esmp2_handle *h);
 void antisym_project(esmp2_handle *h, double *v);
 void combine_sym(esmp2_handle *h, double *y);

@@ -246,27 +246,6 @@ __global__ void ki_init(ICtx c, const double *r64, float *r, float *p, float *d,
   block_partials<2>(v, red);
 }
 
-__global__ void ki_dot(ICtx c, const float *u, const float *q, double *red) {
-  float a = 0.f;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int blk = 0; blk < 5; ++blk) {
-    float s = 0.f;
-    if (c.vec) {
-      const int64_t n4 = c.B >> 2;
-      const float4 *u4 = reinterpret_cast<const float4 *>(u + blk * c.B), *q4 = reinterpret_cast<const float4 *>(q + blk * c.B);
-      for (int64_t e = t0; e < n4; e += stride) {
-        const float4 a4 = u4[e], b4 = q4[e];
-        s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
-      }
-    } else {
-      for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) s += u[e] * q[e];
-    }
-    a += blk_weight(blk) * s;
-  }
-  double v[1] = {(double)a};
-  block_partials<1>(v, red);
-}
-
 // r -= alpha q; partials <r, M^-1 r>, <r, r>
 __global__ void ki_update(ICtx c, const double *slots, float *r, const float *q, double *red) {
   const float alpha = (float)slots[4];
@@ -830,11 +809,19 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   h->r_true = false;
   double eta = 1e-2;
   if (const char *ev = std::getenv("ESMP2_INNER_ETA")) eta = std::max(1e-12, std::atof(ev));
+  // An intermediate true residual only has to be accurate relative to itself: its digit
+  // levels follow the relative residual it is expected to show (a low estimate, so never
+  // too few levels); the residual that ends the refinement, and feeds the energy, always
+  // takes the full count.
+  double rho_next = 0.0;
   while (true) {
+    int lv_k = lv;
+    if (lv && rho_next > 1e1 * tol) lv_k = std::min(lv, split_levels_for(rho_next));
     if (outer == 0 && h->x_zero) {  // cold start: the first true residual is b itself
       cudaMemsetAsync(q, 0, sizeof(double) * h->d.n, st);
+      lv_k = lv;
     } else {
-      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv))) return s;
+      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k))) return s;
       ++nsig64;
     }
     k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, q, r, h->red);
@@ -843,7 +830,9 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if ((s = read_slots(h, sl, 32))) return s;
     const double rn = std::sqrt(sl[8]), bn = std::sqrt(sl[9]);
     relres = bn > 0 ? rn / bn : 0.0;
-    if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d\n", outer, relres, inner_total);
+    if (std::getenv("ESMP2_DEBUG"))
+      std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d levels %d\n", outer, relres, inner_total, lv_k);
+    if (relres <= 1e1 * tol && lv_k < lv) { rho_next = 0.0; continue; }  // confirm with every level
     if (relres <= tol) { result = ESMP2_OK; h->r_true = true; break; }
     if (inner_total >= maxit) break;
     // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
@@ -860,14 +849,13 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     // one inner iteration: q = A p, alpha, x/r update, beta, p update (device scalars only)
     auto inner_step = [&]() -> esmp2_status {
       const int64_t l0 = h->launches;
-      esmp2_status s2 = sigma_inner(h, p32, q32, fused_bf16);
+      esmp2_status s2 = sigma_inner(h, p32, q32, fused_bf16, h->red);  // p.q partials from the coupling pass
       if (s2) return s2;
-      ki_dot<<<kRedBlocks, kRedThreads, 0, st>>>(ic, p32, q32, h->red);
-      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 1);
+      k_finalize<<<1, 256, 0, st>>>(h->red, (int)couple_dot_parts(h), 1, h->red_out, 1);
       ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
       ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32, d32);
-      h->launches += 5;
+      h->launches += 4;
       h->inner_graph_launches_pending = h->launches - l0;
       return check_cuda(h, cudaGetLastError(), "inner step");
     };
@@ -909,6 +897,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     }
     if (result == ESMP2_ERR_INDEFINITE) break;
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine:   inner %d  |r_in|/|r0| %.3e\n", inner, std::sqrt(sl[1]) / r0);
+    rho_next = relres * std::max(r0 > 0 ? std::sqrt(sl[1]) / r0 : 0.0, 1e-4);
     kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
     h->launches += 1;
     h->x_zero = false;

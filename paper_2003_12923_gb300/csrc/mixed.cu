@@ -240,13 +240,14 @@ esmp2_status check_device_flag(esmp2_handle *h) {
 // virtual-index terms from bf16 operands on tcgen05 and everything else in float32.
 // p_bf16_ready: the PCG update already wrote bf16(p) into the operand buffer.  The T, X, Y
 // slices j > i are filled from i < j (antisymmetry), so p is taken as antisymmetric.
-esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready) {
+// dot: optional per-CTA partials of the weighted <p, q> (couple_dot_parts(h) doubles).
+esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready, double *dot) {
   const int No = h->d.No, Nv = h->d.Nv;
   const int64_t rows = (int64_t)5 * No * No * Nv;
   if (!p_bf16_ready) to_bf16_f32(h, p, h->xlp, rows);
   esmp2_status s = virt_bf16_sym(h, h->xlp, h->Fvlp, q, h->dflag);
   if (s) return s;
-  couple32(h, h->F32, p, q);
+  couple32(h, h->F32, p, q, dot);
   return check_cuda(h, cudaGetLastError(), "sigma_inner");
 }
 

@@ -436,8 +436,10 @@ esmp2_status setup_top_basis(esmp2_handle *h) {
   return check_cuda(h, ce, "TOP basis");
 }
 
-// Integral transforms (in place on the handle's copies) + f0 + right-hand side.
-// ovov_in / ooov_in / ovvv_in are device copies of the inputs; ovvv_in is consumed.
+// Integral transforms + f0 + right-hand side.  ovov_src / ovvv_src are the device inputs
+// (read only: the first pass of each transform reads them directly); ovov_in, ooov_in
+// and ovvv_in are the handle's work buffers (ooov_in holds a copy of the input, ovvv_in
+// No Nv Nv No elements), all consumed.
 namespace {
 // out[o0][o1][o2][o3] = in[...] with input axis ax[k] running along output axis k
 __global__ void k_permute4(const double *in, double *out, int d0, int d1, int d2, int d3, int a0, int a1, int a2,
@@ -546,7 +548,8 @@ __global__ void __launch_bounds__(256) k_xr_df(const double *in, double *out, in
 // GEMMs; rotations by W_v (Nv x Nv) run as X W_v on the tensor cores from exact digit
 // products (float64 accuracy), after moving the rotated index last.  The contraction of
 // the last OVVV index with the TOP virtuals (Nv -> No columns) stays a float64 GEMM.
-esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, double *ovvv_in, double *scratch) {
+esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovov_in, double *ooov_in,
+                            const double *ovvv_src, double *ovvv_in, double *scratch) {
   const int No = h->d.No, Nv = h->d.Nv;
   cudaStream_t st = h->stream;
   const bool tc = (int64_t)9 * Nv * 1024 < (1LL << 24);   // exact ten-level digit sums (one term)
@@ -554,7 +557,7 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
   {
     const int dims[4] = {No, Nv, No, Nv};
     if (tc) {
-      mode_product_small(ovov_in, scratch, 1, No, (int64_t)Nv * No * Nv, h->U, st);   // i
+      mode_product_small(ovov_src, scratch, 1, No, (int64_t)Nv * No * Nv, h->U, st);  // i
       mode_product_small(scratch, ovov_in, (int64_t)No * Nv, No, Nv, h->U, st);       // j
       h->launches += 2;
       if ((s = xwv_split(h, ovov_in, (int64_t)No * Nv * No, scratch))) return s;   // b
@@ -563,6 +566,8 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
       const int d2[4] = {No, No, Nv, Nv};
       permute4(h, scratch, h->ovov, d2, 0, 3, 1, 2);                                // [i][a][j][b]
     } else {
+      if (ovov_src != ovov_in)
+        cudaMemcpyAsync(ovov_in, ovov_src, sizeof(double) * h->d.B, cudaMemcpyDeviceToDevice, st);
       double *src = ovov_in, *dst = scratch;
       const double *R[4] = {h->U, h->Wv, h->U, h->Wv};
       const int K[4] = {No, Nv, No, Nv};
@@ -603,10 +608,10 @@ esmp2_status setup_rhs_from(esmp2_handle *h, double *ovov_in, double *ooov_in, d
         cudaFuncSetAttribute(k_xr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
       }
-      k_xr_df<<<1216, 256, smem, st>>>(ovvv_in, scratch, (int64_t)No * Nv * Nv, Nv, No, h->Wv, Nv);
+      k_xr_df<<<1216, 256, smem, st>>>(ovvv_src, scratch, (int64_t)No * Nv * Nv, Nv, No, h->Wv, Nv);
       h->launches += 1;
     } else {
-      mode_product(ovvv_in, scratch, dims, 3, h->Wv, No, Nv, st);
+      mode_product(ovvv_src, scratch, dims, 3, h->Wv, No, Nv, st);
     }
     dims[3] = No;
     debug_phase(h, "  ovvv last index -> u'");

@@ -12,6 +12,8 @@
 // Part (1) runs as four float64 GEMM passes here (the mixed-precision path replaces
 // them with tcgen05 contractions), parts (2)-(3) as one element-wise pass fed by
 // small intermediates.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace esmp2 {
@@ -25,6 +27,7 @@ struct CtxT {
   const CT *F;
   CT omega;
   int arrow;  // 1: F_oo is diagonal apart from the t row/column (occupied terms done here)
+  double *dot = nullptr;  // coupling pass: per-CTA weighted partials of <x, y>, or none
   __device__ __forceinline__ CT Fo(int k, int l) const { return F[(int64_t)k * N + l]; }
   __device__ __forceinline__ CT Fv(int a, int b) const { return F[(int64_t)(No + a) * N + No + b]; }
   __device__ __forceinline__ CT Fov(int k, int a) const { return F[(int64_t)k * N + No + a]; }
@@ -150,10 +153,74 @@ __global__ void k_inter_d(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
   }
 }
 
+// (b) in one pass for the arrow form (No <= 32): a thread owns one (blk, a, b) and reads
+// the block's No x No occupied matrix at that (a, b) once; its row sums give OC2 (and OZ
+// on Z), its column sums OC1 (and OX on X), the column sums held in registers.
+// BLK < 0: grid.y runs over T, S, Y (no OX/OZ terms); else the one block BLK.
+template <int BLK, typename T, typename CT>
+__global__ void __launch_bounds__(128, 4) k_inter_b1(CtxT<CT> c, const T *__restrict__ x, CouplingsT<CT> cp) {
+  __shared__ CT fl[32], fk[32];
+  const int No = c.No;
+  const int blk = BLK >= 0 ? BLK : (blockIdx.y == 0 ? BT : (blockIdx.y == 1 ? BS : BY));
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    fl[l] = (l >= 1 && l < No) ? c.Fo(l, 0) : CT(0);
+    fk[l] = l < No ? c.Fov(l, 0) : CT(0);
+  }
+  __syncthreads();
+  const int64_t NvNv = (int64_t)c.Nv * c.Nv, n = (int64_t)No * NvNv;
+  const T *xb = x + blk * c.B;
+  CT *oc1 = cp.OC1 + blk * n, *oc2 = cp.OC2 + blk * n;
+  for (int64_t ab = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ab < NvNv; ab += (int64_t)gridDim.x * blockDim.x) {
+    CT o1[32];
+    CT ox[BLK == BX ? 32 : 1];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) o1[m] = CT(0);
+#pragma unroll
+    for (int m = 0; m < (BLK == BX ? 32 : 1); ++m) ox[m] = CT(0);
+    for (int l = 0; l < No; ++l) {
+      const T *row = xb + (int64_t)l * n + ab;
+      const CT fll = fl[l], fkl = fk[l];
+      CT r2 = CT(0), rz = CT(0);
+#pragma unroll
+      for (int m = 0; m < 32; ++m) {
+        if (m < No) {
+          const CT v = (CT)row[(int64_t)m * NvNv];
+          o1[m] += fll * v;
+          r2 += fl[m] * v;
+          if constexpr (BLK == BX) ox[m] += fkl * v;
+          if constexpr (BLK == BZ) rz += fk[m] * v;
+        }
+      }
+      oc2[(int64_t)l * NvNv + ab] = r2;
+      if constexpr (BLK == BZ) cp.OZ[(int64_t)l * NvNv + ab] = rz;
+    }
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+      if (m < No) {
+        oc1[(int64_t)m * NvNv + ab] = o1[m];
+        if constexpr (BLK == BX) cp.OX[(int64_t)m * NvNv + ab] = ox[m];
+      }
+    }
+  }
+}
+
 template <typename T, typename CT>
 void launch_inter(esmp2_handle *h, const CtxT<CT> &c, const T *x, const CouplingsT<CT> &cp) {
   k_inter_a<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
-  k_inter_b<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
+  bool one_pass = false;
+  if constexpr (sizeof(CT) == 4) one_pass = c.arrow && c.No <= 32;
+  if (one_pass) {
+    if constexpr (sizeof(CT) == 4) {
+      const unsigned gx = (unsigned)std::min<int64_t>(cdiv((int64_t)c.Nv * c.Nv, 128), 8192);
+      k_inter_b1<-1, T, CT><<<dim3(gx, 3), 128, 0, h->stream>>>(c, x, cp);
+      k_inter_b1<BX, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp);
+      k_inter_b1<BZ, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp);
+      h->launches += 2;
+    }
+  } else {
+    k_inter_b<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
+  }
   k_inter_c<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
   k_inter_d<T, CT><<<(unsigned)cdiv(3LL * c.No * c.Nv, 256), 256, 0, h->stream>>>(c, x, cp);
   h->launches += 4;
@@ -187,15 +254,22 @@ __device__ __forceinline__ void stv(T *p, const CT (&v)[VW]) {
   }
 }
 
+// Bulk prefetch of a contiguous range into L2 (16-byte aligned, a multiple of 16 bytes):
+// nothing waits on it and no register holds it, so a CTA's whole strip is in flight at once.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // y += couplings - omega x (+ pair energy on L blocks); y = 0 on non-amplitude slots.
 // One launch per block; a CTA owns a 32-row strip of one slice (i, j) and walks its
 // 32 x (32 VW) tiles along b, each thread VW consecutive columns of four rows.  Block,
 // slice and strip are uniform over the CTA, so every gather is a coalesced (vector) row of
 // some slice or a broadcast, all slice pointers are formed once, and the element loop runs
 // on 32-bit offsets; the one transposed operand (Z_ji^ba of the S block) goes through
-// shared memory.
+// shared memory.  With c.dot set, the CTA also leaves w_blk <x, y> over its strip (y final:
+// this pass is the last writer) in c.dot[(BLK gridDim.y + blockIdx.y) gridDim.x + blockIdx.x].
 template <int BLK, int VW, typename TX, typename TY, typename CT>
-__global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restrict__ x, TY *__restrict__ y,
+__global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, const TX *__restrict__ x, TY *__restrict__ y,
                                                 CouplingsT<CT> cp) {
   constexpr int TW = 32 * VW;  // tile columns
   __shared__ CT zt[TW][33];
@@ -215,6 +289,23 @@ __global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restr
   const CT *OC1 = c.arrow ? cp.OC1 + ((int64_t)BLK * No + j) * NvNv : nullptr;
   const CT *OC2 = c.arrow ? cp.OC2 + ((int64_t)BLK * No + i) * NvNv : nullptr;
   const CT *Fo_i = c.F + (int64_t)i * c.N + No, *Fo_j = c.F + (int64_t)j * c.N + No, *Fo_0 = c.F + No;
+  if constexpr (VW * sizeof(TX) == 16 && sizeof(TY) == sizeof(TX)) {
+    // rows start on 16-byte boundaries here: fetch the strip of every operand streamed from
+    // HBM (x, y and the same-slot slice of the block this one couples to) ahead of the loads
+    const int64_t off = (int64_t)a_base * Nv;
+    const uint32_t bytes = (uint32_t)(min(32, Nv - a_base) * Nv * (int)sizeof(TX));
+    const TX *other = BLK == BT ? S(BX, i, j) : BLK == BS ? S(BZ, i, j) : BLK == BZ ? S(BS, i, j) : S(BT, i, j);
+    if (threadIdx.x == 0) l2_prefetch(xs + off, bytes);
+    if (threadIdx.x == 32) l2_prefetch(ys + off, bytes);
+    if (threadIdx.x == 64) l2_prefetch(other + off, bytes);
+    if (BLK == BT && threadIdx.x == 96) l2_prefetch(S(BY, i, j) + off, bytes);
+    if (BLK == BS) {  // the transposed slice: Nv rows of the strip's 32 columns
+      const TX *zji = S(BZ, j, i) + a_base;
+      const uint32_t rb = (uint32_t)(min(32, Nv - a_base) * (int)sizeof(TX));
+      for (int bb = threadIdx.x; bb < Nv; bb += blockDim.x) l2_prefetch(zji + (int64_t)bb * Nv, rb);
+    }
+  }
+  CT xy = CT(0);
   for (int tb = 0; tb < nt; ++tb) {
     const int b = tb * TW + tx * VW;  // first of this thread's VW columns
     if constexpr (BLK == BS) {  // Z_ji[b][a] for the tile, read along a and used along b
@@ -234,6 +325,15 @@ __global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restr
       fob_i[k] = Fo_i[b + k];
       fob_j[k] = Fo_j[b + k];
     }
+    // t-row vectors (a = 0 row of a slice) used by every row of the tile
+    CT h1[VW], h2[VW], h3[VW];
+    if constexpr (BLK == BX) {
+      ldv<VW>(S(BT, i, j) + b, h1); ldv<VW>(S(BT, 0, j) + b, h2); ldv<VW>(S(BT, 0, i) + b, h3);
+    } else if constexpr (BLK == BY) {
+      ldv<VW>(S(BS, 0, i) + b, h1); ldv<VW>(S(BS, 0, j) + b, h2);
+    } else if constexpr (BLK == BZ) {
+      ldv<VW>(S(BT, 0, j) + b, h1); ldv<VW>(S(BY, 0, j) + b, h2);
+    }
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int r = ty + 8 * rr;
@@ -241,8 +341,9 @@ __global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restr
       if (a >= Nv) break;
       const int ab = a * Nv + b;
       const bool a0f = a == 0;
-      CT xe[VW], v[VW], t1[VW], t2[VW];
+      CT xe[VW], yo[VW], v[VW], t1[VW], t2[VW];
       ldv<VW>(xs + ab, xe);
+      ldv<VW>(ys + ab, yo);  // issued with x: one memory round trip per row
 #pragma unroll
       for (int k = 0; k < VW; ++k) v[k] = -om * xe[k];
       if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
@@ -287,22 +388,20 @@ __global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restr
         const TX *T = S(BT, i, j), *T0j = S(BT, 0, j), *T0i = S(BT, 0, i);
         const CT foa_0 = Fo_0[a], foa_i = Fo_i[a], foa_j = Fo_j[a];
         const CT Ta = (CT)T[a], T0ja = (CT)T0j[a], T0ia = (CT)T0i[a];
-        CT Tab[VW], Tb[VW], T0jab[VW], T0iab[VW], T0jb[VW], T0ib[VW];
-        ldv<VW>(T + ab, Tab); ldv<VW>(T + b, Tb);
-        ldv<VW>(T0j + ab, T0jab); ldv<VW>(T0i + ab, T0iab);
-        ldv<VW>(T0j + b, T0jb); ldv<VW>(T0i + b, T0ib);
+        CT Tab[VW], T0jab[VW], T0iab[VW];
+        ldv<VW>(T + ab, Tab); ldv<VW>(T0j + ab, T0jab); ldv<VW>(T0i + ab, T0iab);
 #pragma unroll
-        for (int k = 0; k < VW; ++k)
-          v[k] += shift * xe[k] + f00 * Tab[k] - foa_0 * Tb[k] + fob_0[k] * Ta - fio * T0jab[k] + fjo * T0iab[k]
-                + foa_i * T0jb[k] - foa_j * T0ib[k] - fob_i[k] * T0ja + fob_j[k] * T0ia;
+        for (int k = 0; k < VW; ++k)  // h1 = T_ij row 0, h2 = T_0j row 0, h3 = T_0i row 0 at b
+          v[k] += shift * xe[k] + f00 * Tab[k] - foa_0 * h1[k] + fob_0[k] * Ta - fio * T0jab[k] + fjo * T0iab[k]
+                + foa_i * h2[k] - foa_j * h3[k] - fob_i[k] * T0ja + fob_j[k] * T0ia;
       } else if constexpr (BLK == BY) {
         const TX *S0i = S(BS, 0, i), *S0j = S(BS, 0, j);
         const CT S0ia = (CT)S0i[a], S0ja = (CT)S0j[a], foa_i = Fo_i[a], foa_j = Fo_j[a];
-        CT Tab[VW], S0ib[VW], S0jb[VW];
-        ldv<VW>(S(BT, i, j) + ab, Tab); ldv<VW>(S0i + b, S0ib); ldv<VW>(S0j + b, S0jb);
+        CT Tab[VW];
+        ldv<VW>(S(BT, i, j) + ab, Tab);
 #pragma unroll
-        for (int k = 0; k < VW; ++k)
-          v[k] += shift * xe[k] + f00 * Tab[k] + fob_j[k] * S0ia - fob_i[k] * S0ja - foa_j * S0ib[k] + foa_i * S0jb[k];
+        for (int k = 0; k < VW; ++k)  // h1 = S_0i row 0, h2 = S_0j row 0 at b
+          v[k] += shift * xe[k] + f00 * Tab[k] + fob_j[k] * S0ia - fob_i[k] * S0ja - foa_j * h1[k] + foa_i * h2[k];
         if (i0 && a0f) { ldv<VW>(cp.CYZ + j * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
         if (j0 && a0f) { ldv<VW>(cp.CYZ + i * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
         if (b == 0) {
@@ -312,22 +411,34 @@ __global__ void __launch_bounds__(256, 3) k_couple(CtxT<CT> c, const TX *__restr
       } else {  // BZ
         const TX *Sij = S(BS, i, j), *Si0 = S(BS, i, 0);
         const CT Sija0 = (CT)Sij[a * Nv], Si0a0 = (CT)Si0[a * Nv], foa_i = Fo_i[a], fva = c.Fv(a, 0);
-        CT Sijab[VW], Si0ab[VW], T0jb[VW], Y0jb[VW];
+        CT Sijab[VW], Si0ab[VW];
         ldv<VW>(Sij + ab, Sijab); ldv<VW>(Si0 + ab, Si0ab);
-        ldv<VW>(S(BT, 0, j) + b, T0jb); ldv<VW>(S(BY, 0, j) + b, Y0jb);
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < VW; ++k) {  // h1 = T_0j row 0, h2 = Y_0j row 0 at b
           v[k] += shift * xe[k] + f00 * Sijab[k] - fob_0[k] * Sija0 - fjo * Si0ab[k] + fob_j[k] * Si0a0
-                + foa_i * T0jb[k];
-          if (i0) v[k] += fva * Y0jb[k];
-          if (a0f) v[k] -= foi * Y0jb[k];
+                + foa_i * h1[k];
+          if (i0) v[k] += fva * h2[k];
+          if (a0f) v[k] -= foi * h2[k];
         }
       }
-      CT yo[VW];
-      ldv<VW>(ys + ab, yo);
 #pragma unroll
-      for (int k = 0; k < VW; ++k) yo[k] = valid_elem(BLK, i, j, a, b + k) ? yo[k] + v[k] : CT(0);
+      for (int k = 0; k < VW; ++k) {
+        yo[k] = valid_elem(BLK, i, j, a, b + k) ? yo[k] + v[k] : CT(0);
+        xy += xe[k] * yo[k];
+      }
       stv<VW>(ys + ab, yo);
+    }
+  }
+  if (c.dot) {
+    __shared__ double wsum[8];
+    const double s = (double)warp_sum<CT>(xy);
+    if (tx == 0) wsum[ty] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += wsum[w];
+      const double wb = BLK == BS ? 1.0 : (BLK == BZ ? 2.0 : 0.5);
+      c.dot[((int64_t)BLK * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = wb * t;
     }
   }
 }
@@ -376,9 +487,14 @@ void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *
 
 // float coupling + arrow occupied pass of the inner (low-precision) sigma: float arithmetic
 // throughout (float64 runs at a small fraction of the float32 rate on this part).
-void couple32(esmp2_handle *h, const float *F32, const float *x, float *y) {
-  const CtxT<float> c = make_ctx<float>(h, F32, 1);
+int64_t couple_dot_parts(const esmp2_handle *h) {
+  return 5 * cdiv(h->d.Nv, 32) * h->d.No * h->d.No;
+}
+
+void couple32(esmp2_handle *h, const float *F32, const float *x, float *y, double *dot) {
+  CtxT<float> c = make_ctx<float>(h, F32, 1);
   launch_inter<float, float>(h, c, x, h->cp32);
+  c.dot = dot;
   launch_couple<float, float, float>(c, x, y, h->cp32, h->stream);
   h->launches += 5;
 }
