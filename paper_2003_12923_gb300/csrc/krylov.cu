@@ -406,14 +406,6 @@ struct SCtx {
   }
 };
 
-// 1 / D from a float seed and one Newton-Raphson step (it squares the relative error:
-// 2^-24 -> 2^-48, far below what the S-space sum needs); D is a sum of orbital energies,
-// far from the float range limits.
-__device__ __forceinline__ double rcp64(double D) {
-  const double r = (double)(1.0f / (float)D);
-  return fma(r, fma(-D, r, 1.0), r);
-}
-
 // In every sector the common case holds exactly one TOP pair (u, u'); then b_I is a single
 // antisymmetrised integral times lam_u and the term is evaluated inline.  Triples whose
 // other indices form a second TOP pair take the general P(k/ij)P(c/ab) form (s.term, in

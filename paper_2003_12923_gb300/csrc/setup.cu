@@ -8,6 +8,7 @@
 //    positive, u_k = C v_k / lambda_k;
 //  * AVOs = columns No.. of the product of the Householder reflectors that
 //    triangularise V (H = I - 2 w w^T / w^T w, w = x - alpha e_0, alpha = -sign(x_0)|x|).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -464,18 +465,29 @@ void permute4(esmp2_handle *h, const double *in, double *out, const int d[4], in
   h->launches += 1;
 }
 
-// Double-float arithmetic (two floats hi + lo per float64 value): products with their exact
-// fma error, sums by Knuth's two-sum, renormalised after every step; about 2^-46 relative.
-__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
-  const float ph = ah * bh;
-  const float pe = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
-  const float t = sh + ph;
-  const float bv = t - sh;
-  const float err = (sh - (t - bv)) + (ph - bv);
-  const float lo = sl + err + pe;
-  sh = t + lo;
-  sl = lo - (sh - t);
+// v = hi + lo: hi holds the leading 24 significand bits of v (truncated), lo the remaining
+// 29 bits rounded to float, so |v - hi - lo| <= 2^-48 |v|.  Integer operations only (one
+// integer-to-float conversion): float64 conversions and adds run at the float64 rate,
+// which GB300 keeps at a small fraction of the float32 rate.  |v| < 2^-74 (and zero)
+// gives (0, 0) up to that bound; |v| >= 2^127 takes the float64 route.
+__device__ __forceinline__ float2 split_df(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF);  // biased float64 exponent
+  if (e < 949) return make_float2(0.f, 0.f);
+  if (e > 1150) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+  // lo = rest * 2^(e - 1075), the power of two a normal float for e >= 949
+  const float scale = __uint_as_float(sign | ((unsigned)(e - 948) << 23));
+  const float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * scale;
+  return make_float2(hi, lo);
 }
+
+// Double-float sum (two floats hi + lo per float64 value): Knuth's two-sum, renormalised.
 __device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
   const float t = sh + bh;
   const float bv = t - sh;
@@ -486,60 +498,74 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl)
 }
 
 // out[m][n] = sum_k in[m][k] R[k][n] for n < N <= 32 (a tall matrix times a narrow right
-// factor held in shared memory), one warp per row, double-float accumulation.  The
-// contraction of the last OVVV index with the TOP virtuals: No multiply-adds per input
-// element, float64-bound on this part in plain float64.
-constexpr int kXrN = 32;
-__global__ void __launch_bounds__(256) k_xr_df(const double *in, double *out, int64_t M, int K, int N, const double *R,
-                                               int64_t ldR) {
-  extern __shared__ float2 sR2[];         // [K][N + 1] (hi, lo) pairs: one 8-byte load per product
-  const int ldS = N + 1;
-  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
-    const int k = e / N, n = e % N;
-    const double r = R[(int64_t)k * ldR + n];
-    const float hi = (float)r;
-    sR2[k * ldS + n] = make_float2(hi, (float)(r - (double)hi));
+// factor): lane n of a warp owns output column n of kXrRows rows at once, so one shared
+// load of R[k][n] serves kXrRows products and no cross-lane sum is needed.  The rows are
+// staged 32 columns at a time, split into (hi, lo) floats, through a per-warp shared
+// buffer while the next 32 columns are in flight.  Double-float accumulation: exact
+// leading product and two-sum per term, every 32-term chunk added into the running sum
+// with a renormalised double-float add.  The contraction of the last OVVV index with the
+// TOP virtuals (No multiply-adds per input element).
+constexpr int kXrN = 32, kXrRows = 8, kXrWarps = 16;
+size_t xr_df_smem(int K) { return sizeof(float2) * ((size_t)K * kXrN + (size_t)kXrWarps * kXrRows * 32); }
+__global__ void __launch_bounds__(kXrWarps * 32) k_xr_df(const double *__restrict__ in, double *__restrict__ out,
+                                                         int64_t M, int K, int N, const double *__restrict__ R,
+                                                         int64_t ldR) {
+  extern __shared__ float2 sm[];
+  float2 *sR = sm;  // [K][32] (hi, lo), columns >= N zero
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2 *sx = sm + (size_t)K * kXrN + warp * (kXrRows * 32);  // this warp's [kXrRows][32]
+  for (int e = threadIdx.x; e < K * kXrN; e += blockDim.x) {
+    const int k = e >> 5, n = e & 31;
+    sR[e] = n < N ? split_df(R[(int64_t)k * ldR + n]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t m = w0; m < M; m += nw) {
-    float ah[kXrN], al[kXrN];
+  const int64_t groups = (M + kXrRows - 1) / kXrRows;
+  for (int64_t g = (int64_t)blockIdx.x * kXrWarps + warp; g < groups; g += (int64_t)gridDim.x * kXrWarps) {
+    const int64_t m0 = g * kXrRows;
+    float sh[kXrRows], sl[kXrRows];
+    double nx[kXrRows];
 #pragma unroll
-    for (int n = 0; n < kXrN; ++n) { ah[n] = 0.f; al[n] = 0.f; }
-    const double *row = in + m * K;
-    for (int k = lane; k < K; k += 32) {
-      const double v = row[k];
-      const float xh = (float)v, xl = (float)(v - (double)xh);
-      const float2 *rk = sR2 + k * ldS;
+    for (int r = 0; r < kXrRows; ++r) {
+      sh[r] = 0.f;
+      sl[r] = 0.f;
+      nx[r] = (m0 + r < M && lane < K) ? in[(m0 + r) * K + lane] : 0.0;
+    }
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      __syncwarp();
 #pragma unroll
-      for (int n = 0; n < kXrN; ++n) {
-        if (n < N) {   // (ah, al) += (xh + xl)(rh + rl): exact leading product, two-sum, no renormalisation
-          const float2 r = rk[n];
-          const float ph = xh * r.x;
-          const float pe = fmaf(xh, r.x, -ph) + fmaf(xh, r.y, xl * r.x);
-          const float t = ah[n] + ph;
-          const float bv = t - ah[n];
-          al[n] += ((ah[n] - (t - bv)) + (ph - bv)) + pe;
-          ah[n] = t;
+      for (int r = 0; r < kXrRows; ++r) sx[r * 32 + lane] = split_df(nx[r]);
+      __syncwarp();
+      if (k0 + 32 < K) {
+        const int k = k0 + 32 + lane;
+#pragma unroll
+        for (int r = 0; r < kXrRows; ++r) nx[r] = (m0 + r < M && k < K) ? in[(m0 + r) * K + k] : 0.0;
+      }
+      const int kn = min(32, K - k0);
+      float ah[kXrRows], al[kXrRows];
+#pragma unroll
+      for (int r = 0; r < kXrRows; ++r) { ah[r] = 0.f; al[r] = 0.f; }
+#pragma unroll 2
+      for (int kk = 0; kk < kn; ++kk) {
+        const float2 rv = sR[(k0 + kk) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < kXrRows; ++r) {
+          const float2 xv = sx[r * 32 + kk];  // broadcast
+          const float ph = xv.x * rv.x;
+          const float pe = fmaf(xv.x, rv.x, -ph) + fmaf(xv.x, rv.y, xv.y * rv.x);
+          const float t = ah[r] + ph;
+          const float bv = t - ah[r];
+          al[r] += ((ah[r] - (t - bv)) + (ph - bv)) + pe;
+          ah[r] = t;
         }
       }
-    }
-    double mine = 0.0;
 #pragma unroll
-    for (int n = 0; n < kXrN; ++n) {
-      if (n < N) {
-        float sh = ah[n] + al[n];          // renormalise once
-        float sl = al[n] - (sh - ah[n]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
-          df_add(sh, sl, oh, ol);
-        }
-        if (lane == n) mine = (double)sh + (double)sl;
-      }
+      for (int r = 0; r < kXrRows; ++r) df_add(sh[r], sl[r], ah[r], al[r]);
     }
-    if (lane < N) out[m * N + lane] = mine;
+    if (lane < N) {
+#pragma unroll
+      for (int r = 0; r < kXrRows; ++r)
+        if (m0 + r < M) out[(m0 + r) * N + lane] = (double)sh[r] + (double)sl[r];
+    }
   }
 }
 }  // namespace
@@ -601,14 +627,16 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
   {
     debug_phase(h, "  ooov transform");
     int dims[4] = {No, Nv, Nv, Nv};
-    const size_t smem = sizeof(float2) * (size_t)Nv * (No + 1);
-    if (No <= kXrN && smem <= 200 * 1024) {  // c -> u' (first No columns of Wv)
+    const size_t smem = xr_df_smem(Nv);
+    if (No <= kXrN && smem <= 220 * 1024) {  // c -> u' (first No columns of Wv)
       static size_t attr = 0;
       if (smem > attr) {
         cudaFuncSetAttribute(k_xr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
       }
-      k_xr_df<<<1216, 256, smem, st>>>(ovvv_src, scratch, (int64_t)No * Nv * Nv, Nv, No, h->Wv, Nv);
+      const int64_t M = (int64_t)No * Nv * Nv;
+      const unsigned grid = (unsigned)std::min<int64_t>(1216, cdiv(cdiv(M, kXrRows), kXrWarps));
+      k_xr_df<<<grid, kXrWarps * 32, smem, st>>>(ovvv_src, scratch, M, Nv, No, h->Wv, Nv);
       h->launches += 1;
     } else {
       mode_product(ovvv_src, scratch, dims, 3, h->Wv, No, Nv, st);
