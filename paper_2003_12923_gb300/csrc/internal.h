@@ -90,6 +90,8 @@ struct esmp2_handle {
   esmp2::Couplings cp{};
   esmp2::CouplingsT<float> cp32{};
   float *F32 = nullptr;     // float copy of Fsemi (inner solve)
+  float arrow_w[64] = {};   // host copy of F32[l][0] (1 <= l < No) and F32[l][No] (l < No)
+  bool arrow_w_ready = false;
   __half *dinv32 = nullptr; // Jacobi preconditioner in that basis (n halves)
   double *P64 = nullptr;    // x F for the T, S, X, Y blocks (float64 sigma workspace, 4 blocks)
   double *red = nullptr;    // reduction partials

@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace esmp2 {
@@ -218,6 +220,20 @@ esmp2_status ensure_mixed(esmp2_handle *h, bool semi) {
   debug_phase(h, "  mixed: rhs rotation");
   k_f64_to_f32<<<64, 256, 0, h->stream>>>(h->Fsemi, h->F32, (int64_t)N * N);
   h->launches += 1;
+  {  // the t and t' columns of the occupied rows, as the float copy holds them (launch weights)
+    std::vector<double> rows((size_t)No * N);
+    e = cudaMemcpyAsync(rows.data(), h->Fsemi, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      dfree(V, h->stream); dfree(work, h->stream); dfree(W2, h->stream); dfree(T1, h->stream);
+      return check_cuda(h, e, "mixed set-up");
+    }
+    for (int l = 0; l < 32; ++l) {
+      h->arrow_w[l] = (l >= 1 && l < No) ? (float)rows[(size_t)l * N] : 0.f;
+      h->arrow_w[32 + l] = l < No ? (float)rows[(size_t)l * N + No] : 0.f;
+    }
+    h->arrow_w_ready = true;
+  }
   dfree(V, h->stream); dfree(work, h->stream); dfree(W2, h->stream); dfree(T1, h->stream);
   h->mixed_ready = true;
   return check_cuda(h, cudaGetLastError(), "mixed set-up");

@@ -288,63 +288,80 @@ __device__ __forceinline__ bool valid_elem(int blk, int i, int j, int a, int b) 
 // b = Q H Psi0 on the stored blocks (Slater-Condon rules with Psi0 = sum_u lam_u (u -> u')):
 //  doubles: P(ij)P(ab)[s_ia f0_bj] + P(ij) sum_c <ab||cj> s_ic - P(ab) sum_k <kb||ij> s_ka
 //  triples: P(k/ij)P(c/ab)[<ab||ij> s_kc]  (disconnected product of the double and the single)
-__global__ void k_rhs(const double *lam, const double *f0, const double *ovov, const double *ooov,
-                      const double *ovvt, double *out, int No, int Nv) {
-  const int64_t B = (int64_t)No * No * Nv * Nv;
-  const int64_t n = 5 * B;
-  const int64_t sNv = Nv;
+//  Q[i][u][b][a] = (ia|bu'): the OVVT integrals with the last two index pairs moved so
+//  that one of the two OVVT terms of every T/S element runs along b; the other (a and b
+//  exchanged) is staged through shared memory.  One CTA per (block, i, j, 32-row strip of
+//  a), b in tiles of 32.
+__global__ void __launch_bounds__(256) k_rhs(const double *lam, const double *f0, const double *ovov,
+                                             const double *ooov, const double *Q, double *out, int No, int Nv) {
+  __shared__ double tji[32][33], tij[32][33];
+  const int64_t sNv = Nv, NvNv = (int64_t)Nv * Nv;
+  const int blk = blockIdx.z, i = blockIdx.y / No, j = blockIdx.y % No, a0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #define OVOV(i, a, j, b) ovov[(((int64_t)(i) * sNv + (a)) * No + (j)) * sNv + (b)]
 #define OOOV(i, j, k, a) ooov[(((int64_t)(i) * No + (j)) * No + (k)) * sNv + (a)]
-#define OVVT(i, a, b, u) ovvt[(((int64_t)(i) * sNv + (a)) * sNv + (b)) * No + (u)]
 #define F0(a, j) f0[(int64_t)(a) * No + (j)]
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t f = e;
-    const int b = (int)(f % Nv); f /= Nv;
-    const int a = (int)(f % Nv); f /= Nv;
-    const int j = (int)(f % No); f /= No;
-    const int i = (int)(f % No); f /= No;
-    const int blk = (int)f;
-    double v = 0.0;
-    if (valid_elem(blk, i, j, a, b)) {
-      const double l0 = lam[0];
-      if (blk == BT) {
-        if (a == i) v += lam[i] * F0(b, j);
-        if (a == j) v -= lam[j] * F0(b, i);
-        if (b == i) v -= lam[i] * F0(a, j);
-        if (b == j) v += lam[j] * F0(a, i);
-        v += lam[i] * (OVVT(j, b, a, i) - OVVT(j, a, b, i)) - lam[j] * (OVVT(i, b, a, j) - OVVT(i, a, b, j));
-        if (a < No) v -= lam[a] * (OOOV(a, i, j, b) - OOOV(a, j, i, b));
-        if (b < No) v += lam[b] * (OOOV(b, i, j, a) - OOOV(b, j, i, a));
-      } else if (blk == BS) {
-        if (a == i) v += lam[i] * F0(b, j);
-        if (b == j) v += lam[j] * F0(a, i);
-        v += lam[i] * OVVT(j, b, a, i) + lam[j] * OVVT(i, a, b, j);
-        if (a < No) v -= lam[a] * OOOV(a, i, j, b);
-        if (b < No) v -= lam[b] * OOOV(b, j, i, a);
-      } else if (blk == BX || blk == BY) {
-        // t j k -> t' b c  (here j,k,b,c = i,j,a,b):  lam_t <bc||jk> + P(jk)P(bc)[lam_k d_ck q(j,b)]
-        v = l0 * (OVOV(i, a, j, b) - OVOV(j, a, i, b));
-        // X: q(j,b) = <t'b||tj> = (t't|bj) - (t'j|bt);  Y: q(j,b) = (t't|bj) (opposite spins)
-        auto q = [&](int jj, int bb) {
-          double r = OVOV(0, 0, jj, bb);
-          if (blk == BX) r -= OVOV(jj, 0, 0, bb);
-          return r;
-        };
-        if (b == j) v += lam[j] * q(i, a);
-        if (b == i) v -= lam[i] * q(j, a);
-        if (a == j) v -= lam[j] * q(i, b);
-        if (a == i) v += lam[i] * q(j, b);
-      } else {  // BZ: i t k -> a t' c  (here k,c = j,b)
-        v = l0 * OVOV(i, a, j, b);
-        if (b == j) v += lam[j] * OVOV(i, a, 0, 0);
-        if (a == i) v += lam[i] * (OVOV(j, b, 0, 0) - OVOV(0, b, j, 0));
+  const double *Qji = Q + ((int64_t)j * No + i) * NvNv;  // Qji[a][b] = OVVT(j, b, a, i)
+  const double *Qij = Q + ((int64_t)i * No + j) * NvNv;  // Qij[a][b] = OVVT(i, b, a, j)
+  double *ys = out + (((int64_t)blk * No + i) * No + j) * NvNv;
+  const double li = lam[i], lj = lam[j], l0 = lam[0];
+  for (int b0 = 0; b0 < Nv; b0 += 32) {
+    if (blk == BT || blk == BS) {  // tji[bb][aa] = OVVT(j, a, b, i), tij[bb][aa] = OVVT(i, a, b, j)
+      __syncthreads();
+      for (int r = ty; r < 32; r += 8) {
+        const int bb = b0 + r, aa = a0 + tx;
+        const bool in = bb < Nv && aa < Nv;
+        tji[r][tx] = in ? Qji[(int64_t)bb * Nv + aa] : 0.0;
+        tij[r][tx] = in ? Qij[(int64_t)bb * Nv + aa] : 0.0;
       }
+      __syncthreads();
     }
-    out[e] = v;
+    const int b = b0 + tx;
+    if (b >= Nv) continue;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int ar = ty + 8 * rr, a = a0 + ar;
+      if (a >= Nv) break;
+      double v = 0.0;
+      if (valid_elem(blk, i, j, a, b)) {
+        if (blk == BT) {
+          if (a == i) v += li * F0(b, j);
+          if (a == j) v -= lj * F0(b, i);
+          if (b == i) v -= li * F0(a, j);
+          if (b == j) v += lj * F0(a, i);
+          v += li * (Qji[(int64_t)a * Nv + b] - tji[tx][ar]) - lj * (Qij[(int64_t)a * Nv + b] - tij[tx][ar]);
+          if (a < No) v -= lam[a] * (OOOV(a, i, j, b) - OOOV(a, j, i, b));
+          if (b < No) v += lam[b] * (OOOV(b, i, j, a) - OOOV(b, j, i, a));
+        } else if (blk == BS) {
+          if (a == i) v += li * F0(b, j);
+          if (b == j) v += lj * F0(a, i);
+          v += li * Qji[(int64_t)a * Nv + b] + lj * tij[tx][ar];
+          if (a < No) v -= lam[a] * OOOV(a, i, j, b);
+          if (b < No) v -= lam[b] * OOOV(b, j, i, a);
+        } else if (blk == BX || blk == BY) {
+          // t j k -> t' b c  (here j,k,b,c = i,j,a,b):  lam_t <bc||jk> + P(jk)P(bc)[lam_k d_ck q(j,b)]
+          v = l0 * (OVOV(i, a, j, b) - OVOV(j, a, i, b));
+          // X: q(j,b) = <t'b||tj> = (t't|bj) - (t'j|bt);  Y: q(j,b) = (t't|bj) (opposite spins)
+          auto q = [&](int jj, int bb) {
+            double r = OVOV(0, 0, jj, bb);
+            if (blk == BX) r -= OVOV(jj, 0, 0, bb);
+            return r;
+          };
+          if (b == j) v += lj * q(i, a);
+          if (b == i) v -= li * q(j, a);
+          if (a == j) v -= lj * q(i, b);
+          if (a == i) v += li * q(j, b);
+        } else {  // BZ: i t k -> a t' c  (here k,c = j,b)
+          v = l0 * OVOV(i, a, j, b);
+          if (b == j) v += lj * OVOV(i, a, 0, 0);
+          if (a == i) v += li * (OVOV(j, b, 0, 0) - OVOV(0, b, j, 0));
+        }
+      }
+      ys[(int64_t)a * Nv + b] = v;
+    }
   }
 #undef OVOV
 #undef OOOV
-#undef OVVT
 #undef F0
 }
 
@@ -580,6 +597,7 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
   cudaStream_t st = h->stream;
   const bool tc = (int64_t)9 * Nv * 1024 < (1LL << 24);   // exact ten-level digit sums (one term)
   esmp2_status s = ESMP2_OK;
+  const double *q_ovvt = nullptr;  // (ia|bu') as [i][u][b][a], for the right-hand side
   {
     const int dims[4] = {No, Nv, No, Nv};
     if (tc) {
@@ -652,6 +670,7 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
       permute4(h, ovvv_in, scratch, d2, 0, 1, 3, 2);                               // [i][u][b][a]
       if ((s = xwv_split(h, scratch, (int64_t)No * No * Nv, ovvv_in))) return s;  // a
       permute4(h, ovvv_in, h->ovvt, d2, 0, 3, 2, 1);                               // [i][a][b][u]
+      q_ovvt = ovvv_in;                                                             // [i][u][b][a]
     } else {
       double *src = scratch, *dst = ovvv_in;
       const double *R[3] = {h->U, h->Wv, h->Wv};
@@ -661,11 +680,15 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
         double *t = src; src = dst; dst = t;
       }
       cudaMemcpyAsync(h->ovvt, src, sizeof(double) * (size_t)No * Nv * Nv * No, cudaMemcpyDeviceToDevice, st);
+      const int d4[4] = {No, Nv, Nv, No};
+      permute4(h, h->ovvt, scratch, d4, 0, 3, 2, 1);                               // [i][u][b][a]
+      q_ovvt = scratch;
     }
   }
   debug_phase(h, "  ovvt rotations");
   k_f0vo<<<(unsigned)cdiv((int64_t)No * Nv, 256), 256, 0, st>>>(h->F, h->lam, h->ooov, h->ovvt, h->f0vo, No, Nv);
-  k_rhs<<<1216, 256, 0, st>>>(h->lam, h->f0vo, h->ovov, h->ooov, h->ovvt, h->b, No, Nv);
+  k_rhs<<<dim3((unsigned)cdiv(Nv, 32), (unsigned)(No * No), 5), 256, 0, st>>>(h->lam, h->f0vo, h->ovov, h->ooov, q_ovvt,
+                                                                               h->b, No, Nv);
   h->launches += 2;
   return check_cuda(h, cudaGetLastError(), "rhs");
 }

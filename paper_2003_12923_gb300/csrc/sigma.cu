@@ -63,6 +63,7 @@ __global__ void k_inter_a(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
     const T *X = x + c.at(BX, 0, 0, 0, 0) + (int64_t)ij * Nv * Nv + b;
     const T *Z = x + c.at(BZ, 0, 0, 0, 0) + (int64_t)ij * Nv * Nv + b;
     CT vx = CT(0), g = CT(0);
+#pragma unroll 8
     for (int cc = 0; cc < Nv; ++cc) {
       const CT xv = (CT)X[(int64_t)cc * Nv], zv = (CT)Z[(int64_t)cc * Nv];
       vx += c.Fov(0, cc) * xv;
@@ -117,6 +118,7 @@ __global__ void k_inter_c(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
     const T *Y = x + c.at(BY, 0, 0, 0, 0) + r * Nv;
     const T *Z = x + c.at(BZ, 0, 0, 0, 0) + r * Nv;
     CT wz = CT(0), hp = CT(0);
+#pragma unroll 4
     for (int cc = lane; cc < Nv; cc += 32) {
       const CT zv = (CT)Z[cc];
       wz += c.Fov(0, cc) * zv;
@@ -146,6 +148,7 @@ __global__ void k_inter_d(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
       for (int k = 0; k < No; ++k) s += cp.HP[((int64_t)p * No + k) * Nv + q];
       cp.H[f] = s;
     } else {
+#pragma unroll 8
       for (int d = 0; d < Nv; ++d) s += c.Fv(0, d) * (CT)x[c.at(BZ, 0, p, d, q)];
       for (int l = 0; l < No; ++l) s -= c.Fo(l, 0) * (CT)x[c.at(BZ, l, p, 0, q)];
       cp.CYZ[f] = s;
@@ -155,19 +158,19 @@ __global__ void k_inter_d(CtxT<CT> c, const T *x, CouplingsT<CT> cp) {
 
 // (b) in one pass for the arrow form (No <= 32): a thread owns one (blk, a, b) and reads
 // the block's No x No occupied matrix at that (a, b) once; its row sums give OC2 (and OZ
-// on Z), its column sums OC1 (and OX on X), the column sums held in registers.
+// on Z), its column sums OC1 (and OX on X), the column sums held in registers.  The
+// weights F_l0 (l >= 1) and F_l,t' travel as launch parameters, so the unrolled sums take
+// them as constant operands instead of registers or shared-memory loads.
 // BLK < 0: grid.y runs over T, S, Y (no OX/OZ terms); else the one block BLK.
+struct ArrowW {
+  float fl[32];  // F_l0 for 1 <= l < No, else 0
+  float fk[32];  // F_l,t' for l < No, else 0
+};
 template <int BLK, typename T, typename CT>
-__global__ void __launch_bounds__(128, 4) k_inter_b1(CtxT<CT> c, const T *__restrict__ x, CouplingsT<CT> cp) {
-  __shared__ CT fl[32], fk[32];
+__global__ void __launch_bounds__(128, 4) k_inter_b1(CtxT<CT> c, const T *__restrict__ x, CouplingsT<CT> cp,
+                                                     const ArrowW w) {
   const int No = c.No;
   const int blk = BLK >= 0 ? BLK : (blockIdx.y == 0 ? BT : (blockIdx.y == 1 ? BS : BY));
-  if (threadIdx.x < 32) {
-    const int l = threadIdx.x;
-    fl[l] = (l >= 1 && l < No) ? c.Fo(l, 0) : CT(0);
-    fk[l] = l < No ? c.Fov(l, 0) : CT(0);
-  }
-  __syncthreads();
   const int64_t NvNv = (int64_t)c.Nv * c.Nv, n = (int64_t)No * NvNv;
   const T *xb = x + blk * c.B;
   CT *oc1 = cp.OC1 + blk * n, *oc2 = cp.OC2 + blk * n;
@@ -180,16 +183,16 @@ __global__ void __launch_bounds__(128, 4) k_inter_b1(CtxT<CT> c, const T *__rest
     for (int m = 0; m < (BLK == BX ? 32 : 1); ++m) ox[m] = CT(0);
     for (int l = 0; l < No; ++l) {
       const T *row = xb + (int64_t)l * n + ab;
-      const CT fll = fl[l], fkl = fk[l];
+      const CT fll = w.fl[l], fkl = w.fk[l];
       CT r2 = CT(0), rz = CT(0);
 #pragma unroll
       for (int m = 0; m < 32; ++m) {
         if (m < No) {
           const CT v = (CT)row[(int64_t)m * NvNv];
           o1[m] += fll * v;
-          r2 += fl[m] * v;
+          r2 += w.fl[m] * v;
           if constexpr (BLK == BX) ox[m] += fkl * v;
-          if constexpr (BLK == BZ) rz += fk[m] * v;
+          if constexpr (BLK == BZ) rz += w.fk[m] * v;
         }
       }
       oc2[(int64_t)l * NvNv + ab] = r2;
@@ -209,13 +212,15 @@ template <typename T, typename CT>
 void launch_inter(esmp2_handle *h, const CtxT<CT> &c, const T *x, const CouplingsT<CT> &cp) {
   k_inter_a<T, CT><<<1216, 256, 0, h->stream>>>(c, x, cp);
   bool one_pass = false;
-  if constexpr (sizeof(CT) == 4) one_pass = c.arrow && c.No <= 32;
+  if constexpr (sizeof(CT) == 4) one_pass = c.arrow && c.No <= 32 && h->arrow_w_ready;
   if (one_pass) {
     if constexpr (sizeof(CT) == 4) {
+      ArrowW w;
+      for (int l = 0; l < 32; ++l) { w.fl[l] = h->arrow_w[l]; w.fk[l] = h->arrow_w[32 + l]; }
       const unsigned gx = (unsigned)std::min<int64_t>(cdiv((int64_t)c.Nv * c.Nv, 128), 8192);
-      k_inter_b1<-1, T, CT><<<dim3(gx, 3), 128, 0, h->stream>>>(c, x, cp);
-      k_inter_b1<BX, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp);
-      k_inter_b1<BZ, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp);
+      k_inter_b1<-1, T, CT><<<dim3(gx, 3), 128, 0, h->stream>>>(c, x, cp, w);
+      k_inter_b1<BX, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp, w);
+      k_inter_b1<BZ, T, CT><<<gx, 128, 0, h->stream>>>(c, x, cp, w);
       h->launches += 2;
     }
   } else {
