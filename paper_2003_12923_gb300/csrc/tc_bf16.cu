@@ -147,6 +147,9 @@ struct Args {
   int64_t tiles;     // nslices * a_tiles * b_tiles
   int npairs;        // operand pairs accumulated into one tile (digit products of one level)
   int dx[9], df[9];  // digit plane of x and of F for each pair
+  int lmin, lmax;    // lmax > 0: every tile runs levels lmin..lmax in turn (mode 1), level L
+                     // pairing x digit p with F digit L - 2 - p (p = 0 .. L - 2) in one
+                     // accumulator round; dx, df and level unused, npairs the total pairs
   int S_plane;       // slices per digit plane of x
   int mode;          // 0: fp32 store into y32; 1: float64 (y64 | p64) (+)= 2^(es[s] + eF - 6 level) acc
   float *y32;        // [S][Nv][Nv]
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_after();
   const uint32_t tmem = tmem_base;
   const int per_slice = g.a_tiles * g.b_tiles;
+  const int nlev = g.lmax ? g.lmax - g.lmin + 1 : 1;  // work items (accumulator rounds) per tile
 
   if (warp == 0) {
     if (lane == 0) {  // ------------------------------------------------ TMA producer
@@ -202,8 +206,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
         const int terms = terms_of(g, s);
         const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
-        for (int pr = 0; pr < g.npairs && ok; ++pr) {
-          const int zx = g.dx[pr] * g.S_plane + s, zf = g.df[pr];
+        for (int lv = 0; lv < nlev && ok; ++lv) {
+        const int L = g.lmax ? g.lmin + lv : g.level, np = g.lmax ? L - 1 : g.npairs;
+        for (int pr = 0; pr < np && ok; ++pr) {
+          const int zx = (g.lmax ? pr : g.dx[pr]) * g.S_plane + s, zf = g.lmax ? L - 2 - pr : g.df[pr];
           for (int kc = 0; kc < g.nk && ok; ++kc) {
             const int c0 = kc * BK;
             for (int term = 1; term <= 2; ++term, ++it) {   // 1: x F, 2: F x
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
         }
+        }
       }
       if (!ok) atomicExch(&fail, 1);
       // wait (bounded) until no copy of this CTA is still in flight
@@ -236,20 +243,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t it = 0;
       int lt = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++lt) {
+      for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
         const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
         const int terms = terms_of(g, s);
         const int b0 = (rem % g.b_tiles) * g.bn;
         const int nvalid = min(g.bn, g.Nv - b0);
         const int nmma = (nvalid + 15) & ~15;
         const uint32_t id2 = idesc_bf16(BM, nmma, 0), id1 = idesc_bf16(BM, nmma, 1);
+        for (int lv = 0; lv < nlev && ok; ++lv, ++lt) {
+        const int np = g.lmax ? g.lmin + lv - 1 : g.npairs;
         const int ab = lt & 1;
         const uint32_t ar = (uint32_t)(lt >> 1);
         if (!mbar_wait(&acc_empty[ab], (ar & 1) ^ 1)) { ok = false; break; }
         tc_after();
         const uint32_t d = tmem + (uint32_t)(ab * BN_MAX);
         bool first = true;
-        for (int pr = 0; pr < g.npairs && ok; ++pr) {
+        for (int pr = 0; pr < np && ok; ++pr) {
           for (int kc = 0; kc < g.nk && ok; ++kc) {
             const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);
             for (int term = 1; term <= 2; ++term, ++it) {
@@ -272,6 +281,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok) break;
         umma_commit(&acc_full[ab]);
+        }
       }
       if (!ok) atomicExch(&fail, 1);
     }
@@ -280,14 +290,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // a lane quarter split the tile's columns
     const int quarter = warp & 3, chalf = (warp - 2) >> 2;
     int lt = 0;
-    for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x, ++lt) {
+    bool stop = false;
+    for (int64_t t = blockIdx.x; t < g.tiles && !stop; t += gridDim.x) {
       const int s = slice_of(g, t / per_slice), rem = (int)(t % per_slice);
       const int a0 = (rem / g.b_tiles) * BM, b0 = (rem % g.b_tiles) * g.bn;
       const int nvalid = min(g.bn, g.Nv - b0);
+      for (int lv = 0; lv < nlev; ++lv, ++lt) {
+      const int L = g.lmax ? g.lmin + lv : g.level;
+      const bool first = g.first && lv == 0;
       const int ab = lt & 1;
       const uint32_t ar = (uint32_t)(lt >> 1);
       const bool got = mbar_wait(&acc_full[ab], ar & 1);
-      if (!got) { if (lane == 0) atomicExch(&fail, 1); break; }
+      if (!got) { if (lane == 0) atomicExch(&fail, 1); stop = true; break; }
       tc_after();
       const int row = quarter * 32 + lane;
       const int a = a0 + row;
@@ -310,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tmem_ld16(taddr + (uint32_t)c, v);
           if (a < g.Nv) {
             const int m = min(16, nvalid - c);
-            if (!g.first)
+            if (!first)
               for (int q = 0; q < m; ++q) v[q] += dst[c + q];   // second pass of a split slice
             if (m == 16 && (g.Nv & 3) == 0) {
               float4 *d4 = reinterpret_cast<float4 *>(dst + c);
@@ -333,7 +347,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // every accumulator value is an integer below 2^24 (exact in fp32); the float64
         // sum over levels is the only rounding step
         double *dst = (g.to_p64[s / g.per_block] ? g.p64 : g.y64) + off;
-        const double scale = ldexp(1.0, g.es[s] + g.eF - 6 * g.level);
+        const double scale = ldexp(1.0, g.es[s] + g.eF - 6 * L);
         for (int c = c_begin; c < c_end; c += 16) {
           float v[16];
           tmem_ld16(taddr + (uint32_t)c, v);
@@ -343,13 +357,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               double2 *d2 = reinterpret_cast<double2 *>(dst + c);
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                double2 o = g.first ? make_double2(0.0, 0.0) : d2[q];
+                double2 o = first ? make_double2(0.0, 0.0) : d2[q];
                 o.x += (double)v[2 * q] * scale;
                 o.y += (double)v[2 * q + 1] * scale;
                 d2[q] = o;
               }
             } else {
-              for (int q = 0; q < m; ++q) dst[c + q] = (g.first ? 0.0 : dst[c + q]) + (double)v[q] * scale;
+              for (int q = 0; q < m; ++q) dst[c + q] = (first ? 0.0 : dst[c + q]) + (double)v[q] * scale;
             }
           }
         }
@@ -357,6 +371,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
+      }
     }
   }
   tc_before();
@@ -741,7 +756,8 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
   h->launches += 2;
   const bool split = sym && split_terms();
   const int half = No * (No - 1) / 2;
-  for (int L = 2; L <= levels; ++L) {
+  {  // every level 2 .. levels of every tile in one launch per pass
+   const int L = levels;
    for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
     tc::Args g{};
     g.Nv = Nv;
@@ -754,19 +770,15 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
       g.to_p64[b] = sym && txy;
     }
     g.S_plane = S;
-    g.npairs = 0;
-    for (int p = 1; p < L; ++p) {
-      g.dx[g.npairs] = p - 1;     // digit p of x with digit L - p of F
-      g.df[g.npairs] = L - p - 1;
-      ++g.npairs;
-    }
+    g.lmin = 2;                   // level l pairs digit p of x with digit l - p of F
+    g.lmax = L;
+    g.npairs = L * (L - 1) / 2;   // pairs over all levels (flop accounting)
     g.mode = 1;
     g.y64 = y;
     g.p64 = p64;
     g.es = h->es;
     g.eF = h->eF;
-    g.level = L;
-    g.first = (L == 2 && pass == 0);
+    g.first = (pass == 0);
     g.err = h->dflag;
     const double nv3 = (double)Nv * Nv * Nv;
     double per_pair = 4.0 * nv3 * S, alg_pair = per_pair;
@@ -814,7 +826,7 @@ esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y
   tc::k_digits<<<1216, 256, 0, h->stream>>>(X, S, Nv, Nv, Nvp, Nv, NvNv, h->es, P,
                                             static_cast<__nv_bfloat16 *>(h->xdig));
   h->launches += 2;
-  for (int L = 2; L <= levels; ++L) {
+  {  // levels 2 .. levels of every tile in one launch
     tc::Args g{};
     g.Nv = Nv;
     g.nslices = S;
@@ -822,19 +834,15 @@ esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y
     g.per_block = S;
     for (int b = 0; b < 5; ++b) { g.tm[b] = 1; g.to_p64[b] = 1; }
     g.S_plane = S;
-    g.npairs = 0;
-    for (int p = 1; p < L; ++p) {
-      g.dx[g.npairs] = p - 1;
-      g.df[g.npairs] = L - p - 1;
-      ++g.npairs;
-    }
+    g.lmin = 2;
+    g.lmax = levels;
+    g.npairs = levels * (levels - 1) / 2;   // pairs over all levels (flop accounting)
     g.mode = 1;
     g.y64 = nullptr;
     g.p64 = Y;
     g.es = h->es;
     g.eF = h->eR;
-    g.level = L;
-    g.first = (L == 2);
+    g.first = 1;
     g.err = h->dflag;
     const double fl = 2.0 * g.npairs * (double)rows * Nv * Nv;
     if (const char *m = launch_virt(h->stream, h->xdig, P, h->Rdig, P, g, fl, fl)) {
