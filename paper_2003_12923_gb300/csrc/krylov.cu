@@ -338,13 +338,24 @@ __global__ void k_dinv32(VCtx c, __half *dinv) {
 }
 
 // r = -b - q (fp64 true residual); partials <r,r>, <b,b>
-__global__ void k_residual(VCtx c, const double *b, const double *q, double *r, double *red) {
+// r = -b - q (q == nullptr: q = 0); partials <r, r>_w and, with with_b, <b, b>_w.  Block by
+// block (no per-element index arithmetic), weights applied to the block sums: float64 runs
+// at a small fraction of the float32 rate on GB300, so the pass keeps to one add and one or
+// two fused multiply-adds per element.
+__global__ void k_residual(VCtx c, const double *b, const double *q, double *r, double *red, int with_b) {
   double v[2] = {0.0, 0.0};
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = -b[e] - q[e], w = c.w(e);
-    r[e] = ri;
-    v[0] += w * ri * ri;
-    v[1] += w * b[e] * b[e];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int blk = 0; blk < 5; ++blk) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
+      const double bi = b[e], ri = q ? -bi - q[e] : -bi;
+      r[e] = ri;
+      s0 = fma(ri, ri, s0);
+      if (with_b) s1 = fma(bi, bi, s1);
+    }
+    const double w = blk == 1 ? 1.0 : (blk == 4 ? 2.0 : 0.5);
+    v[0] += w * s0;
+    v[1] += w * s1;
   }
   block_partials<2>(v, red);
 }
@@ -805,22 +816,23 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // levels follow the relative residual it is expected to show (a low estimate, so never
   // too few levels); the residual that ends the refinement, and feeds the energy, always
   // takes the full count.
-  double rho_next = 0.0;
+  double rho_next = 0.0, bb = -1.0;  // bb: <b, b>_w, taken with the first residual
   while (true) {
     int lv_k = lv;
     if (lv && rho_next > 1e1 * tol) lv_k = std::min(lv, split_levels_for(rho_next));
-    if (outer == 0 && h->x_zero) {  // cold start: the first true residual is b itself
-      cudaMemsetAsync(q, 0, sizeof(double) * h->d.n, st);
+    const bool cold = outer == 0 && h->x_zero;  // cold start: the first true residual is -b
+    if (cold) {
       lv_k = lv;
     } else {
       if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k))) return s;
       ++nsig64;
     }
-    k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, q, r, h->red);
+    k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, cold ? nullptr : q, r, h->red, bb < 0.0 ? 1 : 0);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 3);
     h->launches += 2;
     if ((s = read_slots(h, sl, 32))) return s;
-    const double rn = std::sqrt(sl[8]), bn = std::sqrt(sl[9]);
+    if (bb < 0.0) bb = sl[9];
+    const double rn = std::sqrt(sl[8]), bn = std::sqrt(bb);
     relres = bn > 0 ? rn / bn : 0.0;
     if (std::getenv("ESMP2_DEBUG"))
       std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d levels %d\n", outer, relres, inner_total, lv_k);

@@ -290,6 +290,9 @@ __global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, c
   const CT om = c.omega, shift = c.Fv(0, 0) - c.Fo(0, 0), f00 = c.Fov(0, 0);
   const CT fdiag = c.Fo(i, i) + c.Fo(j, j), foi = c.Fo(0, i), foj = c.Fo(0, j);
   const CT fio = c.Fov(i, 0), fjo = c.Fov(j, 0);
+  // every diagonal term of the element in one coefficient: -omega, the pair energy of the
+  // L blocks, and in the arrow form -(F_ii + F_jj)
+  const CT cxe = -om + (BLK >= BX ? shift : CT(0)) - (c.arrow ? fdiag : CT(0));
   const TX *A0j = S(BLK, 0, j), *Ai0 = S(BLK, i, 0);
   const CT *OC1 = c.arrow ? cp.OC1 + ((int64_t)BLK * No + j) * NvNv : nullptr;
   const CT *OC2 = c.arrow ? cp.OC2 + ((int64_t)BLK * No + i) * NvNv : nullptr;
@@ -350,13 +353,13 @@ __global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, c
       ldv<VW>(xs + ab, xe);
       ldv<VW>(ys + ab, yo);  // issued with x: one memory round trip per row
 #pragma unroll
-      for (int k = 0; k < VW; ++k) v[k] = -om * xe[k];
+      for (int k = 0; k < VW; ++k) v[k] = cxe * xe[k];
       if (c.arrow) {  // - sum_l F_li x[l][j] - sum_l F_lj x[i][l] with F_oo diagonal off the t row/column
         if (i0) ldv<VW>(OC1 + ab, t1); else ldv<VW>(A0j + ab, t1);
         if (j0) ldv<VW>(OC2 + ab, t2); else ldv<VW>(Ai0 + ab, t2);
         const CT s1 = i0 ? CT(1) : foi, s2 = j0 ? CT(1) : foj;
 #pragma unroll
-        for (int k = 0; k < VW; ++k) v[k] -= fdiag * xe[k] + s1 * t1[k] + s2 * t2[k];
+        for (int k = 0; k < VW; ++k) v[k] -= s1 * t1[k] + s2 * t2[k];
       }
       if constexpr (BLK == BT) {
         ldv<VW>(S(BX, i, j) + ab, t1);
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, c
         ldv<VW>(T + ab, Tab); ldv<VW>(T0j + ab, T0jab); ldv<VW>(T0i + ab, T0iab);
 #pragma unroll
         for (int k = 0; k < VW; ++k)  // h1 = T_ij row 0, h2 = T_0j row 0, h3 = T_0i row 0 at b
-          v[k] += shift * xe[k] + f00 * Tab[k] - foa_0 * h1[k] + fob_0[k] * Ta - fio * T0jab[k] + fjo * T0iab[k]
+          v[k] += f00 * Tab[k] - foa_0 * h1[k] + fob_0[k] * Ta - fio * T0jab[k] + fjo * T0iab[k]
                 + foa_i * h2[k] - foa_j * h3[k] - fob_i[k] * T0ja + fob_j[k] * T0ia;
       } else if constexpr (BLK == BY) {
         const TX *S0i = S(BS, 0, i), *S0j = S(BS, 0, j);
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, c
         ldv<VW>(S(BT, i, j) + ab, Tab);
 #pragma unroll
         for (int k = 0; k < VW; ++k)  // h1 = S_0i row 0, h2 = S_0j row 0 at b
-          v[k] += shift * xe[k] + f00 * Tab[k] + fob_j[k] * S0ia - fob_i[k] * S0ja - foa_j * h1[k] + foa_i * h2[k];
+          v[k] += f00 * Tab[k] + fob_j[k] * S0ia - fob_i[k] * S0ja - foa_j * h1[k] + foa_i * h2[k];
         if (i0 && a0f) { ldv<VW>(cp.CYZ + j * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] += t1[k]; }
         if (j0 && a0f) { ldv<VW>(cp.CYZ + i * Nv + b, t1); for (int k = 0; k < VW; ++k) v[k] -= t1[k]; }
         if (b == 0) {
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(256, BLK == BX ? 2 : 3) k_couple(CtxT<CT> c, c
         ldv<VW>(Sij + ab, Sijab); ldv<VW>(Si0 + ab, Si0ab);
 #pragma unroll
         for (int k = 0; k < VW; ++k) {  // h1 = T_0j row 0, h2 = Y_0j row 0 at b
-          v[k] += shift * xe[k] + f00 * Sijab[k] - fob_0[k] * Sija0 - fjo * Si0ab[k] + fob_j[k] * Si0a0
+          v[k] += f00 * Sijab[k] - fob_0[k] * Sija0 - fjo * Si0ab[k] + fob_j[k] * Si0a0
                 + foa_i * h1[k];
           if (i0) v[k] += fva * h2[k];
           if (a0f) v[k] -= foi * h2[k];
