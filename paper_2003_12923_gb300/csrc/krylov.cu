@@ -500,25 +500,29 @@ __global__ void k_e2s_a(SCtx s, SDf gd, double *red) {
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
     dflt acc = {0.f, 0.f};
     for (int c = 1; c < Nv; ++c) {
-      if (c == u) continue;
+      if (c == u || c == j || c == k) continue;
       const dflt Dc = df_of(Dh + s.Fv(c));
-      const bool cjk = (c == j || c == k);
       for (int b = threadIdx.x; b < c; b += blockDim.x) {
-        if (b == u) continue;
-        if (cjk || b == j || b == k) {
-          const bool pj = (b == j || c == j), pk = (b == k || c == k);
-          if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
-          if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
-          const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
-          v[0] += s.term(ho, hs, po, ps);
-          continue;
-        }
+        if (b == u || b == j || b == k) continue;
         const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
         const float2 f = fv[b];
         acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
       }
     }
     v[0] += df_to_double(acc);
+    // virtual pairs (b < c) holding j or k: the general float64 form, spread over the
+    // threads (one term per thread at a time, no lane waiting on another's float64 work)
+    for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
+      const int x = e < Nv ? j : k, y = e % Nv;
+      if (y == x || ((y == j || y == k) && x != j)) continue;  // the pair (j, k) once
+      const int b = min(x, y), c = max(x, y);
+      if (c < 1 || c == u || b == u) continue;
+      const bool pj = (b == j || c == j), pk = (b == k || c == k);
+      if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
+      if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
+      const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
+      v[0] += s.term(ho, hs, po, ps);
+    }
   }
   block_partials<1>(v, red);
 }
@@ -538,21 +542,26 @@ __global__ void k_e2s_b(SCtx s, SDf gd, double *red) {
     const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
     dflt acc = {0.f, 0.f};
     for (int c = 1; c < Nv; ++c) {
+      if (c == j || c == k) continue;
       const dflt Dc = df_of(Dh + s.Fv(c));
-      const bool cjk = (c == j || c == k);
       for (int b = threadIdx.x; b < c; b += blockDim.x) {
-        if (cjk || b == j || b == k) {
-          if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
-          const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
-          v[0] += s.term(ho, hs, po, ps);
-          continue;
-        }
+        if (b == j || b == k) continue;
         const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
         const float2 f = fv[b];
         acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
       }
     }
     v[0] += df_to_double(acc);
+    // virtual pairs (b < c) holding j or k: general float64 form spread over the threads
+    for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
+      const int x = e < Nv ? j : k, y = e % Nv;
+      if (y == x || ((y == j || y == k) && x != j)) continue;  // the pair (j, k) once
+      const int b = min(x, y), c = max(x, y);
+      if (c < 1) continue;
+      if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
+      const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
+      v[0] += s.term(ho, hs, po, ps);
+    }
   }
   block_partials<1>(v, red);
 }
@@ -572,17 +581,15 @@ __global__ void k_e2s_c(SCtx s, SDf gd, double *red) {
     const dflt c2 = df_of(-2.0 * lu * lu);
     const double Dh = s.Fv(u) - s.Fo(i) - s.Fo(u) - s.Fo(k) - s.omega;
     dflt acc = {0.f, 0.f};
-    for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
-      if (c == u) continue;
-      if (c == k) {
-        if (k < u || k == 0) continue;
-        for (int a = 0; a < Nv; ++a) {
-          if (a == i) continue;
-          const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, c}, ps[3] = {0, 1, 1};
-          v[0] += s.term(ho, hs, po, ps);
-        }
-        continue;
+    if (k >= u && k != 0) {  // c == k: the general float64 form, a spread over the threads
+      for (int a = threadIdx.x; a < Nv; a += blockDim.x) {
+        if (a == i) continue;
+        const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, k}, ps[3] = {0, 1, 1};
+        v[0] += s.term(ho, hs, po, ps);
       }
+    }
+    for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
+      if (c == u || c == k) continue;
       const dflt Dc = df_of(Dh + s.Fv(c));
       for (int a = 0; a < Nv; ++a) {
         if (a == i) continue;
