@@ -132,7 +132,9 @@ namespace esmp2 {
 esmp2_status setup_top_basis(esmp2_handle *h);
 esmp2_status setup_rhs(esmp2_handle *h);
 esmp2_status sigma64(esmp2_handle *h, const double *x, double *y, int tc_levels = 0);
-esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels = 0);
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels = 0,
+                       int couplings = 1);
+void couple_f32_into(esmp2_handle *h, const double *x, double *y);
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
 esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int mode);
 void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);

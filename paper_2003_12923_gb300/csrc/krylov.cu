@@ -831,7 +831,11 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (cold) {
       lv_k = lv;
     } else {
-      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k))) return s;
+      // far from the tolerance the coupling pass runs in float32 (its ~1e-7 relative error
+      // is a small fraction of the residual it feeds), next to reduced digit levels
+      const bool c32 = lv_k < lv && rho_next >= 1e-5;
+      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k, c32 ? 0 : 1))) return s;
+      if (c32) couple_f32_into(h, x, q);
       ++nsig64;
     }
     k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, cold ? nullptr : q, r, h->red, bb < 0.0 ? 1 : 0);

@@ -745,12 +745,54 @@ void combine_sym(esmp2_handle *h, double *y) {
   h->launches += 1;
 }
 
+namespace {
+__global__ void k_round_f32(const double *src, float *dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+// y += (double) y32 on amplitude slots, y = 0 on the others; a warp per row (block, i, j, a)
+__global__ void k_add_f32_masked(const float *src, double *dst, int No, int Nv) {
+  const int64_t rows = 5LL * No * No * Nv;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int a = (int)(r % Nv);
+    int64_t f = r / Nv;
+    const int j = (int)(f % No);
+    f /= No;
+    const int i = (int)(f % No), blk = (int)(f / No);
+    for (int b = lane; b < Nv; b += 32) {
+      const int64_t e = r * Nv + b;
+      dst[e] = valid_elem(blk, i, j, a, b) ? dst[e] + (double)src[e] : 0.0;
+    }
+  }
+}
+}  // namespace
+
+// Couplings, shifts, arrow terms and masks of y = A x in float32, added to the float64 y
+// (semicanonical-occupied basis): x rounded to float into the inner p buffer, the inner
+// coupling pass on it into the inner q buffer, the result added in float64 and the
+// non-amplitude slots cleared.  For the intermediate true residuals of the refinement,
+// which need A x to about 1e-7 of |A x| only; the float64 coupling pass runs at the
+// float64 rate.
+void couple_f32_into(esmp2_handle *h, const double *x, double *y) {
+  const int64_t n = h->d.n;
+  k_round_f32<<<1216, 256, 0, h->stream>>>(x, h->p32, n);
+  cudaMemsetAsync(h->q32, 0, sizeof(float) * (size_t)n, h->stream);
+  couple32(h, h->F32, h->p32, h->q32);
+  k_add_f32_masked<<<1216, 256, 0, h->stream>>>(h->q32, y, h->d.No, h->d.Nv);
+  h->launches += 2;
+}
+
 // float64 sigma with an arbitrary orthonormal-basis Fock matrix F (t = occupied 0, t' =
 // virtual 0).  arrow = 1 when F_oo is diagonal apart from its t row and column: then the
 // occupied-index terms are applied element-wise instead of by GEMM.
 // tc_levels >= 2: the virtual-index terms come from exact digit products on the tensor
 // cores, digit levels 2 .. tc_levels (F_vv of the handle); 0: float64 GEMMs with F.
-esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels) {
+// couplings = 0 (arrow form only): stop after the index contractions (the caller adds the
+// coupling pass).
+esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels,
+                       int couplings) {
   if (!h->P64) {
     cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->P64), sizeof(double) * 4 * (size_t)h->d.B, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "sigma64 workspace");
@@ -763,8 +805,10 @@ esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double
     virt64_sym(h, F, x, y);
   }
   if (!arrow) contractions64(h, F, x, y, 2);
-  launch_intermediates64(h, F, arrow, x);
-  launch_couple64(h, F, arrow, x, y);
+  if (couplings || !arrow) {
+    launch_intermediates64(h, F, arrow, x);
+    launch_couple64(h, F, arrow, x, y);
+  }
   return check_cuda(h, cudaGetLastError(), "sigma64");
 }
 
