@@ -152,6 +152,9 @@ esmp2_status esmp2_rhs(esmp2_handle *h, double *b);
  * (Sec. III.A uses CG).  ESMP2_FP64: plain fp64 PCG.  ESMP2_MIXED_BF16: fp64
  * iterative refinement, each step solving the correction with bf16/fp32 inner
  * PCG.  Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
+ * (Mixed: intermediate true residuals far from tol take fewer exact digit levels and a
+ * float32 coupling pass, accurate relative to their own size; the residual that stops
+ * the solve, and that the energy reuses, is float64-accurate throughout.)
  * Errors: NOT_CONVERGED (maxit CG iterations in total), INDEFINITE, CUDA.
  * The solution stays on the device (esmp2_get_solution); a later solve warm-starts
  * from it. */
