@@ -166,6 +166,14 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
             "t_sigma_s": t_sigma, "n_sigma": n_sigma, "wall_s": time.time() - t0}
 
 
+def max_over_ranks(value, dist, device):
+    """Largest per-rank float over the process group: the whole job's time."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     if args.config not in WORKLOADS:
         print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-instance configs"}))
@@ -339,9 +347,7 @@ def main():
     esmp2.kernel_timing(False)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, dev)
     tts = elapsed / args.steps
 
     # dominant kernel family of the timed region, from its own CUDA events
