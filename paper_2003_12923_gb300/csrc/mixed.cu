@@ -57,7 +57,7 @@ __global__ void k_build_rot(const double *V, int No, int Nv, double *R, double *
 // float64 operand is split into two floats (hi + lo); products are formed with the exact
 // product error (fma) and summed with Knuth's two-sum, so the float32 pipes do the work at
 // about 2^-46 relative accuracy; the float64 result is hi + lo.  The orbital rotations have
-// only No multiply-adds per element, which on this part would otherwise be float64-bound.
+// only No multiply-adds per element, which on GB300 would otherwise be float64-bound.
 constexpr int kDfK = 32;
 
 __global__ void __launch_bounds__(256) k_mode_df(const double *in, double *out, int64_t P, int K, int64_t Q,

@@ -494,7 +494,7 @@ void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *
 }
 
 // float coupling + arrow occupied pass of the inner (low-precision) sigma: float arithmetic
-// throughout (float64 runs at a small fraction of the float32 rate on this part).
+// throughout (float64 runs at a small fraction of the float32 rate on GB300).
 int64_t couple_dot_parts(const esmp2_handle *h) {
   return 5 * cdiv(h->d.Nv, 32) * h->d.No * h->d.No;
 }
