@@ -29,13 +29,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ESMP2 time-to-solution (res<1e-8) & sigma TFLOP/s at No=30 Nv=400, mixed vs FP64"
 WORKLOADS = {
-    # name: (No, Nv, seed, sigma_off)
-    "c3": (30, 400, 3, 1e-3),
-    "c2": (20, 200, 1, 1e-3),
-    "c1": (6, 30, 0, 1e-3),
+    # name: (No, Nv, seed, sigma_off, default precision, default tol)
+    "c3": (30, 400, 3, 1e-3, "mixed", 1e-8),
+    "c3_off1e-4": (30, 400, 2, 1e-4, "mixed", 1e-8),   # conditioning sweep of the off-diagonal Fock
+    "c3_off1e-2": (30, 400, 4, 1e-2, "mixed", 1e-8),
+    "c2": (20, 200, 1, 1e-3, "fp64", 1e-10),
+    "c1": (6, 30, 0, 1e-3, "fp64", 1e-10),
 }
-NOMINAL_FP64_TFLOPS = 1.25      # GB300 float64 (CUDA-core) nominal rate
-NOMINAL_BF16_TFLOPS = 2250.0
+# stored oracle energies (written by tests/golden/make_o2_reference.py from oracle/ alone)
+GOLDEN = {"c2": "tests/golden/o2_e2_c2.json"}
+# DRAM traffic per launch of a kernel, from one ncu capture of the named profile summary;
+# valid only while the kernel's source file is byte-identical to the captured one (sha256
+# prefix), else reported as null
+TRAFFIC = {}
 
 
 def comb2(n):
@@ -56,6 +62,61 @@ def sigma_flops(No, Nv):
     n = unique_amplitudes(No, Nv)
     return {"alg_total": 4.0 * n * (No + Nv), "alg_virtual": 4.0 * n * Nv,
             "exec_virtual": 20.0 * No * No * Nv ** 3, "exec_total": 20.0 * No * No * Nv * Nv * (No + Nv)}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def measure_fp64_peak(dev):
+    """Float64 GEMM rate of this GPU (cuBLAS through torch.matmul, 4096^3, best of 3, CUDA
+    events): the denominator for kernels bound by the float64 pipe."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def kernel_traffic(kernel):
+    ent = TRAFFIC.get(kernel)
+    if not ent:
+        return None, None
+    import hashlib
+    path = os.path.join(ROOT, ent["source"])
+    try:
+        h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None, None
+    if h != ent["sha256_16"]:
+        return None, f"{ent['profile']} (kernel changed since the capture: traffic not reported)"
+    return ent, ent["profile"]
 
 
 def load_peaks():
@@ -124,13 +185,35 @@ def make_inputs(No, Nv, seed, sigma_off):
     return synth.make_instance(No, Nv, seed, sigma_off=sigma_off)
 
 
-def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
-    """The oracle (O2, as it stands) on this host's cores: sampled sigma elements of the same
-    workload extrapolated to one full sigma build, times the number of sigma builds the
-    oracle's own CG needs on the small instance of the same recipe (No=6, Nv=30, seed 0)."""
+def _golden(config):
+    path = GOLDEN.get(config)
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    with open(os.path.join(ROOT, path)) as f:
+        return json.load(f)
+
+
+def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None, tol=1e-8, config=None):
+    """The oracle (O2, as it stands) on this host's cores.  Small workloads (at most 2e6
+    amplitudes): one whole O2 solve (create + plain CG to tol + energy), timed.  Larger ones:
+    O2 sigma on randomly sampled elements of the same workload for about budget_s seconds,
+    extrapolated to one full sigma build, times the number of sigma builds of an O2 solve of
+    the same recipe (the stored oracle solve of this workload when there is one, else the
+    No=6 Nv=30 seed 0 solve run here) -- an extrapolation, reported as such."""
     from oracle import o2, top
     import synth
     t0 = time.time()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    n = 5 * No * No * Nv * Nv
+    if n <= 2_000_000:
+        full = inst if inst is not None else synth.make_instance(No, Nv, seed, sigma_off=sigma_off)
+        ts = time.perf_counter()
+        res = o2.solve(top.prepare(full), tol=tol)
+        t = time.perf_counter() - ts
+        return {"value": t, "unit": "s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+                "extrapolated": False, "E2": res["E2"], "cg_iterations": res["iters"],
+                "sample": f"whole O2 solve of the No={No} Nv={Nv} seed={seed} instance to {tol} (timed)",
+                "wall_s": time.time() - t0}
     if inst is None:
         F = synth.fock(No, Nv, seed, sigma_off)
         C = synth.singles_coefficients(F, No, Nv, seed)
@@ -142,7 +225,6 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
             "ovov": np.zeros((No, Nv, No, Nv)), "ooov": np.zeros((No, No, No, Nv)),
             "ovvt": np.zeros((No, Nv, Nv, No))}   # sigma needs no integrals
     o = o2.O2(prep)
-    n = 5 * No * No * Nv * Nv
     x = np.full(n, 1e-3)
     rng = np.random.default_rng(0)
     done, t_spent, batch = 0, 0.0, 256
@@ -154,15 +236,21 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None):
         done += batch
         batch = min(batch * 2, 65536)
     t_elem = t_spent / done
-    small = synth.make_instance(6, 30, 0)
-    res = o2.solve(top.prepare(small), tol=1e-8)
-    n_sigma = res["iters"] + 2
+    g = _golden(config) if config else None
+    if g is not None:
+        n_sigma = g["cg_iterations"] + 2
+        src = f"the stored O2 solve of this workload ({g['task']}: {g['cg_iterations']} CG iterations to {g['tol']})"
+    else:
+        small = synth.make_instance(6, 30, 0)
+        res = o2.solve(top.prepare(small), tol=tol)
+        n_sigma = res["iters"] + 2
+        src = f"the O2 solve of No=6 Nv=30 seed 0 to {tol} ({res['iters']} CG iterations)"
     t_sigma = t_elem * n
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": t_sigma * n_sigma, "unit": "s", "cores": cores, "kind": "oracle",
+    return {"value": t_sigma * n_sigma, "unit": "s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+            "extrapolated": True,
             "sample": (f"O2 sigma at {done} random elements of the No={No} Nv={Nv} block vector "
                        f"({t_spent:.1f} s), extrapolated to {n} elements = {t_sigma:.1f} s per sigma build, "
-                       f"x {n_sigma} builds (O2 plain CG to 1e-8 on No=6 Nv=30 seed 0)"),
+                       f"x {n_sigma} builds as in {src}"),
             "t_sigma_s": t_sigma, "n_sigma": n_sigma, "wall_s": time.time() - t0}
 
 
@@ -178,14 +266,15 @@ def run_reference(args):
     if args.config not in WORKLOADS:
         print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-instance configs"}))
         return 0
-    No, Nv, seed, so = WORKLOADS[args.config]
+    No, Nv, seed, so, _, tol0 = WORKLOADS[args.config]
+    tol = args.tol if args.tol is not None else tol0
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     vals = []
     last = None
     for _ in range(args.warmup + args.steps):
-        last = cpu_baseline(No, Nv, seed, so, budget_s=args.ref_budget)
+        last = cpu_baseline(No, Nv, seed, so, budget_s=args.ref_budget, tol=tol, config=args.config)
         vals.append(last["value"])
     v = statistics.mean(vals[args.warmup:])
     cb = dict(last)
@@ -193,7 +282,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1) tol={args.tol}"},
+            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1) tol={tol}"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -262,6 +351,39 @@ def run_batch(args):
     return 0
 
 
+def family_roofline(name, kt, peaks, peak_src, fp64_peak, steps):
+    """Achieved rate of one kernel family from its own CUDA events over the timed region."""
+    sec = kt["ms"] * 1e-3
+    out = {"launches": kt["launches"], "kernel_ms_per_step": kt["ms"] / steps,
+           "avg_launch_ms": kt["ms"] / max(1, kt["launches"])}
+    if sec <= 0:
+        return out
+    if name in ("contraction", "digits"):
+        out.update({"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops_sustained"],
+                    "achieved": kt["alg_units"] / sec / 1e12, "achieved_executed": kt["exec_units"] / sec / 1e12,
+                    "peak_source": f"bf16 dense sustained, {peak_src} (MEASURED_PEAKS.json)"})
+        out["kernel"] = ("k_virt, bf16 operands (inner sigma): achieved = the method's flops 4 n_unique Nv per build"
+                         if name == "contraction" else
+                         "k_virt, exact bf16 digit products (float64-accurate residual, energy, rotations): "
+                         "achieved = the method's flops of each contraction once; achieved_executed = every "
+                         "digit pair the tensor cores run")
+    elif name == "coupling":
+        out.update({"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"], "achieved": kt["alg_units"] / sec / 1e9,
+                    "kernel": "k_couple: element-wise coupling pass (one read of x, one read and write of y)",
+                    "peak_source": f"copy bandwidth, {peak_src} (MEASURED_PEAKS.json)"})
+    elif name == "gemm64":
+        out.update({"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak, "achieved": kt["alg_units"] / sec / 1e12,
+                    "kernel": "gemm64_kernel: float64 GEMM on the CUDA cores",
+                    "peak_source": "float64 GEMM rate measured in this run (torch.matmul 4096^3, cuBLAS)"})
+    else:
+        out.update({"bound": "alu", "unit": "Gelem/s", "peak": None, "achieved": kt["alg_units"] / sec / 1e9,
+                    "kernel": "k_e2s: S-space energy sum (double-float on the float32 pipes)",
+                    "peak_source": "no measured float32 peak"})
+    if out.get("achieved") is not None and out.get("peak"):
+        out["frac"] = out["achieved"] / out["peak"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,8 +395,8 @@ def main():
     ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
     ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--maxit", type=int, default=2000)
+    ap.add_argument("--tol", type=float, default=None, help="default: the workload's (1e-8 mixed, 1e-10 fp64)")
+    ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -284,6 +406,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "c4":
+        if args.tol is None:
+            args.tol = 1e-8
         return run_batch(args)
 
     import torch
@@ -298,21 +422,21 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    No, Nv, seed, so = WORKLOADS[args.config]
+    No, Nv, seed, so, prec0, tol0 = WORKLOADS[args.config]
+    tol = args.tol if args.tol is not None else tol0
     seed = seed + 1000 * rank
     inst = make_inputs(No, Nv, seed, so)
     names = ("F", "ovov", "ooov", "ovvv", "C")
     dins = {k: torch.from_numpy(inst[k]).to(dev) for k in names}
-    lib = esmp2.load()
-    prec_name = args.precision
-    if prec_name == "auto":
-        prec_name = "mixed" if os.environ.get("ESMP2_BENCH_FP64") is None and _mixed_available() else "fp64"
+    esmp2.load()
+    prec_name = prec0 if args.precision == "auto" else args.precision
     prec = esmp2.MIXED_BF16 if prec_name == "mixed" else esmp2.FP64
     stream = torch.cuda.current_stream()
+    fp64_peak = measure_fp64_peak(dev)
 
     def step(inputs):
         h = esmp2.Handle(*(inputs[k] for k in names))
-        info = h.solve(tol=args.tol, maxit=args.maxit, precision=prec)
+        info = h.solve(tol=tol, maxit=args.maxit, precision=prec)
         e = h.energy()
         n_l = h.kernel_launches
         h.close()
@@ -350,47 +474,28 @@ def main():
         elapsed = max_over_ranks(elapsed, dist, dev)
     tts = elapsed / args.steps
 
-    # dominant kernel family of the timed region, from its own CUDA events
+    # every kernel family of the timed region from its own CUDA events; the headline roofline
+    # is the family with the largest device time
     peaks, peak_src = load_peaks()
+    fams = {k: family_roofline(k, v, peaks, peak_src, fp64_peak, args.steps) for k, v in ktimes.items()}
+    for k in fams:
+        fams[k]["share_of_step"] = ktimes[k]["ms"] / 1e3 / elapsed
     dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
-    kt = ktimes[dom]
-    sec = kt["ms"] * 1e-3
-    if dom == "contraction":
-        roofline = {"bound": "tensor", "achieved": kt["alg_units"] / sec / 1e12,
-                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                    "kernel": "k_virt: tcgen05 virtual-index contraction (bf16 inner and digit-split float64 levels)",
-                    "peak_source": f"bf16 dense sustained, {peak_src} (MEASURED_PEAKS.json)",
-                    "achieved_executed": kt["exec_units"] / sec / 1e12}
-    elif dom == "coupling":
-        roofline = {"bound": "hbm", "achieved": kt["alg_units"] / sec / 1e9, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "kernel": "k_couple: element-wise coupling pass",
-                    "peak_source": f"copy bandwidth, {peak_src} (MEASURED_PEAKS.json)"}
-    elif dom == "gemm64":
-        roofline = {"bound": "alu", "achieved": kt["alg_units"] / sec / 1e12, "peak": NOMINAL_FP64_TFLOPS,
-                    "unit": "TFLOP/s", "kernel": "gemm64_kernel: float64 GEMM",
-                    "peak_source": "GB300 nominal float64 rate (CUDA cores)"}
-    else:
-        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
-                    "kernel": "k_e2s: S-space energy sum (double-float on the float32 pipes)",
-                    "peak_source": "no measured float32 peak"}
-    if roofline["achieved"] is not None:
-        roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    else:
-        roofline["frac"] = None
-    roofline["traffic"] = None
-    roofline["launches"] = kt["launches"]
-    roofline["kernel_ms_per_step"] = kt["ms"] / args.steps
-    roofline["avg_launch_ms"] = kt["ms"] / max(1, kt["launches"])
-    kernel_share = {k: {"ms_per_step": v["ms"] / args.steps, "share_of_step": v["ms"] / 1e3 / elapsed,
-                        "launches_per_step": v["launches"] / args.steps} for k, v in ktimes.items()}
+    roofline = dict(fams[dom])
+    roofline["family"] = dom
+    ent, prof = kernel_traffic(dom)
+    roofline["traffic"] = ent["bytes_per_launch"] if ent else None
+    roofline["traffic_source"] = prof
 
     # per-stage view of one sigma build of this precision (outside the timed region)
     h = esmp2.Handle(*(dins[k] for k in names))
     x = h.rhs()
     ms = h.profile_sigma(x, precision=prec, reps=3)
     fl = sigma_flops(No, Nv)
+    nu = unique_amplitudes(No, Nv)
     roofline["sigma_stage_ms"] = [float(v) for v in ms[:5]]
     sigma_alg_tflops = fl["alg_total"] / (ms[4] * 1e-3) / 1e12
+    sigma_alg_gbs = (16.0 if prec == esmp2.FP64 else 6.0) * nu / (ms[4] * 1e-3) / 1e9
     h.close()
 
     e2e = None
@@ -415,7 +520,7 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         h64 = esmp2.Handle(*(dins[k] for k in names))
-        info64 = h64.solve(tol=args.tol, maxit=args.maxit, precision=esmp2.FP64)
+        info64 = h64.solve(tol=tol, maxit=args.maxit, precision=esmp2.FP64)
         en64 = h64.energy()
         h64.close()
         e1.record(stream)
@@ -425,22 +530,25 @@ def main():
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(No, Nv, seed, so, inst=inst)
+        cb = cpu_baseline(No, Nv, seed, so, inst=inst, tol=tol, config=args.config)
 
     info, e = infos[-1]
     line = {"metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == esmp2.FP64 else "bf16+f64", "data": "synthetic",
             "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1)",
-                       "tol": args.tol, "precision": prec_name, "step": "create+solve+energy, inputs resident",
+                       "tol": tol, "precision": prec_name, "step": "create+solve+energy, inputs resident",
                        "l2": "no flush: every block vector (5.8 GB at No=30 Nv=400) is larger than L2"},
-            "roofline": roofline, "kernel_families": kernel_share, "cpu_baseline": cb, "e2e": e2e,
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-            "sigma_builds_per_s": 1e3 / ms[4], "sigma_tflops_alg": sigma_alg_tflops,
+            "roofline": roofline, "kernel_families": fams, "fp64_gemm_peak_tflops": fp64_peak,
+            "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "sigma_builds_per_s": 1e3 / ms[4], "sigma_tflops_alg": sigma_alg_tflops, "sigma_gbs_alg": sigma_alg_gbs,
             "iterations": info["iterations"], "outer": info["outer"], "sigma_fp64": info["sigma_fp64"],
             "sigma_lowp": info["sigma_lowp"], "rel_residual": info["rel_residual"], "E2": e["E2"],
             "E2_parts": e}
+    g = _golden(args.config)
+    if g is not None and seed == g["instance"]["seed"]:
+        line["E2_error_vs_oracle"] = {k: e[k] - g[k] for k in ("E2", "E2_D", "E2_L", "E2_S")}
+        line["E2_error_vs_oracle"]["oracle"] = GOLDEN[args.config]
     if fp64_cmp is not None:
         fp64_cmp["E2_mixed_minus_fp64"] = e["E2"] - fp64_cmp["E2"]
         fp64_cmp["speedup_mixed_over_fp64"] = fp64_cmp["time_to_solution_s"] / tts

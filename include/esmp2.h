@@ -76,6 +76,17 @@ typedef struct {
   const double *C;          /* No x Nv singles coefficients (any normalisation; rescaled so 2|C|^2 = 1) */
   int spin;                 /* +1 singlet (supported); -1 triplet -> ESMP2_ERR_UNSUPPORTED */
   int inputs_on_device;     /* 0: host pointers, 1: device pointers (read during create only) */
+  /* Large transition-orbital pairs (Sec. II.C partition of the triples into L / S / N):
+   * n_large > 0: the n_large largest singular values; n_large == 0 and eta > 0: every pair with
+   * lambda_u > eta; n_large == 0 and eta <= 0: TOP(1), the largest.  This library builds
+   * TOP(1): any selection of more than one pair returns ESMP2_ERR_UNSUPPORTED, none
+   * ESMP2_ERR_INVALID_ARG. */
+  double eta;
+  int n_large;
+  int avo_convention;       /* completion of the virtual space (AVOs): 0 = Householder QR (only) */
+  double level_shift;       /* s added to H0 on the first-order space (A -> A + s, every S-space
+                               denominator + s): the intruder-state remedy the paper cites for
+                               CASPT2 (Sec. III); 0 = the paper's ESMP2 */
 } esmp2_desc;
 
 typedef struct {
@@ -123,9 +134,13 @@ esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv
  * doubles and L-triples, minus E0.  x, y: caller-owned DEVICE buffers of n_elems
  * float64 in the block layout; x must be zero on masked elements and antisymmetric
  * where the layout says so; y is written on every element (zero on masked ones).
- * p = ESMP2_FP64 computes in float64; ESMP2_MIXED_BF16 rounds x and F to bf16 for
- * the N_o^2 N_v^3 virtual-index contractions (fp32 accumulation), keeps the rest
- * in fp32/fp64.  x and y must not overlap. */
+ * p = ESMP2_FP64 computes in float64; ESMP2_MIXED_BF16 computes it the way the inner solve
+ * of the mixed-precision solver does: the N_o^2 N_v^3 virtual-index contractions from bf16
+ * operands (fp32 accumulation) as one tensor-core GEMM, everything else in float32, in the
+ * basis whose occupied orbitals other than t diagonalise F_oo; for No <= 32 it needs x to
+ * have the spin-flip symmetry of the singlet, S_ij^ab = S_ji^ba (every vector of the problem
+ * has it: b, the solution and every Krylov vector), and returns y with that symmetry and the
+ * antisymmetry of T, X, Y exactly.  x and y must not overlap. */
 esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
 
 /* Per-stage device timing of `reps` sigma builds y = A x (same arguments as esmp2_sigma),
@@ -207,13 +222,19 @@ int64_t esmp2_kernel_launches(const esmp2_handle *h);
 /* Process-wide timing of the kernel families of the hot path (measurement support; the
  * paper has no counterpart).  While enabled, each launch of an instrumented family is
  * bracketed by two CUDA events on the stream it runs on, and its work is recorded:
- *   ESMP2_KT_CONTRACTION  tcgen05 virtual-index contraction (bf16 and digit-split launches);
- *                         alg_units = algorithmic flops (unique amplitudes, per digit pair),
- *                         exec_units = flops the tensor cores execute on stored slices
+ *   ESMP2_KT_CONTRACTION  tcgen05 virtual-index contraction with bf16 operands (inner sigma);
+ *                         alg_units = the method's flops, 4 n_unique Nv per sigma build
+ *                         (n_unique = unique D+L amplitudes, spin-flip pairs once),
+ *                         exec_units = flops the tensor cores execute on the stored slices
  *   ESMP2_KT_COUPLING     element-wise coupling pass (five block launches); units = bytes of
  *                         one read of x and one read and write of y
  *   ESMP2_KT_GEMM64       float64 GEMM (transforms, float64 sigma); units = flops
  *   ESMP2_KT_E2S          S-space energy sum; units = S-space elements
+ *   ESMP2_KT_DIGITS       float64-accurate contraction from exact bf16 digit products (true
+ *                         residual, energy, integral rotations); alg_units = the method's
+ *                         flops of ONE contraction (4 n_unique Nv, or 2 rows Nv^2 for a
+ *                         rotation), however many digit pairs emulate it; exec_units = the
+ *                         tensor-core flops of every digit pair
  * esmp2_kernel_times synchronises the recorded events, fills out[ESMP2_KT_COUNT] with the
  * totals since the last call and clears them ("launches" counts timed scopes: one coupling
  * pass, one E2_S sector).  Enabling adds two event records per scope. */
@@ -222,7 +243,8 @@ typedef enum {
   ESMP2_KT_COUPLING = 1,
   ESMP2_KT_GEMM64 = 2,
   ESMP2_KT_E2S = 3,
-  ESMP2_KT_COUNT = 4
+  ESMP2_KT_DIGITS = 4,
+  ESMP2_KT_COUNT = 5
 } esmp2_kernel_family;
 typedef struct {
   int64_t launches;
@@ -258,6 +280,18 @@ esmp2_status esmp2_kernel_times(esmp2_kernel_time *out);
 #define ESMP2_NOALLOC_MAX_BYTES (64u << 20)
 esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const double *Fvv, double *y, int S, int Nv,
                                                void *stream);
+
+/* Self-test of the failure detection of the tensor-core kernel (the paper has no
+ * counterpart).  Every mbarrier wait of that kernel is bounded; a wait that runs out raises a
+ * device error flag that the host turns into ESMP2_ERR_TIMEOUT, and the CUDA context stays
+ * usable.  This call runs one CTA of the kernel on a 16 x 16 dummy slice whose producer issues
+ * no copies, so the consumer's first waits run out after wait_ms milliseconds (1 .. 2000) with
+ * no copy, MMA or TMEM load in flight.  It returns ESMP2_ERR_TIMEOUT when the expiry was
+ * detected and reported (the expected outcome), ESMP2_OK if it was not, ESMP2_ERR_CUDA on a
+ * CUDA error, ESMP2_ERR_INVALID_ARG for wait_ms out of range.  It allocates nothing: it uses
+ * the scratch array of esmp2_virtual_contraction_noalloc (so it must not overlap such a call
+ * on the GPU) and synchronises `stream` (a cudaStream_t, NULL = legacy default). */
+esmp2_status esmp2_selftest_bounded_wait(int wait_ms, void *stream);
 
 #ifdef __cplusplus
 }

@@ -215,10 +215,17 @@ def classify(sys: System, det: int, large: set):
 
 
 def solve(F: np.ndarray, eri: np.ndarray, C: np.ndarray, No: int, Nv: int,
-          eta: float | None = None, n_large: int = 1, basis=None) -> Result:
+          eta: float | None = None, n_large: int = 1, basis=None, h0: str = "modified",
+          shift: float = 0.0) -> Result:
     """ESMP2 in the determinant space.  Inputs in the ESMF orbital basis: F (N x N),
     eri (N^4 chemist), C (No x Nv).  Large TOPs: lambda_u > eta if eta is given,
-    else the n_large largest.  `basis` optionally overrides (U, lam, Wv)."""
+    else the n_large largest.  `basis` optionally overrides (U, lam, Wv).
+
+    h0 = "modified": Eq. qfq_replacement, the full Fock operator on D + L and its diagonal on
+    S + N (the N^5 method).  h0 = "original": Eq. old_H0, the full Fock operator on every
+    first-order determinant (D and all triples; the N^7 parent method, here for tiny spaces).
+    shift: a level shift added to H0 on the first-order space (A -> A + shift, every
+    denominator + shift), the remedy for intruder states the paper cites (CASPT2)."""
     sys = System(No, Nv)
     Cn = top.normalise_singles(C)
     U, lam, Wv = basis if basis is not None else top.top_basis(Cn)
@@ -233,8 +240,11 @@ def solve(F: np.ndarray, eri: np.ndarray, C: np.ndarray, No: int, Nv: int,
 
     dets = sys.determinants()
     cls = {d: classify(sys, d, large) for d in dets}
-    DL = [d for d in dets if cls[d] in ("D", "L")]
-    SN = [d for d in dets if cls[d] in ("S", "N")]
+    full = ("D", "L", "S", "N") if h0 == "original" else ("D", "L")
+    if h0 not in ("modified", "original"):
+        raise ValueError(h0)
+    DL = [d for d in dets if cls[d] in full]
+    SN = [d for d in dets if cls[d] in ("S", "N") and cls[d] not in full]
     idx = {d: k for k, d in enumerate(DL)}
 
     Hpsi = apply_hamiltonian(sys, psi0, h, eri_t)
@@ -249,7 +259,7 @@ def solve(F: np.ndarray, eri: np.ndarray, C: np.ndarray, No: int, Nv: int,
             i = idx.get(d)
             if i is not None:
                 A[i, j] += v
-    A -= E0 * np.eye(n)
+    A -= (E0 - shift) * np.eye(n)
     fdiag = np.diag(Ft)
 
     def diag_energy(det):
@@ -258,7 +268,7 @@ def solve(F: np.ndarray, eri: np.ndarray, C: np.ndarray, No: int, Nv: int,
             for p in range(sys.N):
                 if (det >> sys.so(p, s)) & 1:
                     e += fdiag[p]
-        return e - E0
+        return e - E0 + shift
 
     bDL = np.array([b.get(d, 0.0) for d in DL])
     xDL = np.linalg.solve(A, -bDL) if n else np.zeros(0)

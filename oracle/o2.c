@@ -21,6 +21,7 @@
  *   doubles <- triples : sum_kc f_kc x_ijk^abc
  *   triples <- triples : the same one-body terms on all three particle / hole slots
  *   triples <- doubles : P(k/ij) P(c/ab) f_ck x_ij^ab
+ *   (an optional level shift s adds s to A and to every S-space denominator)
  *   E_Phi[F] - E0 = -omega,  omega = sum_u 2 lam_u^2 (F_u'u' - F_uu)  (gamma of Psi0
  *   is diagonal in the TOP basis: 2 - 2 lam_u^2 on u, 2 lam_u^2 on u').
  * Right-hand side b = Q H Psi0 (Slater-Condon, Psi0 = sum_u lam_u singles u -> u'):
@@ -45,6 +46,7 @@ typedef struct {
   const double *ooov;  /* (ij|ka)  [No][No][No][Nv] */
   const double *ovvt;  /* (ia|bu') [No][Nv][Nv][No] */
   double omega;
+  double shift;        /* level shift of H0 on the first-order space (0: the paper's H0) */
   double *f0vo;        /* [Nv][No] */
   int err;
 } o2_ctx;
@@ -180,7 +182,7 @@ static const int PSGN[3] = {1, -1, -1};
 /* ------------------------------------------------------------------ sigma */
 static double sigma_string(const o2_ctx *c, const double *x, int n, const orb *H, const orb *P) {
   const int No = c->No, Nv = c->Nv;
-  double val = -c->omega * amp(c, x, n, H, P);
+  double val = (c->shift - c->omega) * amp(c, x, n, H, P);   /* E_Phi[F] - E0 + shift */
   orb H2[3], P2[3];
   for (int m = 0; m < n; ++m) {                       /* particle slots: + sum_d f_{p d} */
     memcpy(H2, H, sizeof(orb) * n); memcpy(P2, P, sizeof(orb) * n);
@@ -329,7 +331,7 @@ void o2_rhs_at(o2_ctx *c, int64_t count, const int64_t *flat, double *out) {
  * one transition-orbital pair u -> u' (same spin) and none of them is the large t = 0.
  * Each triple is visited once, from its lowest pair; the spin-flipped sector doubles it. */
 static double diag3(const o2_ctx *c, const orb *H, const orb *P) {
-  double e = -c->omega;
+  double e = c->shift - c->omega;
   for (int k = 0; k < 3; ++k) e += Fvv(c, P[k].o, P[k].o) - Foo(c, H[k].o, H[k].o);
   return e;
 }
@@ -433,6 +435,8 @@ o2_ctx *o2_create(int No, int Nv, const double *F, const double *lam, const doub
 }
 
 double o2_omega(const o2_ctx *c) { return c->omega; }
+/* level shift s: H0 -> H0 + s on the first-order space (every denominator + s) */
+void o2_set_shift(o2_ctx *c, double s) { c->shift = s; }
 int o2_error(const o2_ctx *c) { return c->err; }
 void o2_f0vo(const o2_ctx *c, double *out) { memcpy(out, c->f0vo, sizeof(double) * (size_t)c->Nv * c->No); }
 void o2_destroy(o2_ctx *c) { if (c) { free(c->f0vo); free(c); } }

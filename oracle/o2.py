@@ -47,6 +47,8 @@ def _load():
             lib.o2_destroy.argtypes = [P]
             lib.o2_omega.restype = D
             lib.o2_omega.argtypes = [P]
+            lib.o2_set_shift.restype = None
+            lib.o2_set_shift.argtypes = [P, D]
             lib.o2_error.restype = I
             lib.o2_error.argtypes = [P]
             lib.o2_f0vo.argtypes = [P, P]
@@ -65,7 +67,7 @@ def _load():
 class O2:
     """Oracle context in the TOP basis.  `prep` is the dict returned by oracle.top.prepare."""
 
-    def __init__(self, prep: dict):
+    def __init__(self, prep: dict, shift: float = 0.0):
         self.No, self.Nv = prep["No"], prep["Nv"]
         self._keep = [np.ascontiguousarray(prep[k], dtype=np.float64)
                       for k in ("F", "lam", "ovov", "ooov", "ovvt")]
@@ -74,6 +76,8 @@ class O2:
         self.F = F
         self._c = _load().o2_create(self.No, self.Nv, F.ctypes.data, lam.ctypes.data,
                                     ovov.ctypes.data, ooov.ctypes.data, ovvt.ctypes.data)
+        if shift:
+            _load().o2_set_shift(self._c, float(shift))
 
     def __del__(self):
         if getattr(self, "_c", None) and _lib is not None:
@@ -171,10 +175,11 @@ def cg(o: O2, b: np.ndarray, tol: float = 1e-10, maxit: int = 1000, x0=None):
     return x, it, hist
 
 
-def solve(prep: dict, tol: float = 1e-10, maxit: int = 1000) -> dict:
+def solve(prep: dict, tol: float = 1e-10, maxit: int = 1000, shift: float = 0.0) -> dict:
     """E2 of ESMP2-TOP(1): E2_DL by the Hylleraas functional 2 b.x + x.Ax at the CG
-    solution (error quadratic in the residual), plus the direct S-space sum."""
-    o = O2(prep)
+    solution (error quadratic in the residual), plus the direct S-space sum.  shift: level
+    shift of H0 on the first-order space."""
+    o = O2(prep, shift)
     b = o.rhs()
     x, it, hist = cg(o, b, tol, maxit)
     Ax = o.sigma(x)

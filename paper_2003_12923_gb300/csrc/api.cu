@@ -33,7 +33,8 @@ void free_handle(esmp2_handle *h) {
                   h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
                   h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
-                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig};
+                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig, h->pr, h->pp, h->pq, h->pd, h->pdinv, h->pop, h->pW,
+                  h->pP, h->pVX, h->pGP, h->pWZ, h->pHP, h->pOC, h->pOC2, h->pOX, h->pOZ, h->pG, h->pH, h->pCYZ, h->pdot};
   for (void *p : ptrs)
     if (p) dfree(p, h->stream);
   cudaStreamSynchronize(h->stream);
@@ -73,6 +74,15 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   }
   if (d->spin != 1) { h->err = "only singlet states (spin = +1) are supported"; return ESMP2_ERR_UNSUPPORTED; }
   if (!d->F || !d->ovov || !d->ooov || !d->ovvv || !d->C) { h->err = "NULL input array"; return ESMP2_ERR_INVALID_ARG; }
+  if (d->avo_convention != 0) { h->err = "only the Householder completion of the virtual space (avo_convention 0)"; return ESMP2_ERR_UNSUPPORTED; }
+  if (d->n_large > 1) { h->err = "TOP(k) with k > 1 large pairs is not supported (TOP(1) only)"; return ESMP2_ERR_UNSUPPORTED; }
+  if (d->n_large < 0 || !std::isfinite(d->eta) || !std::isfinite(d->level_shift)) {
+    h->err = "n_large < 0 or non-finite eta / level_shift";
+    return ESMP2_ERR_INVALID_ARG;
+  }
+  h->level_shift = d->level_shift;
+  h->eta = d->eta;
+  h->n_large = d->n_large;
   const int N = No + Nv;
   h->d.No = No; h->d.Nv = Nv; h->d.N = N;
   h->d.B = (int64_t)No * No * Nv * Nv;
@@ -133,6 +143,16 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   esmp2_status s = check_cuda(h, ce, "input copy");
   debug_phase(h, "create: input copies");
   if (!s) s = setup_top_basis(h);
+  if (!s && h->n_large == 0 && h->eta > 0.0) {  // eta selects the large pairs: exactly one (TOP(1))
+    std::vector<double> lam(No);
+    s = check_cuda(h, cudaMemcpyAsync(lam.data(), h->lam, sizeof(double) * No, cudaMemcpyDeviceToHost, h->stream), "lambda");
+    if (!s) s = check_cuda(h, cudaStreamSynchronize(h->stream), "lambda");
+    int nl = 0;
+    for (int u = 0; u < No; ++u) nl += lam[u] > h->eta;
+    if (!s && nl == 0) { h->err = "eta exceeds every singular value: no large pair"; s = ESMP2_ERR_INVALID_ARG; }
+    if (!s && nl > 1) { h->err = "eta selects more than one large pair (TOP(k), k > 1, is not supported)"; s = ESMP2_ERR_UNSUPPORTED; }
+  }
+  h->omega_op = h->omega - h->level_shift;
   debug_phase(h, "create: TOP basis");
   if (!s) s = setup_rhs_from(h, ovov_src, ovov_in, ooov_in, ovvv_src, ovvv_in, scratch);
   debug_phase(h, "create: transforms + rhs");

@@ -434,7 +434,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
   cudaMemsetAsync(Gd, 0, sizeof(double) * (N + 1), st);
   GCtx c;
   c.No = No; c.Nv = Nv; c.N = N; c.B = h->d.B; c.x = h->s64.x; c.lam = h->lam; c.ovov = h->ovov; c.F = h->F;
-  c.omega = h->omega;
+  c.omega = h->omega_op;
   densities(h, h->s64.x, Gf);
   kg_ovov_L<<<1216, 256, 0, st>>>(c, Gov);
   kg_small<<<(unsigned)cdiv((int64_t)No * Nv, 128), 128, 0, st>>>(c, Gov, Gf);

@@ -1,0 +1,911 @@
+// The inner (float32 / bf16) sigma of the mixed-precision solve on the packed layout.
+//
+// The inner solve works in the basis whose occupied orbitals other than t diagonalise F_oo
+// (D and L do not change under rotations that fix t), so the occupied-index terms of the
+// operator are a diagonal plus the t row and column ("arrow" form).  Its vectors keep only
+// the T, X, Y slices i < j (the slice (j, i) is the negative) and every S and Z slice, with
+// rows padded to Nvp (see esmp2::Packed).  One sigma build q = A p:
+//   1. the bf16 operand (written by the PCG update) gets the transposed Z slices appended;
+//   2. one tensor-core GEMM (vgemm.cu) forms P = A F_vv for every operand row;
+//   3. the slice-direction arrow sums (sums over an occupied index weighted by F_l,t and
+//      F_l,t') are one streaming pass, the few N^3-sized intermediates of the N^4 coupling
+//      terms (reductions over one virtual index with the occupied-virtual Fock rows) three
+//      small ones, all float32 from p: computed from the bf16 operand they made the inner
+//      operator lose the symmetry of its float32 coefficients, and CG stalled;
+//   4. the coupling pass forms y = (P combined with its transpose) + the N^4 coupling terms
+//      (Table 1's T3<->T, S3<->S, S3<->T rows and the mixed-spin L-triple cross terms) +
+//      the diagonal (-omega, the L pair energy, the arrow diagonal), masks the slots that
+//      are not amplitudes, and leaves the per-CTA partials of <p, q>.  T, X, Y are computed on
+//      tile pairs and written with exact antisymmetry in (a, b); S on slice pairs (i, j),
+//      (j, i), written with the exact spin-flip symmetry S_ij^ab = S_ji^ba of the singlet.
+// Every formula below is the element-wise form of the full-storage coupling pass (sigma.cu)
+// with the packed slice access.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace esmp2 {
+
+Packed make_packed(int No, int Nv) {
+  Packed L{};
+  L.No = No;
+  L.Nv = Nv;
+  L.Nvp = (Nv + 7) & ~7;
+  L.nh = No * (No - 1) / 2;
+  L.NN = No * No;
+  L.SL = (int64_t)Nv * L.Nvp;
+  const int ns[6] = {L.nh, L.NN, L.nh, L.nh, L.NN, L.NN};
+  int64_t o = 0;
+  for (int k = 0; k < 6; ++k) {
+    L.boff[k] = o;
+    o += ns[k] * L.SL;
+  }
+  L.nslices = 3 * L.nh + 2 * L.NN;
+  L.n = L.boff[5];
+  return L;
+}
+
+namespace {
+
+constexpr int kT = 32;          // coupling tile edge
+constexpr int kThreads = 256;   // 32 x 8
+
+__host__ __device__ __forceinline__ int pair_ij(int No, int i, int j) { return i * No - i * (i + 1) / 2 + (j - i - 1); }
+__host__ __device__ __forceinline__ void pair_decode(int No, int k, int &i, int &j) {
+  i = 0;
+  while (k >= No - 1 - i) {
+    k -= No - 1 - i;
+    ++i;
+  }
+  j = i + 1 + k;
+}
+
+__device__ __forceinline__ bool valid_elem(int blk, int i, int j, int a, int b) {
+  if ((blk == BT || blk == BX || blk == BY) && (i == j || a == b)) return false;
+  if (blk == BX && (i == 0 || j == 0 || a == 0 || b == 0)) return false;
+  if (blk == BZ && (j == 0 || b == 0 || (i == 0 && a == 0))) return false;
+  return true;
+}
+
+// slice index (in slices of SL elements) of block blk's first slice, packed order
+__host__ __device__ __forceinline__ int slice0(const Packed &L, int blk) { return (int)(L.boff[blk] / L.SL); }
+
+struct PV {
+  Packed L;
+  // slice (blk, i, j): pointer and sign; nullptr for the identically zero slices i == j of T, X, Y
+  template <typename T>
+  __device__ __forceinline__ T *sl(T *v, int blk, int i, int j, float &sg) const {
+    if (blk == BS || blk == BZ) {
+      sg = 1.f;
+      return v + L.boff[blk] + ((int64_t)i * L.No + j) * L.SL;
+    }
+    if (i == j) {
+      sg = 0.f;
+      return nullptr;
+    }
+    if (i < j) {
+      sg = 1.f;
+      return v + L.boff[blk] + (int64_t)pair_ij(L.No, i, j) * L.SL;
+    }
+    sg = -1.f;
+    return v + L.boff[blk] + (int64_t)pair_ij(L.No, j, i) * L.SL;
+  }
+  __device__ __forceinline__ float at(const float *v, int blk, int i, int j, int a, int b) const {
+    float sg;
+    const float *p = sl(v, blk, i, j, sg);
+    return p ? sg * p[(int64_t)a * L.Nvp + b] : 0.f;
+  }
+  // block, i, j of slice s of the packed order (T | S | X | Y | Z)
+  __device__ __forceinline__ void decode(int s, int &blk, int &i, int &j) const {
+    const int nh = L.nh, NN = L.NN;
+    if (s < nh) { blk = BT; pair_decode(L.No, s, i, j); }
+    else if (s < nh + NN) { blk = BS; s -= nh; i = s / L.No; j = s % L.No; }
+    else if (s < 2 * nh + NN) { blk = BX; pair_decode(L.No, s - nh - NN, i, j); }
+    else if (s < 3 * nh + NN) { blk = BY; pair_decode(L.No, s - 2 * nh - NN, i, j); }
+    else { blk = BZ; s -= 3 * nh + NN; i = s / L.No; j = s % L.No; }
+  }
+};
+
+struct FF {  // float Fock matrix of the working basis
+  const float *F;
+  int N, No;
+  __device__ __forceinline__ float o(int k, int l) const { return F[k * N + l]; }
+  __device__ __forceinline__ float v(int a, int b) const { return F[(No + a) * N + No + b]; }
+  __device__ __forceinline__ float ov(int k, int a) const { return F[k * N + No + a]; }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// sum of one value per thread of the CTA into red[slot] (one CTA writes one slot)
+__device__ __forceinline__ void cta_partial(double v, double *red, int64_t slot) {
+  __shared__ double sh[32];
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) red[slot] = s;
+  }
+  __syncthreads();
+}
+template <int NQ>
+__device__ __forceinline__ void cta_partials(double (&v)[NQ], double *red) {
+  __shared__ double sh[NQ][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double s = warp_sum_d(v[q]);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : 0.0;
+      s = warp_sum_d(s);
+      if (lane == 0) red[(int64_t)q * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ float blk_w(int blk) { return blk == BZ ? 2.f : 1.f; }
+
+// ---------------------------------------------------------------- layout conversions
+// r = r64 (full storage) on the packed slots, p = M^-1 r, d = 0, pb = bf16(p); partials
+// <r, M^-1 r>_w, <r, r>_w.  One CTA iteration per packed row (slice, a).
+__global__ void kp_init(PV pv, const double *r64, const __half *dinv, float *r, float *p, float *d,
+                        __nv_bfloat16 *pb, double *red) {
+  const Packed &L = pv.L;
+  const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
+  float a0 = 0.f, a1 = 0.f;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+    int blk, i, j;
+    pv.decode(s, blk, i, j);
+    const double *src = r64 + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
+    const int64_t e0 = (int64_t)s * L.SL + (int64_t)a * L.Nvp;
+    const float w = blk_w(blk);
+    for (int b = threadIdx.x; b < L.Nvp; b += blockDim.x) {
+      const int64_t e = e0 + b;
+      const float ri = b < L.Nv ? (float)src[b] : 0.f;
+      const float z = __half2float(dinv[e]) * ri;
+      r[e] = ri;
+      p[e] = z;
+      d[e] = 0.f;
+      pb[e] = __float2bfloat16_rn(z);
+      a0 += w * ri * z;
+      a1 += w * ri * ri;
+    }
+  }
+  double v[2] = {(double)a0, (double)a1};
+  cta_partials<2>(v, red);
+}
+
+// x64 (full storage) += d (packed); T, X, Y slices also update their (j, i) partner with -d
+__global__ void kp_acc64(PV pv, double *x, const float *d) {
+  const Packed &L = pv.L;
+  const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+    int blk, i, j;
+    pv.decode(s, blk, i, j);
+    const float *src = d + (int64_t)s * L.SL + (int64_t)a * L.Nvp;
+    double *x1 = x + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
+    double *x2 = x + blk * B + ((int64_t)j * L.No + i) * NvNv + (int64_t)a * L.Nv;
+    const bool anti = !(blk == BS || blk == BZ);
+    for (int b = threadIdx.x; b < L.Nv; b += blockDim.x) {
+      const double v = (double)src[b];
+      x1[b] += v;
+      if (anti) x2[b] -= v;
+    }
+  }
+}
+
+// packed float32 copy of a full-storage float64 vector
+__global__ void kp_from64(PV pv, const double *x, float *out) {
+  const Packed &L = pv.L;
+  const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+    int blk, i, j;
+    pv.decode(s, blk, i, j);
+    const double *src = x + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
+    float *dst = out + (int64_t)s * L.SL + (int64_t)a * L.Nvp;
+    for (int b = threadIdx.x; b < L.Nvp; b += blockDim.x) dst[b] = b < L.Nv ? (float)src[b] : 0.f;
+  }
+}
+
+// full-storage float64 vector from a packed float32 one (T, X, Y expanded antisymmetrically;
+// the i == j slices of T, X, Y are zero)
+__global__ void kp_to64(PV pv, const float *in, double *y) {
+  const Packed &L = pv.L;
+  const int64_t rows = 5LL * L.NN * L.Nv, NvNv = (int64_t)L.Nv * L.Nv;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int a = (int)(row % L.Nv);
+    const int64_t f = row / L.Nv;
+    const int j = (int)(f % L.No), i = (int)((f / L.No) % L.No), blk = (int)(f / L.NN);
+    float sg;
+    const float *src = pv.sl(in, blk, i, j, sg);
+    double *dst = y + f * NvNv + (int64_t)a * L.Nv;
+    for (int b = threadIdx.x; b < L.Nv; b += blockDim.x)
+      dst[b] = src ? (double)(sg * src[(int64_t)a * L.Nvp + b]) : 0.0;
+  }
+}
+
+// zero the non-amplitude slots of a full-storage float64 vector (one CTA iteration per row)
+__global__ void kp_mask64(int No, int Nv, double *y) {
+  const int64_t rows = 5LL * No * No * Nv;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int a = (int)(row % Nv);
+    const int64_t f = row / Nv;
+    const int j = (int)(f % No), i = (int)((f / No) % No), blk = (int)(f / ((int64_t)No * No));
+    for (int b = threadIdx.x; b < Nv; b += blockDim.x)
+      if (!valid_elem(blk, i, j, a, b)) y[row * Nv + b] = 0.0;
+  }
+}
+
+// Jacobi preconditioner 1 / diag(A) in half precision, zero on non-amplitude and pad slots
+__global__ void kp_dinv(PV pv, FF F, float omega, __half *dinv) {
+  const Packed &L = pv.L;
+  const int64_t rows = (int64_t)L.nslices * L.Nv;
+  const float shift = F.v(0, 0) - F.o(0, 0);
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+    int blk, i, j;
+    pv.decode(s, blk, i, j);
+    // (F_aa + F_bb) - (F_ii + F_jj): the same rounding for (i, j, a, b) and (j, i, b, a), so
+    // the preconditioner keeps the symmetries of the amplitudes exactly
+    const float occ = F.o(i, i) + F.o(j, j) + omega - (blk >= BX ? shift : 0.f), fa = F.v(a, a);
+    __half *out = dinv + (int64_t)s * L.SL + (int64_t)a * L.Nvp;
+    for (int b = threadIdx.x; b < L.Nvp; b += blockDim.x) {
+      const bool ok = b < L.Nv && valid_elem(blk, i, j, a, b);
+      out[b] = __float2half_rn(ok ? 1.f / ((fa + F.v(b, b)) - occ) : 0.f);
+    }
+  }
+}
+
+__global__ void kp_bf16(const float *src, __nv_bfloat16 *dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// the transposed Z slices of the bf16 operand: op[ZT(s)][b][a] = op[Z(s)][a][b]
+__global__ void kp_zt(PV pv, __nv_bfloat16 *op) {
+  const Packed &L = pv.L;
+  __shared__ __nv_bfloat16 t[kT][kT + 2];
+  const int nt = (L.Nv + kT - 1) / kT;
+  const int64_t items = (int64_t)L.NN * nt * nt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int s = (int)(it / (nt * nt)), tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    const __nv_bfloat16 *src = op + L.boff[BZ] + (int64_t)s * L.SL;
+    __nv_bfloat16 *dst = op + L.boff[5] + (int64_t)s * L.SL;
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx;
+      t[r][tx] = (a < L.Nv && b < L.Nv) ? src[(int64_t)a * L.Nvp + b] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int r = ty; r < kT; r += 8) {
+      const int b = tb * kT + r, a = ta * kT + tx;
+      if (a < L.Nv && b < L.Nv) dst[(int64_t)b * L.Nvp + a] = t[tx][r];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- arrow sums over slices
+struct ArrowWP {
+  float fl[32];  // F_l,t for 1 <= l < No, else 0
+  float fk[32];  // F_l,t' for l < No, else 0
+};
+
+// T, X, Y (packed i < j): OC1[q][e] = sum_{l>=1} F_lt x_lq[e] (x_lq = -x_ql for l > q), and for X
+// also OX[m][e] = sum_l F_l,t' X_lm[e].  One thread per element e of a slice; the No column sums
+// are shared-memory accumulators indexed [q][thread].
+template <int BLK>
+__global__ void __launch_bounds__(128) kp_arrow_anti(PV pv, const float *__restrict__ x, float *oc1, float *ox,
+                                                      const ArrowWP w) {
+  const Packed &L = pv.L;
+  extern __shared__ float acc[];   // [2][32][128]
+  float *a1 = acc, *ax = acc + 32 * 128;
+  const int No = L.No, t = threadIdx.x;
+  const float *xb = x + L.boff[BLK];
+  float *o1 = oc1 + (int64_t)BLK * No * L.SL;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + t; e < L.SL; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int q = 0; q < No; ++q) { a1[q * 128 + t] = 0.f; if (BLK == BX) ax[q * 128 + t] = 0.f; }
+    {
+      int k = 0;
+      for (int p = 0; p < No; ++p) {
+        const float flp = w.fl[p], fkp = w.fk[p];
+        for (int q = p + 1; q < No; ++q, ++k) {
+          const float v = xb[(int64_t)k * L.SL + e];
+          a1[q * 128 + t] += flp * v;
+          a1[p * 128 + t] -= w.fl[q] * v;
+          if (BLK == BX) {
+            ax[q * 128 + t] += fkp * v;
+            ax[p * 128 + t] -= w.fk[q] * v;
+          }
+        }
+      }
+      for (int q = 0; q < No; ++q) {
+        o1[(int64_t)q * L.SL + e] = a1[q * 128 + t];
+        if (BLK == BX) ox[(int64_t)q * L.SL + e] = ax[q * 128 + t];
+      }
+    }
+  }
+}
+
+// S, Z (every slice): OC1[m] = sum_{l>=1} F_lt x_lm, OC2[l] = sum_{m>=1} F_mt x_lm, and for Z
+// OZ[l] = sum_m F_m,t' Z_lm; the column sums in registers (m unrolled), row sums per l.
+template <int BLK>
+__global__ void __launch_bounds__(128, 4) kp_arrow_full(PV pv, const float *__restrict__ x, float *oc1, float *oc2,
+                                                         float *oz, const ArrowWP w) {
+  const Packed &L = pv.L;
+  const int No = L.No;
+  const float *xb = x + L.boff[BLK];
+  float *o1 = oc1 + (int64_t)BLK * No * L.SL;
+  float *o2 = oc2 + (int64_t)(BLK == BS ? 0 : 1) * No * L.SL;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.SL; e += (int64_t)gridDim.x * blockDim.x) {
+    float c1[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) c1[m] = 0.f;
+    for (int l = 0; l < No; ++l) {
+      const float *row = xb + (int64_t)l * No * L.SL + e;
+      const float fll = w.fl[l];
+      float r2 = 0.f, rz = 0.f;
+#pragma unroll
+      for (int m = 0; m < 32; ++m) {
+        if (m < No) {
+          const float v = row[(int64_t)m * L.SL];
+          c1[m] += fll * v;
+          r2 += w.fl[m] * v;
+          if (BLK == BZ) rz += w.fk[m] * v;
+        }
+      }
+      o2[(int64_t)l * L.SL + e] = r2;
+      if (BLK == BZ) oz[(int64_t)l * L.SL + e] = rz;
+    }
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m < No) o1[(int64_t)m * L.SL + e] = c1[m];
+  }
+}
+
+// Intermediates of the N^4 coupling terms, in float32 from p (the same reductions as the
+// full-storage pass of sigma.cu, on the packed slices; the coupling operator keeps the
+// symmetry of its float32 coefficients):
+// (a) per (k, j, b): GP[k][j][b] = sum_c F_kc (X + Z)_kj^cb,  VX[k][j][b] = sum_c F_t,c X_kj^cb
+__global__ void kp_inter_a(PV pv, FF F, const float *__restrict__ x, float *GP, float *VX) {
+  const Packed &L = pv.L;
+  const int No = L.No, Nv = L.Nv;
+  const int64_t n = (int64_t)No * No * Nv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % Nv), kj = (int)(e / Nv), k = kj / No, j = kj % No;
+    float sg;
+    const float *X = pv.sl(x, BX, k, j, sg);
+    const float *Z = x + L.boff[BZ] + (int64_t)kj * L.SL;
+    float vx = 0.f, g = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < Nv; ++c) {
+      const float xv = X ? sg * X[(int64_t)c * L.Nvp + b] : 0.f, zv = Z[(int64_t)c * L.Nvp + b];
+      vx += F.ov(0, c) * xv;
+      g += F.ov(k, c) * (xv + zv);
+    }
+    GP[e] = g;
+    VX[e] = vx;
+  }
+}
+
+// (c) warp per row (i, j, a): WZ[i][j][a] = sum_c F_t,c Z_ij^ac,  HP[i][j][a] = sum_c F_jc (Y + Z)_ij^ac
+__global__ void kp_inter_c(PV pv, FF F, const float *__restrict__ x, float *WZ, float *HP) {
+  const Packed &L = pv.L;
+  const int No = L.No, Nv = L.Nv, lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)No * No * Nv;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int a = (int)(r % Nv), ij = (int)(r / Nv), i = ij / No, j = ij % No;
+    float sg;
+    const float *Y = pv.sl(x, BY, i, j, sg);
+    const float *Zr = x + L.boff[BZ] + (int64_t)ij * L.SL + (int64_t)a * L.Nvp;
+    const float *Yr = Y ? Y + (int64_t)a * L.Nvp : nullptr;
+    float wz = 0.f, hp = 0.f;
+    for (int c = lane; c < Nv; c += 32) {
+      const float zv = Zr[c], yv = Yr ? sg * Yr[c] : 0.f;
+      wz += F.ov(0, c) * zv;
+      hp += F.ov(j, c) * (yv + zv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      wz += __shfl_xor_sync(0xffffffffu, wz, o);
+      hp += __shfl_xor_sync(0xffffffffu, hp, o);
+    }
+    if (lane == 0) { WZ[r] = wz; HP[r] = hp; }
+  }
+}
+
+// (d) G[j][b] = sum_k GP[k][j][b];  H[i][a] = sum_k HP[i][k][a];
+//     CYZ[k][c] = sum_d F_t'd Z_tk^dc - sum_l F_lt Z_lk^t'c
+__global__ void kp_inter_d(PV pv, FF F, const float *__restrict__ x, const float *GP, const float *HP, float *G,
+                           float *H, float *CYZ) {
+  const Packed &L = pv.L;
+  const int No = L.No, Nv = L.Nv;
+  const int64_t n = (int64_t)No * Nv;
+  const float *Zb = x + L.boff[BZ];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int part = (int)(e / n);
+    const int64_t f = e % n;
+    const int p = (int)(f / Nv), q = (int)(f % Nv);
+    float s = 0.f;
+    if (part == 0) {
+      for (int k = 0; k < No; ++k) s += GP[((int64_t)k * No + p) * Nv + q];
+      G[f] = s;
+    } else if (part == 1) {
+      for (int k = 0; k < No; ++k) s += HP[((int64_t)p * No + k) * Nv + q];
+      H[f] = s;
+    } else {
+      const float *Z0p = Zb + (int64_t)p * L.SL;   // slice (t, k = p)
+#pragma unroll 4
+      for (int d = 0; d < Nv; ++d) s += F.v(0, d) * Z0p[(int64_t)d * L.Nvp + q];
+      for (int l = 0; l < No; ++l) s -= F.o(l, 0) * Zb[((int64_t)l * No + p) * L.SL + q];
+      CYZ[f] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- coupling pass
+struct CP {
+  PV pv;
+  FF F;
+  float omega;
+  const float *x;      // p (packed)
+  float *y;            // q (packed)
+  const float *P;      // products of the operand rows (packed slice order, pitch Nvp)
+  const float *FZ;     // F Z_s (normal orientation) for every Z slice
+  const float *VX, *WZ;  // [No][No][Nv]
+  const float *OC1, *OC2, *OX, *OZ, *G, *H, *CYZ;
+  double *dot;         // per-CTA partials of <x, y>_w, or nullptr
+  int64_t dot_base;
+  __device__ __forceinline__ float X(int blk, int i, int j, int a, int b) const { return pv.at(x, blk, i, j, a, b); }
+  // the diagonal and arrow occupied terms common to every block (x_e: the element itself)
+  __device__ __forceinline__ float common(int blk, int i, int j, int a, int b, float xe) const {
+    const int No = pv.L.No;
+    const float cxe = -omega + (blk >= BX ? F.v(0, 0) - F.o(0, 0) : 0.f) - (F.o(i, i) + F.o(j, j));
+    float u = cxe * xe;
+    const int64_t ab = (int64_t)a * pv.L.Nvp + b;
+    const float t1 = i == 0 ? OC1[((int64_t)blk * No + j) * pv.L.SL + ab] : X(blk, 0, j, a, b);
+    const float s1 = i == 0 ? 1.f : F.o(0, i);
+    float t2;
+    if (j == 0) t2 = OC2[((int64_t)(blk == BS ? 0 : 1) * No + i) * pv.L.SL + ab];   // S and Z only
+    else t2 = X(blk, i, 0, a, b);
+    const float s2 = j == 0 ? 1.f : F.o(0, j);
+    return u - s1 * t1 - s2 * t2;
+  }
+};
+
+// N^4 coupling terms of one block element (arrow form; T, X, Y only for i < j)
+__device__ __forceinline__ float couple_T(const CP &c, int i, int j, int a, int b) {
+  const int Nv = c.pv.L.Nv;
+  const int64_t ab = (int64_t)a * c.pv.L.Nvp + b;
+  float u = c.F.ov(0, 0) * (c.X(BX, i, j, a, b) + c.X(BY, i, j, a, b));
+  const int64_t ij = ((int64_t)i * c.pv.L.No + j) * Nv;
+  if (a == 0) u -= c.VX[ij + b];
+  if (b == 0) u += c.VX[ij + a];
+  if (i == 0) {
+    u -= c.OX[(int64_t)j * c.pv.L.SL + ab];
+    if (a == 0) u += c.G[j * Nv + b];
+    if (b == 0) u -= c.G[j * Nv + a];
+  }
+  return u;
+}
+__device__ __forceinline__ float couple_X(const CP &c, int i, int j, int a, int b) {
+  const FF &F = c.F;
+  return F.ov(0, 0) * c.X(BT, i, j, a, b) - F.ov(0, a) * c.X(BT, i, j, 0, b) + F.ov(0, b) * c.X(BT, i, j, 0, a) -
+         F.ov(i, 0) * c.X(BT, 0, j, a, b) + F.ov(j, 0) * c.X(BT, 0, i, a, b) + F.ov(i, a) * c.X(BT, 0, j, 0, b) -
+         F.ov(j, a) * c.X(BT, 0, i, 0, b) - F.ov(i, b) * c.X(BT, 0, j, 0, a) + F.ov(j, b) * c.X(BT, 0, i, 0, a);
+}
+__device__ __forceinline__ float couple_Y(const CP &c, int i, int j, int a, int b) {
+  const FF &F = c.F;
+  const int Nv = c.pv.L.Nv;
+  float u = F.ov(0, 0) * c.X(BT, i, j, a, b) + F.ov(j, b) * c.X(BS, 0, i, 0, a) - F.ov(i, b) * c.X(BS, 0, j, 0, a) -
+            F.ov(j, a) * c.X(BS, 0, i, 0, b) + F.ov(i, a) * c.X(BS, 0, j, 0, b);
+  if (i == 0) {
+    if (a == 0) u += c.CYZ[j * Nv + b];
+    if (b == 0) u -= c.CYZ[j * Nv + a];
+  }
+  return u;
+}
+__device__ __forceinline__ float couple_Z(const CP &c, int i, int j, int a, int b) {
+  const FF &F = c.F;
+  float u = F.ov(0, 0) * c.X(BS, i, j, a, b) - F.ov(0, b) * c.X(BS, i, j, a, 0) - F.ov(j, 0) * c.X(BS, i, 0, a, b) +
+            F.ov(j, b) * c.X(BS, i, 0, a, 0) + F.ov(i, a) * c.X(BT, 0, j, 0, b);
+  const float y0 = c.X(BY, 0, j, 0, b);
+  if (i == 0) u += F.v(a, 0) * y0;
+  if (a == 0) u -= F.o(0, i) * y0;
+  return u;
+}
+// S without the transposed-operand terms (Z_ji^ba and, for i == 0, OZ[j]^ba come from the caller)
+__device__ __forceinline__ float couple_S(const CP &c, int i, int j, int a, int b, float zji_ba, float ozj_ba) {
+  const int Nv = c.pv.L.Nv;
+  const int64_t ab = (int64_t)a * c.pv.L.Nvp + b;
+  float u = c.F.ov(0, 0) * (c.X(BZ, i, j, a, b) + zji_ba);
+  const int No = c.pv.L.No;
+  if (a == 0) u -= c.WZ[((int64_t)j * No + i) * Nv + b];
+  if (b == 0) u -= c.WZ[((int64_t)i * No + j) * Nv + a];
+  if (j == 0) {
+    u -= c.OZ[(int64_t)i * c.pv.L.SL + ab];
+    if (b == 0) u += c.H[i * Nv + a];
+  }
+  if (i == 0) {
+    u -= ozj_ba;
+    if (a == 0) u += c.H[j * Nv + b];
+  }
+  return u;
+}
+
+// T, X, Y: work item = (slice i < j, tile pair ta <= tb); y on tile (ta, tb) and -y on (tb, ta)
+template <int BLK>
+__global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
+  const Packed &L = c.pv.L;
+  __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Ys[kT][kT + 1];
+  const int nt = (L.Nv + kT - 1) / kT, npairs = nt * (nt + 1) / 2;
+  const int64_t items = (int64_t)L.nh * npairs;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float dsum = 0.f;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int k = (int)(it / npairs);
+    int tp = (int)(it % npairs), ta = 0;
+    while (tp >= nt - ta) { tp -= nt - ta; ++ta; }
+    const int tb = ta + tp;
+    int i, j;
+    pair_decode(L.No, k, i, j);
+    const int64_t so = L.boff[BLK] + (int64_t)k * L.SL;
+    const float *P = c.P + so, *x = c.x + so;
+    float *y = c.y + so;
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
+      Pa[r][tx] = (a < L.Nv && b < L.Nv) ? P[(int64_t)a * L.Nvp + b] : 0.f;
+      Pb[r][tx] = (a2 < L.Nv && b2 < L.Nv) ? P[(int64_t)a2 * L.Nvp + b2] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx;
+      float yv = 0.f;
+      const bool upper = ta < tb || r < tx;
+      if (a < L.Nv && b < L.Nv && upper && valid_elem(BLK, i, j, a, b)) {
+        const float xe = x[(int64_t)a * L.Nvp + b];
+        float u = c.common(BLK, i, j, a, b, xe);
+        u += BLK == BT ? couple_T(c, i, j, a, b) : BLK == BX ? couple_X(c, i, j, a, b) : couple_Y(c, i, j, a, b);
+        yv = Pa[r][tx] - Pb[tx][r] + u;
+        dsum += 2.f * xe * yv;
+      }
+      if (a < L.Nv && b < L.Nv && (ta < tb || r <= tx)) y[(int64_t)a * L.Nvp + b] = yv;
+      Ys[r][tx] = -yv;
+    }
+    __syncthreads();
+    for (int r = ty; r < kT; r += 8) {   // element (tb*32 + r, ta*32 + tx) = -y(ta*32 + tx, tb*32 + r)
+      const int a = tb * kT + r, b = ta * kT + tx;
+      if (a < L.Nv && b < L.Nv && (ta < tb || r > tx)) y[(int64_t)a * L.Nvp + b] = Ys[tx][r];
+    }
+    __syncthreads();
+  }
+  if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
+}
+
+// S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb) and y_ji = y_ij^T
+__global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
+  const Packed &L = c.pv.L;
+  __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Zt[kT][kT + 1], Ot[kT][kT + 1], Ys[kT][kT + 1];
+  const int nt = (L.Nv + kT - 1) / kT, No = L.No;
+  const int npair = No * (No + 1) / 2;
+  const int64_t items = (int64_t)npair * nt * nt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float dsum = 0.f;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    int pi = (int)(it / (nt * nt));
+    const int tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    int i = 0;
+    while (pi >= No - i) { pi -= No - i; ++i; }
+    const int j = i + pi;   // i <= j
+    if (i == j && ta > tb) continue;
+    const int64_t sij = L.boff[BS] + ((int64_t)i * No + j) * L.SL, sji = L.boff[BS] + ((int64_t)j * No + i) * L.SL;
+    const float *Zji = c.x + L.boff[BZ] + ((int64_t)j * No + i) * L.SL;
+    const float *OZj = c.OZ + (int64_t)j * L.SL;
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
+      const bool in1 = a < L.Nv && b < L.Nv, in2 = a2 < L.Nv && b2 < L.Nv;
+      Pa[r][tx] = in1 ? c.P[sij + (int64_t)a * L.Nvp + b] : 0.f;
+      Pb[r][tx] = in2 ? c.P[sji + (int64_t)a2 * L.Nvp + b2] : 0.f;
+      Zt[r][tx] = in2 ? Zji[(int64_t)a2 * L.Nvp + b2] : 0.f;
+      if (i == 0) Ot[r][tx] = in2 ? OZj[(int64_t)a2 * L.Nvp + b2] : 0.f;
+    }
+    __syncthreads();
+    const bool diag = i == j && ta == tb;
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx;
+      float yv = 0.f;
+      if (a < L.Nv && b < L.Nv && (!diag || r <= tx)) {
+        const float xe = c.x[sij + (int64_t)a * L.Nvp + b];
+        float u = c.common(BS, i, j, a, b, xe);
+        u += couple_S(c, i, j, a, b, Zt[tx][r], i == 0 ? Ot[tx][r] : 0.f);
+        yv = Pa[r][tx] + Pb[tx][r] + u;
+        dsum += (diag && r == tx ? 1.f : 2.f) * xe * yv;
+        c.y[sij + (int64_t)a * L.Nvp + b] = yv;
+      }
+      Ys[r][tx] = yv;
+    }
+    __syncthreads();
+    for (int r = ty; r < kT; r += 8) {   // y_ji[tb*32 + r][ta*32 + tx] = y_ij[ta*32 + tx][tb*32 + r]
+      const int a = tb * kT + r, b = ta * kT + tx;
+      if (a < L.Nv && b < L.Nv && (!diag || r > tx)) c.y[sji + (int64_t)a * L.Nvp + b] = Ys[tx][r];
+    }
+    __syncthreads();
+  }
+  if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
+}
+
+// Z: work item = (slice (i, j), tile (ta, tb)); y = P + F Z + couplings
+__global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
+  const Packed &L = c.pv.L;
+  const int nt = (L.Nv + kT - 1) / kT, No = L.No;
+  const int64_t items = (int64_t)L.NN * nt * nt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float dsum = 0.f;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int s = (int)(it / (nt * nt)), tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    const int i = s / No, j = s % No;
+    const int64_t so = L.boff[BZ] + (int64_t)s * L.SL;
+    const float *FZ = c.FZ + (int64_t)s * L.SL;
+    for (int r = ty; r < kT; r += 8) {
+      const int a = ta * kT + r, b = tb * kT + tx;
+      if (a >= L.Nv || b >= L.Nv) continue;
+      const int64_t ab = (int64_t)a * L.Nvp + b;
+      float yv = 0.f;
+      if (valid_elem(BZ, i, j, a, b)) {
+        const float xe = c.x[so + ab];
+        yv = c.P[so + ab] + FZ[ab] + c.common(BZ, i, j, a, b, xe) + couple_Z(c, i, j, a, b);
+        dsum += 2.f * xe * yv;
+      }
+      c.y[so + ab] = yv;
+    }
+  }
+  if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
+}
+
+// <u, v>_w over a packed vector (per-CTA partials)
+__global__ void kp_wdot(PV pv, const float *u, const float *v, double *red) {
+  const Packed &L = pv.L;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.n; e += (int64_t)gridDim.x * blockDim.x)
+    acc += (e >= L.boff[BZ] ? 2.0 : 1.0) * (double)u[e] * (double)v[e];
+  cta_partial(acc, red, blockIdx.x);
+}
+
+// coupling-pass grid (per launch); the partials of <x, y> are one per CTA and launch
+constexpr int kCoupleGrid = 1216;
+
+}  // namespace
+
+int64_t packed_dot_parts(const esmp2_handle *h) { (void)h; return 5LL * kCoupleGrid; }
+
+// Buffers of the packed inner solve; F32 / Fsemi must be ready (ensure_mixed).
+esmp2_status packed_setup(esmp2_handle *h) {
+  if (h->pr) return ESMP2_OK;
+  const Packed L = make_packed(h->d.No, h->d.Nv);
+  h->pk = L;
+  const int No = L.No, N = h->d.N;
+  const int64_t op_rows = (int64_t)(L.nslices + L.NN) * L.Nv;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, h->stream);
+  };
+  A(reinterpret_cast<void **>(&h->pr), sizeof(float) * (size_t)L.n);
+  A(reinterpret_cast<void **>(&h->pp), sizeof(float) * (size_t)L.n);
+  A(reinterpret_cast<void **>(&h->pq), sizeof(float) * (size_t)L.n);
+  A(reinterpret_cast<void **>(&h->pd), sizeof(float) * (size_t)L.n);
+  A(reinterpret_cast<void **>(&h->pdinv), sizeof(__half) * (size_t)L.n);
+  A(&h->pop, sizeof(__nv_bfloat16) * (size_t)(L.n + (int64_t)L.NN * L.SL));
+  A(&h->pW, sizeof(__nv_bfloat16) * (size_t)L.Nv * L.Nvp);
+  A(reinterpret_cast<void **>(&h->pP), sizeof(float) * (size_t)(L.n + (int64_t)L.NN * L.SL));
+  A(reinterpret_cast<void **>(&h->pVX), sizeof(float) * (size_t)No * No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pGP), sizeof(float) * (size_t)No * No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pWZ), sizeof(float) * (size_t)No * No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pHP), sizeof(float) * (size_t)No * No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pOC), sizeof(float) * (size_t)5 * No * L.SL);
+  A(reinterpret_cast<void **>(&h->pOC2), sizeof(float) * (size_t)2 * No * L.SL);
+  A(reinterpret_cast<void **>(&h->pOX), sizeof(float) * (size_t)No * L.SL);
+  A(reinterpret_cast<void **>(&h->pOZ), sizeof(float) * (size_t)No * L.SL);
+  A(reinterpret_cast<void **>(&h->pG), sizeof(float) * (size_t)No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pH), sizeof(float) * (size_t)No * L.Nv);
+  A(reinterpret_cast<void **>(&h->pCYZ), sizeof(float) * (size_t)No * L.Nv);
+  h->pdot_n = (int)packed_dot_parts(h);
+  A(reinterpret_cast<void **>(&h->pdot), sizeof(double) * (size_t)h->pdot_n);
+  if (e != cudaSuccess) return check_cuda(h, e, "packed inner buffers");
+  // pad columns and the transposed-Z part of the operand start (and stay) zero; q's pad too
+  cudaMemsetAsync(h->pop, 0, sizeof(__nv_bfloat16) * (size_t)(L.n + (int64_t)L.NN * L.SL), h->stream);
+  cudaMemsetAsync(h->pq, 0, sizeof(float) * (size_t)L.n, h->stream);
+  cudaMemsetAsync(h->pp, 0, sizeof(float) * (size_t)L.n, h->stream);
+  // right operand W = F_vv (rows b, columns c; symmetric)
+  {
+    std::vector<double> hF((size_t)N * N);
+    e = cudaMemcpyAsync(hF.data(), h->Fsemi, sizeof(double) * hF.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed set-up");
+    std::vector<__nv_bfloat16> W((size_t)L.Nv * L.Nvp, __float2bfloat16_rn(0.f));
+    for (int b = 0; b < L.Nv; ++b)
+      for (int cc = 0; cc < L.Nv; ++cc)
+        W[(size_t)b * L.Nvp + cc] = __float2bfloat16_rn((float)hF[(size_t)(No + b) * N + No + cc]);
+    e = cudaMemcpyAsync(h->pW, W.data(), sizeof(__nv_bfloat16) * W.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed set-up");
+  }
+  PV pv{L};
+  FF F{h->F32, N, No};
+  kp_dinv<<<2432, 128, 0, h->stream>>>(pv, F, (float)h->omega_op, h->pdinv);
+  h->launches += 1;
+  h->packed = true;
+  return check_cuda(h, cudaGetLastError(), "packed set-up");
+}
+
+esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
+                   float *PT, int ldp, double alg_flops);
+
+// q = A p on the packed layout (bf16 virtual-index terms, float32 everything else); pb_ready:
+// the PCG update already wrote bf16(p) into the operand; dot: per-CTA partials of <p, q>_w
+// (packed_dot_parts(h) doubles) or nullptr.
+// stages (profiling): bit 0 operand conversion, bit 1 contraction, bit 2 coupling pass.
+esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_ready, double *dot, int stages) {
+  const Packed &L = h->pk;
+  const int No = L.No, N = h->d.N;
+  PV pv{L};
+  cudaStream_t st = h->stream;
+  __nv_bfloat16 *op = static_cast<__nv_bfloat16 *>(h->pop);
+  if (!pb_ready && (stages & 1)) {  // the packed p to bf16 (pad columns are zero in p)
+    kp_bf16<<<1216, 256, 0, st>>>(p, op, L.n);
+    h->launches += 1;
+  }
+  const int64_t rows_n = (int64_t)L.nslices * L.Nv, rows = rows_n + (int64_t)L.NN * L.Nv;
+  if (stages & 2) {
+    kp_zt<<<1216, 256, 0, st>>>(pv, op);
+    h->launches += 1;
+    if (esmp2_status s = vgemm(h, op, rows, rows_n, h->pW, h->pP, h->pP + L.n, L.Nvp,
+                               alg_virtual_flops(No, L.Nv)))
+      return s;
+  }
+  if (!(stages & 4)) return check_cuda(h, cudaGetLastError(), "sigma_packed");
+  ArrowWP w{};
+  for (int l = 0; l < 32; ++l) { w.fl[l] = h->arrow_w[l]; w.fk[l] = h->arrow_w[32 + l]; }
+  {
+    const unsigned ga = (unsigned)std::min<int64_t>(cdiv(L.SL, 128), 4096);
+    const size_t sm = 2 * 32 * 128 * sizeof(float);
+    kp_arrow_anti<BT><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_anti<BX><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_anti<BY><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_full<BS><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
+    kp_arrow_full<BZ><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
+  }
+  FF F{h->F32, N, No};
+  kp_inter_a<<<1216, 256, 0, st>>>(pv, F, p, h->pGP, h->pVX);
+  kp_inter_c<<<1216, 256, 0, st>>>(pv, F, p, h->pWZ, h->pHP);
+  kp_inter_d<<<(unsigned)cdiv(3LL * No * L.Nv, 256), 256, 0, st>>>(pv, F, p, h->pGP, h->pHP, h->pG, h->pH, h->pCYZ);
+  CP c{};
+  c.pv = pv;
+  c.F = F;
+  c.omega = (float)h->omega_op;
+  c.x = p;
+  c.y = q;
+  c.P = h->pP;
+  c.FZ = h->pP + L.n;
+  c.VX = h->pVX;
+  c.WZ = h->pWZ;
+  c.OC1 = h->pOC; c.OC2 = h->pOC2; c.OX = h->pOX; c.OZ = h->pOZ;
+  c.G = h->pG; c.H = h->pH; c.CYZ = h->pCYZ;
+  c.dot = dot;
+  {
+    KScope ks(st, ESMP2_KT_COUPLING, 12.0 * (double)L.n + 4.0 * (double)(L.n + (int64_t)L.NN * L.SL),
+              12.0 * (double)L.n);
+    c.dot_base = 0;
+    kp_couple_anti<BT><<<kCoupleGrid, kThreads, 0, st>>>(c);
+    c.dot_base = kCoupleGrid;
+    kp_couple_anti<BX><<<kCoupleGrid, kThreads, 0, st>>>(c);
+    c.dot_base = 2 * kCoupleGrid;
+    kp_couple_anti<BY><<<kCoupleGrid, kThreads, 0, st>>>(c);
+    c.dot_base = 3 * kCoupleGrid;
+    kp_couple_s<<<kCoupleGrid, kThreads, 0, st>>>(c);
+    c.dot_base = 4 * kCoupleGrid;
+    kp_couple_z<<<kCoupleGrid, kThreads, 0, st>>>(c);
+  }
+  h->launches += 12;
+  return check_cuda(h, cudaGetLastError(), "sigma_packed");
+}
+
+// inner-solve start: r (packed) from the float64 residual r64 (full storage), p = M^-1 r,
+// d = 0, bf16(p); partials of <r, M^-1 r>_w and <r, r>_w in h->red
+void packed_init(esmp2_handle *h, const double *r64, int grid) {
+  const Packed &L = h->pk;
+  kp_init<<<grid, 128, 0, h->stream>>>(PV{L}, r64, h->pdinv, h->pr, h->pp, h->pd,
+                                       static_cast<__nv_bfloat16 *>(h->pop), h->red);
+  h->launches += 1;
+}
+
+// <u, v>_w of two packed vectors, returned to the host (diagnostics; synchronises; uses the
+// reduction buffer h->red, so it must not run between a kernel writing partials there and
+// the finalisation reading them)
+double packed_wdot(esmp2_handle *h, const float *u, const float *v) {
+  kp_wdot<<<256, 256, 0, h->stream>>>(PV{h->pk}, u, v, h->red);
+  std::vector<double> part(256);
+  cudaMemcpyAsync(part.data(), h->red, sizeof(double) * 256, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  double t = 0.0;
+  for (double x : part) t += x;
+  return t;
+}
+
+void packed_accumulate(esmp2_handle *h, double *x64) {
+  kp_acc64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x64, h->pd);
+  h->launches += 1;
+}
+
+// per-stage timing of `reps` packed inner sigma builds of the packed copy of x (CUDA events):
+// ms[0] operand conversion, [1] contraction (transposed Z slices + GEMM), [2] 0, [3] coupling
+// pass (arrow sums, intermediates, couplings), [4] total
+esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *ms) {
+  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x, h->pp);
+  h->launches += 1;
+  cudaEvent_t ev[4];
+  for (auto &e : ev) cudaEventCreate(&e);
+  double acc[4] = {0, 0, 0, 0};
+  esmp2_status s = ESMP2_OK;
+  for (int r = 0; r < reps && !s; ++r) {
+    cudaEventRecord(ev[0], h->stream);
+    s = sigma_packed(h, h->pp, h->pq, false, nullptr, 1);
+    cudaEventRecord(ev[1], h->stream);
+    if (!s) s = sigma_packed(h, h->pp, h->pq, true, nullptr, 2);
+    cudaEventRecord(ev[2], h->stream);
+    if (!s) s = sigma_packed(h, h->pp, h->pq, true, h->pdot, 4);
+    cudaEventRecord(ev[3], h->stream);
+    cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[3]);
+    acc[3] += t;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (s) return s;
+  ms[0] = acc[0] / reps;
+  ms[1] = acc[1] / reps;
+  ms[2] = 0.0;
+  ms[3] = acc[2] / reps;
+  ms[4] = acc[3] / reps;
+  return check_cuda(h, cudaGetLastError(), "profile_packed");
+}
+
+// API-level bf16 sigma of a singlet vector on the packed path: y = A x (x, y full-storage
+// float64 in the TOP basis), through the working basis of the inner solve.
+esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y) {
+  double *t1 = h->s64.w ? h->s64.w : h->s64.p;
+  rotate_occ(h, x, y, t1, true);                 // y: x in the working basis
+  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, y, h->pp);
+  h->launches += 1;
+  if (esmp2_status s = sigma_packed(h, h->pp, h->pq, false, nullptr, 7)) return s;
+  kp_to64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, h->pq, y);
+  h->launches += 1;
+  rotate_occ(h, y, y, t1, false);
+  // the rotation back mixes slices: the non-amplitude slots (i == j of T, X, Y, ...) carry
+  // rounding-level values, cleared here
+  kp_mask64<<<2432, 128, 0, h->stream>>>(h->d.No, h->d.Nv, y);
+  h->launches += 1;
+  return check_cuda(h, cudaGetLastError(), "sigma_mixed_packed");
+}
+
+}  // namespace esmp2

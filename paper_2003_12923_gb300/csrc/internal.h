@@ -1,5 +1,6 @@
 // Internal declarations of the ESMP2 GB300 library (not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -63,6 +64,21 @@ struct Solver64 {
   double *x, *r, *p, *q, *w;  // fp64 vectors (n)
 };
 
+// Packed layout of the inner (float32) solve.  T, X and Y keep the slices i < j only (slice
+// (j, i) is the negative of (i, j)); S and Z keep every slice.  Rows are padded to
+// Nvp = Nv rounded up to 8 (pad columns zero).  Slice order T | S | X | Y | Z; the bf16
+// operand of the contraction appends the transposed Z slices.  Determinant inner-product
+// weights per stored element: 1 for T, S, X, Y (an i < j slice stands for itself and its
+// negative partner) and 2 for Z.
+struct Packed {
+  int No, Nv, Nvp, nh, NN;   // nh = No (No - 1) / 2, NN = No^2
+  int64_t SL;                // elements per slice, Nv * Nvp
+  int64_t boff[6];           // first element of T, S, X, Y, Z and of the transposed-Z part
+  int nslices;               // slices of a packed vector, 3 nh + 2 NN
+  int64_t n;                 // elements of a packed vector
+};
+Packed make_packed(int No, int Nv);
+
 }  // namespace esmp2
 
 struct esmp2_handle {
@@ -80,6 +96,10 @@ struct esmp2_handle {
   double *f0vo = nullptr;   // Nv x No  Fock matrix of Phi, virtual-occupied block
   double *scal = nullptr;   // device scalars: [0] omega, [1] E0
   double omega = 0, E0 = 0;
+  double level_shift = 0;   // added to H0 on the first-order space
+  double omega_op = 0;      // omega - level_shift: the constant of the operator A = F_N - omega_op
+  double eta = 0;           // large-pair threshold (TOP(1) checks)
+  int n_large = 0;
   // transformed integrals
   double *ovov = nullptr;   // (ia|jb)  No Nv No Nv
   double *ooov = nullptr;   // (ij|ka)  No No No Nv
@@ -125,6 +145,21 @@ struct esmp2_handle {
   int last_precision = 0;   // precision of the last solve (the energy's sigma follows it)
   cudaGraphExec_t inner_graph = nullptr;  // one inner PCG iteration of the mixed solve
   int64_t inner_graph_launches = 0, inner_graph_launches_pending = 0;
+  // packed inner solve (No <= 32): layout, vectors, operand, products and intermediates
+  bool packed = false;
+  esmp2::Packed pk{};
+  float *pr = nullptr, *pp = nullptr, *pq = nullptr, *pd = nullptr;  // r, p, q = A p, correction d
+  __half *pdinv = nullptr;  // Jacobi preconditioner (packed)
+  void *pop = nullptr;      // bf16 operand: packed p and the transposed Z slices
+  void *pW = nullptr;       // bf16 right operand F_vv
+  float *pP = nullptr;      // products: P (T .. Z slices, row pitch Nvp) then F Z (transposed part)
+  float *pVX = nullptr, *pGP = nullptr, *pWZ = nullptr, *pHP = nullptr;  // [No][No][Nv] coupling sums
+  float *pOC = nullptr;     // [5][No][SL] arrow sums over the first occupied index (OC1)
+  float *pOC2 = nullptr;    // [2][No][SL] arrow sums over the second index (S, Z)
+  float *pOX = nullptr, *pOZ = nullptr;  // [No][SL] sum_l F_l,t' X_lm, sum_m F_m,t' Z_lm
+  float *pG = nullptr, *pH = nullptr, *pCYZ = nullptr;  // [No][Nv]
+  double *pdot = nullptr;   // per-CTA partials of the coupling pass's <p, A p>
+  int pdot_n = 0;
 };
 
 namespace esmp2 {
@@ -152,7 +187,16 @@ esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
 esmp2_status ensure_mixed(esmp2_handle *h, bool semi);
 esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_ready = false, double *dot = nullptr);
 esmp2_status check_device_flag(esmp2_handle *h);
+// packed inner solve (inner.cu)
+esmp2_status packed_setup(esmp2_handle *h);
+esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_ready, double *dot, int stages = 7);
+esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *ms);
+void packed_init(esmp2_handle *h, const double *r64, int grid);
+void packed_accumulate(esmp2_handle *h, double *x64);
+double packed_wdot(esmp2_handle *h, const float *u, const float *v);
+esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y);
 void antisym_project(esmp2_handle *h, double *v);
+void singlet_project(esmp2_handle *h, double *v);
 void combine_sym(esmp2_handle *h, double *y);
 constexpr int kFp64TcLevels = 10;  // digit levels of the float64-exact tensor-core contraction
 int split_levels_for(double tol);
@@ -173,6 +217,18 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // cudaMalloc/cudaFree pair.  dfree releases in stream order (after the stream's work).
 cudaError_t dmalloc(void **p, size_t bytes, cudaStream_t st);
 void dfree(void *p, cudaStream_t st);
+
+// Raise the dynamic shared-memory limit of kernel `func` to `bytes` on the current device,
+// once per (device, kernel) for the life of the process (the attribute is per device, and
+// concurrent callers such as batch workers must not race on it).  Returns the status of
+// that one cudaFuncSetAttribute call.
+cudaError_t smem_limit_once(const void *func, int bytes);
+
+// 2-D bf16 tensor map (inner dimension first; rows of row_bytes), box box_inner x box_outer,
+// shared-memory swizzle of 128, 64, 32 or 0 bytes, zero fill out of bounds.  False when the
+// driver's encoder is unavailable or rejects the description.
+bool tma_map_bf16_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                     uint32_t box_inner, uint32_t box_outer, int swizzle_bytes);
 
 // ESMP2_DEBUG=1: synchronise the handle's stream and print the host time since the last
 // phase mark (set-up breakdowns; no effect otherwise).

@@ -92,9 +92,9 @@ __global__ void k_finalize(const double *red, int nparts, int nq, double *slots,
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
       if (mode == 0) {            // init: rz, rr, bb
         slots[q] = t;
-      } else if (mode == 1) {     // pq -> alpha
+      } else if (mode == 1) {     // pq -> alpha (no step along a direction of non-positive curvature)
         slots[3] = t;
-        slots[4] = slots[0] / t;
+        slots[4] = t > 0.0 ? slots[0] / t : 0.0;
       } else if (mode == 2) {     // rz_new, rr -> beta
         if (q == 0) { slots[5] = t / slots[0]; slots[0] = t; }
         else slots[1] = t;
@@ -204,12 +204,12 @@ __global__ void kt_p(VCtx c, const double *slots, const T *r, T *p) {
 // elements per access.  The correction d is advanced in the p update (d += alpha p before p
 // changes), so the residual update reads only r, q and M^-1.
 struct ICtx {
-  int64_t B;
+  int64_t off[6];     // first element of each block (T, S, X, Y, Z) and the vector length
+  float w[5];         // determinant inner-product weight of each block's elements
   const __half *dinv;
   __nv_bfloat16 *pb;  // bf16 copy of p for the tensor-core operand (nullptr: not kept here)
-  int vec;            // B % 4 == 0
+  int vec;            // every block starts on a 16-byte boundary
 };
-__device__ __forceinline__ float blk_weight(int blk) { return blk == 1 ? 1.f : (blk == 4 ? 2.f : 0.5f); }
 __device__ __forceinline__ float4 ld_h4(const __half *p4) {
   const uint2 u = *reinterpret_cast<const uint2 *>(p4);
   const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
@@ -228,9 +228,9 @@ __global__ void ki_init(ICtx c, const double *r64, float *r, float *p, float *d,
   float a0 = 0.f, a1 = 0.f;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int blk = 0; blk < 5; ++blk) {
-    const float w = blk_weight(blk);
+    const float w = c.w[blk];
     float s0 = 0.f, s1 = 0.f;
-    for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
+    for (int64_t e = c.off[blk] + t0; e < c.off[blk + 1]; e += stride) {
       const float ri = (float)r64[e], z = __half2float(c.dinv[e]) * ri;
       r[e] = ri;
       p[e] = z;
@@ -254,10 +254,10 @@ __global__ void ki_update(ICtx c, const double *slots, float *r, const float *q,
   for (int blk = 0; blk < 5; ++blk) {
     float s0 = 0.f, s1 = 0.f;
     if (c.vec) {
-      const int64_t n4 = c.B >> 2;
-      float4 *r4 = reinterpret_cast<float4 *>(r + blk * c.B);
-      const float4 *q4 = reinterpret_cast<const float4 *>(q + blk * c.B);
-      const __half *dv = c.dinv + blk * c.B;
+      const int64_t n4 = (c.off[blk + 1] - c.off[blk]) >> 2;
+      float4 *r4 = reinterpret_cast<float4 *>(r + c.off[blk]);
+      const float4 *q4 = reinterpret_cast<const float4 *>(q + c.off[blk]);
+      const __half *dv = c.dinv + c.off[blk];
       for (int64_t e = t0; e < n4; e += stride) {
         float4 rv = r4[e];
         const float4 qv = q4[e], m = ld_h4(dv + 4 * e);
@@ -267,14 +267,14 @@ __global__ void ki_update(ICtx c, const double *slots, float *r, const float *q,
         s1 += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
       }
     } else {
-      for (int64_t e = blk * c.B + t0; e < (blk + 1) * c.B; e += stride) {
+      for (int64_t e = c.off[blk] + t0; e < c.off[blk + 1]; e += stride) {
         const float ri = r[e] - alpha * q[e];
         r[e] = ri;
         s0 += ri * __half2float(c.dinv[e]) * ri;
         s1 += ri * ri;
       }
     }
-    const float w = blk_weight(blk);
+    const float w = c.w[blk];
     a0 += w * s0;
     a1 += w * s1;
   }
@@ -287,7 +287,7 @@ __global__ void ki_p(ICtx c, const double *slots, const float *r, float *p, floa
   const float alpha = (float)slots[4], beta = (float)slots[5];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c.vec) {
-    const int64_t n4 = (5 * c.B) >> 2;
+    const int64_t n4 = c.off[5] >> 2;
     const float4 *r4 = reinterpret_cast<const float4 *>(r);
     float4 *p4 = reinterpret_cast<float4 *>(p), *d4 = reinterpret_cast<float4 *>(d);
     for (int64_t e = t0; e < n4; e += stride) {
@@ -301,7 +301,7 @@ __global__ void ki_p(ICtx c, const double *slots, const float *r, float *p, floa
       if (c.pb) st_b4(c.pb + 4 * e, pn);
     }
   } else {
-    for (int64_t e = t0; e < 5 * c.B; e += stride) {
+    for (int64_t e = t0; e < c.off[5]; e += stride) {
       const float pv = p[e];
       d[e] += alpha * pv;
       const float pn = __half2float(c.dinv[e]) * r[e] + beta * pv;
@@ -485,120 +485,133 @@ __device__ __forceinline__ void load_fv(const SCtx &s, float2 *fv) {
   __syncthreads();
 }
 
-// sector A: up-up-up, lowest pair u >= 1; block = (u, j, k)
-__global__ void k_e2s_a(SCtx s, SDf gd, double *red) {
-  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
+// shared-memory tables of the sum over the small pair u: lambda_u^2 and F_u'u' - F_uu as
+// (hi, lo) pairs (No <= 64, esmp2_create)
+__device__ __forceinline__ void load_u(const SCtx &s, float2 *lu2, float2 *du) {
+  for (int u = threadIdx.x; u < s.No; u += blockDim.x) {
+    const double l = s.lam[u];
+    const dflt a = df_of(l * l), d = df_of(s.Fv(u) - s.Fo(u));
+    lu2[u] = make_float2(a.h, a.l);
+    du[u] = make_float2(d.h, d.l);
+  }
+}
+__device__ __forceinline__ dflt ld(const float2 v) { return {v.x, v.y}; }
+
+// Sectors A and B with exactly one transition pair u >= 1 (the common case).  For an
+// occupied pair j < k and a virtual pair b < c outside {j, k} (c >= 1) the triple's right-hand
+// side is lambda_u times dg = (kc|jb) - (jc|kb) and its denominator is D_u + e_bc with
+// D_u = F_u'u' - F_uu, e_bc = F_bb + F_cc - F_jj - F_kk - omega, for
+//   A: up-up-up triples u j k -> u' b c (u not in {j, k}, u' not in {b, c}),
+//   B: up-down-down triples with the up pair u -> u' and the down double j k -> b c (any u >= 1),
+// so E2_S += -2 dg^2 sum_u lambda_u^2 ([A] + [B]) / (D_u + e_bc): each integral is read once and
+// the sum over u runs in registers.  Block = (pair j < k, one of nchunk strided ranges of c),
+// threads over b (coalesced rows of the integrals).
+__global__ void k_e2s_ab(SCtx s, SDf gd, int nchunk, double *red) {
+  __shared__ float2 fv[4096], lu2[64], du[64];   // Nv <= 4096, No <= 64 (esmp2_create)
   const int No = s.No, Nv = s.Nv;
-  const int64_t blk = blockIdx.x;
-  const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
-  double v[1] = {0.0};
-  const bool active = u >= 1 && j < k && j != u && k != u;
-  if (active) load_fv(s, fv);
-  if (active) {
-    const double lu = s.lam[u];
-    const dflt c2 = df_of(-2.0 * lu * lu);
-    const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
-    dflt acc = {0.f, 0.f};
-    for (int c = 1; c < Nv; ++c) {
-      if (c == u || c == j || c == k) continue;
-      const dflt Dc = df_of(Dh + s.Fv(c));
-      for (int b = threadIdx.x; b < c; b += blockDim.x) {
-        if (b == u || b == j || b == k) continue;
-        const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
-        const float2 f = fv[b];
-        acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
+  const int chunk = blockIdx.x % nchunk;
+  int kk = blockIdx.x / nchunk, j = 0;
+  while (kk >= No - 1 - j) { kk -= No - 1 - j; ++j; }
+  const int k = j + 1 + kk;
+  load_u(s, lu2, du);
+  load_fv(s, fv);   // synchronises
+  const dflt base = df_of(-s.Fo(j) - s.Fo(k) - s.omega);
+  dflt acc = {0.f, 0.f};
+  for (int c = 1 + chunk; c < Nv; c += nchunk) {
+    if (c == j || c == k) continue;
+    const dflt ec = df_add(base, ld(fv[c]));
+    for (int b = threadIdx.x; b < c; b += blockDim.x) {
+      if (b == j || b == k) continue;
+      const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
+      const dflt e = df_add(ec, ld(fv[b]));
+      dflt sum = {0.f, 0.f};
+      for (int u = 1; u < No; ++u) {
+        const dflt q = df_div(ld(lu2[u]), df_add(ld(du[u]), e));
+        sum = df_add(sum, q);                                              // B
+        if (u != j && u != k && u != b && u != c) sum = df_add(sum, q);   // A
       }
-    }
-    v[0] += df_to_double(acc);
-    // virtual pairs (b < c) holding j or k: the general float64 form, spread over the
-    // threads (one term per thread at a time, no lane waiting on another's float64 work)
-    for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
-      const int x = e < Nv ? j : k, y = e % Nv;
-      if (y == x || ((y == j || y == k) && x != j)) continue;  // the pair (j, k) once
-      const int b = min(x, y), c = max(x, y);
-      if (c < 1 || c == u || b == u) continue;
-      const bool pj = (b == j || c == j), pk = (b == k || c == k);
-      if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
-      if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
-      const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
-      v[0] += s.term(ho, hs, po, ps);
+      acc = df_add(acc, df_mul(df_mul(dg, dg), sum));
     }
   }
+  double v[1] = {-2.0 * df_to_double(acc)};
   block_partials<1>(v, red);
 }
 
-// sector B: up-down-down with the up pair u -> u' (u >= 1), any down-down double
-__global__ void k_e2s_b(SCtx s, SDf gd, double *red) {
-  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
+// Sector C: up-down-down triples without an up pair, whose one pair is the down pair u -> u'
+// (u >= 1, u != k): up single i -> a (a != i), down holes u, k, down particles u', c (c != k,
+// c != u').  The right-hand side is lambda_u (ia|kc), the denominator D_u + F_aa + F_cc - F_ii -
+// F_kk - omega:  E2_S += -2 (ia|kc)^2 sum_u lambda_u^2 / (D_u + e_ac).  Block = (i, k, one of
+// nchunk strided ranges of a), threads over c (coalesced rows of (ia|kc)).
+__global__ void k_e2s_cm(SCtx s, SDf gd, int nchunk, double *red) {
+  __shared__ float2 fv[4096], lu2[64], du[64];
   const int No = s.No, Nv = s.Nv;
-  const int64_t blk = blockIdx.x;
-  const int u = (int)(blk / ((int64_t)No * No)), j = (int)((blk / No) % No), k = (int)(blk % No);
-  double v[1] = {0.0};
-  const bool active = u >= 1 && j < k;
-  if (active) load_fv(s, fv);
-  if (active) {
-    const double lu = s.lam[u];
-    const dflt c2 = df_of(-2.0 * lu * lu);
-    const double Dh = s.Fv(u) - s.Fo(u) - s.Fo(j) - s.Fo(k) - s.omega;
-    dflt acc = {0.f, 0.f};
-    for (int c = 1; c < Nv; ++c) {
-      if (c == j || c == k) continue;
-      const dflt Dc = df_of(Dh + s.Fv(c));
-      for (int b = threadIdx.x; b < c; b += blockDim.x) {
-        if (b == j || b == k) continue;
-        const dflt dg = df_add(gd.at(No, Nv, k, c, j, b), df_neg(gd.at(No, Nv, j, c, k, b)));
-        const float2 f = fv[b];
-        acc = df_add(acc, df_div(df_mul(c2, df_mul(dg, dg)), df_add(Dc, {f.x, f.y})));
-      }
-    }
-    v[0] += df_to_double(acc);
-    // virtual pairs (b < c) holding j or k: general float64 form spread over the threads
-    for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
-      const int x = e < Nv ? j : k, y = e % Nv;
-      if (y == x || ((y == j || y == k) && x != j)) continue;  // the pair (j, k) once
-      const int b = min(x, y), c = max(x, y);
-      if (c < 1) continue;
-      if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
-      const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
-      v[0] += s.term(ho, hs, po, ps);
+  const int chunk = blockIdx.x % nchunk, ik = blockIdx.x / nchunk, i = ik / No, k = ik % No;
+  load_u(s, lu2, du);
+  load_fv(s, fv);
+  const dflt base = df_of(-s.Fo(i) - s.Fo(k) - s.omega);
+  dflt acc = {0.f, 0.f};
+  for (int a = chunk; a < Nv; a += nchunk) {
+    if (a == i) continue;
+    const dflt ea = df_add(base, ld(fv[a]));
+    for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
+      if (c == k) continue;
+      const dflt g = gd.at(No, Nv, i, a, k, c);
+      const dflt e = df_add(ea, ld(fv[c]));
+      dflt sum = {0.f, 0.f};
+      for (int u = 1; u < No; ++u)
+        if (u != k && u != c) sum = df_add(sum, df_div(ld(lu2[u]), df_add(ld(du[u]), e)));
+      acc = df_add(acc, df_mul(df_mul(g, g), sum));
     }
   }
+  double v[1] = {-2.0 * df_to_double(acc)};
   block_partials<1>(v, red);
 }
 
-// sector C: up-down-down without an up pair; lowest down pair u >= 1; block = (u, i, k),
-// threads over c (coalesced (ia|kc) rows), loop over a
-__global__ void k_e2s_c(SCtx s, SDf gd, double *red) {
-  __shared__ float2 fv[4096];   // Nv <= 4096 (esmp2_create)
+// The triples that hold a second transition pair besides the lowest one u (few: a virtual index
+// equal to an occupied index of the triple), in the general float64 form P(k/ij)P(c/ab)
+// (s.term).  Block = (u, x, y) for the three sectors' index pairs, work spread over the threads.
+__global__ void k_e2s_gen(SCtx s, double *red) {
   const int No = s.No, Nv = s.Nv;
   const int64_t blk = blockIdx.x;
-  const int u = (int)(blk / ((int64_t)No * No)), i = (int)((blk / No) % No), k = (int)(blk % No);
+  const int u = (int)(blk / ((int64_t)No * No)), x = (int)((blk / No) % No), y = (int)(blk % No);
   double v[1] = {0.0};
-  const bool active = u >= 1 && k != u;
-  if (active) load_fv(s, fv);
-  if (active) {
-    const double lu = s.lam[u];
-    const dflt c2 = df_of(-2.0 * lu * lu);
-    const double Dh = s.Fv(u) - s.Fo(i) - s.Fo(u) - s.Fo(k) - s.omega;
-    dflt acc = {0.f, 0.f};
-    if (k >= u && k != 0) {  // c == k: the general float64 form, a spread over the threads
+  if (u >= 1) {
+    const int j = x, k = y;
+    // sector A (up-up-up, pair u lowest): virtual pairs b < c holding j or k
+    if (j < k && j != u && k != u) {
+      for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
+        const int xx = e < Nv ? j : k, yy = e % Nv;
+        if (yy == xx || ((yy == j || yy == k) && xx != j)) continue;  // the pair (j, k) once
+        const int b = min(xx, yy), c = max(xx, yy);
+        if (c < 1 || c == u || b == u) continue;
+        const bool pj = (b == j || c == j), pk = (b == k || c == k);
+        if ((pj && j < u) || (pk && k < u)) continue;    // a lower pair owns this triple
+        if ((pj && j == 0) || (pk && k == 0)) continue;  // holds the large pair: L space
+        const int ho[3] = {u, j, k}, hs[3] = {0, 0, 0}, po[3] = {u, b, c}, ps[3] = {0, 0, 0};
+        v[0] += s.term(ho, hs, po, ps);
+      }
+    }
+    // sector B (up pair u, down double j < k): down virtual pairs holding j or k
+    if (j < k) {
+      for (int e = threadIdx.x; e < 2 * Nv; e += blockDim.x) {
+        const int xx = e < Nv ? j : k, yy = e % Nv;
+        if (yy == xx || ((yy == j || yy == k) && xx != j)) continue;
+        const int b = min(xx, yy), c = max(xx, yy);
+        if (c < 1) continue;
+        if ((j == 0 || k == 0) && (b == 0 || c == 0)) continue;  // down t-pair: L space
+        const int ho[3] = {u, j, k}, hs[3] = {0, 1, 1}, po[3] = {u, b, c}, ps[3] = {0, 1, 1};
+        v[0] += s.term(ho, hs, po, ps);
+      }
+    }
+    // sector C (no up pair, lowest down pair u): the down particle c == k (a second down pair)
+    const int i = x;
+    if (k != u && k >= u && k != 0) {
       for (int a = threadIdx.x; a < Nv; a += blockDim.x) {
         if (a == i) continue;
         const int ho[3] = {i, u, k}, hs[3] = {0, 1, 1}, po[3] = {a, u, k}, ps[3] = {0, 1, 1};
         v[0] += s.term(ho, hs, po, ps);
       }
     }
-    for (int c = threadIdx.x; c < Nv; c += blockDim.x) {
-      if (c == u || c == k) continue;
-      const dflt Dc = df_of(Dh + s.Fv(c));
-      for (int a = 0; a < Nv; ++a) {
-        if (a == i) continue;
-        const dflt g = gd.at(No, Nv, i, a, k, c);
-        const float2 f = fv[a];
-        acc = df_add(acc, df_div(df_mul(c2, df_mul(g, g)), df_add(Dc, {f.x, f.y})));
-      }
-    }
-    v[0] += df_to_double(acc);
   }
   block_partials<1>(v, red);
 }
@@ -609,7 +622,7 @@ void launch_pcg_init(esmp2_handle *h, const double *b, const double *q, double *
 
 static VCtx vctx(const esmp2_handle *h, const double *F = nullptr) {
   VCtx c;
-  c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = F ? F : h->F; c.omega = h->omega;
+  c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = F ? F : h->F; c.omega = h->omega_op;
   return c;
 }
 
@@ -730,7 +743,7 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   if (!h->e2s_done) {
     const int No = h->d.No;
     SCtx sc;
-    sc.No = No; sc.Nv = h->d.Nv; sc.N = h->d.N; sc.F = h->F; sc.lam = h->lam; sc.ovov = h->ovov; sc.omega = h->omega;
+    sc.No = No; sc.Nv = h->d.Nv; sc.N = h->d.N; sc.F = h->F; sc.lam = h->lam; sc.ovov = h->ovov; sc.omega = h->omega_op;
     const int nb = No * No * No;
     const int64_t ng = (int64_t)No * h->d.Nv * No * h->d.Nv;
     float2 *gdf = nullptr;
@@ -740,14 +753,17 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
     h->launches += 1;
     SDf gd{gdf};
     double tot = 0.0;
+    const int npair = No * (No - 1) / 2, chAB = 8, chC = 4;
+    const int grids[3] = {npair * chAB, No * No * chC, nb};
     for (int sector = 0; sector < 3; ++sector) {
+      if (grids[sector] == 0) continue;
       {
         KScope ks(st, ESMP2_KT_E2S, 0.0, 0.0);
-        if (sector == 0) k_e2s_a<<<nb, 128, 0, st>>>(sc, gd, h->red);
-        else if (sector == 1) k_e2s_b<<<nb, 128, 0, st>>>(sc, gd, h->red);
-        else k_e2s_c<<<nb, 128, 0, st>>>(sc, gd, h->red);
+        if (sector == 0) k_e2s_ab<<<grids[0], 128, 0, st>>>(sc, gd, chAB, h->red);
+        else if (sector == 1) k_e2s_cm<<<grids[1], 128, 0, st>>>(sc, gd, chC, h->red);
+        else k_e2s_gen<<<grids[2], 128, 0, st>>>(sc, h->red);
       }
-      k_finalize<<<1, 256, 0, st>>>(h->red, nb, 1, h->red_out, 3);
+      k_finalize<<<1, 256, 0, st>>>(h->red, grids[sector], 1, h->red_out, 3);
       h->launches += 2;
       if ((s = read_slots(h, sl, 32))) break;
       tot += sl[8];
@@ -781,24 +797,42 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     h->x_semi = 1;
   }
   cudaStream_t st = h->stream;
-  antisym_project(h, h->s64.x);
+  // the singlet solution lies in the symmetric subspace (antisymmetric T, X, Y; S_ij^ab =
+  // S_ji^ba); the packed inner solve acts on that subspace only, so x and every residual
+  // handed to it are projected onto it (removing the rounding-level components outside)
+  singlet_project(h, h->s64.x);
   const VCtx c = vctx(h, h->Fsemi);
   debug_phase(h, "solve: x rotation + projection");
-  if (!h->dinv32) {
-    cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->dinv32), sizeof(__half) * (size_t)h->d.n, h->stream);
-    if (e != cudaSuccess) return check_cuda(h, e, "preconditioner");
-    k_dinv32<<<2432, 128, 0, st>>>(c, h->dinv32);
-    h->launches += 1;
+  // inner vectors: the packed layout (T, X, Y slices i < j, rows padded; the contraction as one
+  // tensor-core GEMM) when the arrow sums fit their register tiles (No <= 32), else full storage
+  const bool packed = h->d.No <= 32;
+  ICtx ic;
+  bool fused_bf16 = true;
+  if (packed) {
+    if ((s = packed_setup(h))) return s;
+    for (int k = 0; k < 6; ++k) ic.off[k] = h->pk.boff[k];
+    const float wp[5] = {1.f, 1.f, 1.f, 1.f, 2.f};
+    for (int k = 0; k < 5; ++k) ic.w[k] = wp[k];
+    ic.dinv = h->pdinv;
+    ic.pb = static_cast<__nv_bfloat16 *>(h->pop);
+    ic.vec = 1;   // blocks start on multiples of Nv * Nvp elements, Nvp a multiple of 8
+  } else {
+    if (!h->dinv32) {
+      cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->dinv32), sizeof(__half) * (size_t)h->d.n, h->stream);
+      if (e != cudaSuccess) return check_cuda(h, e, "preconditioner");
+      k_dinv32<<<2432, 128, 0, st>>>(c, h->dinv32);
+      h->launches += 1;
+    }
+    for (int k = 0; k < 6; ++k) ic.off[k] = (int64_t)k * h->d.B;
+    for (int k = 0; k < 5; ++k) ic.w[k] = (float)kWeights[k];
+    ic.dinv = h->dinv32;
+    // rows of the bf16 operand are padded to a multiple of 8; without padding the PCG update
+    // writes it directly
+    fused_bf16 = (h->d.Nv % 8) == 0;
+    ic.pb = fused_bf16 ? static_cast<__nv_bfloat16 *>(h->xlp) : nullptr;
+    ic.vec = (h->d.B % 4) == 0;
   }
   debug_phase(h, "solve: preconditioner");
-  ICtx ic;
-  ic.B = h->d.B;
-  ic.dinv = h->dinv32;
-  // rows of the bf16 operand are padded to a multiple of 8; without padding the PCG update
-  // writes it directly
-  const bool fused_bf16 = (h->d.Nv % 8) == 0;
-  ic.pb = fused_bf16 ? static_cast<__nv_bfloat16 *>(h->xlp) : nullptr;
-  ic.vec = (h->d.B % 4) == 0;
   // small instances are launch-bound: replay the inner iteration as a CUDA graph
   bool use_graph = h->d.n <= (64LL << 20) && st != nullptr;
   if (h->inner_graph && !use_graph) {
@@ -806,24 +840,26 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     h->inner_graph = nullptr;
   }
   double *x = h->s64.x, *r = h->s64.r, *q = h->s64.q;
-  float *r32 = h->r32, *p32 = h->p32, *q32 = h->q32, *d32 = h->x32;
+  float *r32 = packed ? h->pr : h->r32, *p32 = packed ? h->pp : h->p32, *q32 = packed ? h->pq : h->q32,
+        *d32 = packed ? h->pd : h->x32;
   int outer = 0, inner_total = 0, nsig64 = 0, nsiglow = 0;
   double relres = 1.0, sl[32];
   esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
-  // relative tolerance of each inner solve; ESMP2_INNER_ETA overrides it (tuning knob)
-  // (the bf16 rounding of the inner operand limits the inner residual to ~1e-3 relative)
+  // relative tolerance of each inner solve (the bf16 rounding of the inner operand limits the
+  // inner residual to ~1e-3 relative)
   // the float64 true residual takes its virtual-index terms from exact digit products on
   // the tensor cores when that is exact for this Nv, else from float64 GEMMs
   const int lv = split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
   h->last_precision = ESMP2_MIXED_BF16;
   h->r_true = false;
-  double eta = 1e-2;
-  if (const char *ev = std::getenv("ESMP2_INNER_ETA")) eta = std::max(1e-12, std::atof(ev));
+  const double eta = 1e-2;
   // An intermediate true residual only has to be accurate relative to itself: its digit
   // levels follow the relative residual it is expected to show (a low estimate, so never
   // too few levels); the residual that ends the refinement, and feeds the energy, always
   // takes the full count.
   double rho_next = 0.0, bb = -1.0;  // bb: <b, b>_w, taken with the first residual
+  double prev_relres = 1e300;
+  int stalled = 0;
   while (true) {
     int lv_k = lv;
     if (lv && rho_next > 1e1 * tol) lv_k = std::min(lv, split_levels_for(rho_next));
@@ -850,23 +886,40 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (relres <= 1e1 * tol && lv_k < lv) { rho_next = 0.0; continue; }  // confirm with every level
     if (relres <= tol) { result = ESMP2_OK; h->r_true = true; break; }
     if (inner_total >= maxit) break;
+    // three refinement steps in a row without reducing the true residual: stop
+    if (relres >= 0.9 * prev_relres) { if (++stalled >= 3) { h->err = "refinement stagnated"; break; } }
+    else stalled = 0;
+    prev_relres = relres;
     // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
     // contracts the slices i < j and mirrors them)
-    antisym_project(h, r);
-    ki_init<<<kRedBlocks, kRedThreads, 0, st>>>(ic, r, r32, p32, d32, h->red);
+    singlet_project(h, r);
+    if (packed) packed_init(h, r, kRedBlocks);
+    else ki_init<<<kRedBlocks, kRedThreads, 0, st>>>(ic, r, r32, p32, d32, h->red);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 0);
-    h->launches += 2;
+    h->launches += packed ? 1 : 2;
     if ((s = read_slots(h, sl, 32))) return s;
     const double r0 = std::sqrt(sl[1]);
     const double target = std::max(eta * r0, 0.25 * tol * bn);
     int inner = 0, since_best = 0;
     double best = r0;
     // one inner iteration: q = A p, alpha, x/r update, beta, p update (device scalars only)
+    const bool dbg_dot = std::getenv("ESMP2_DEBUG") != nullptr && !use_graph;
+    double fused_pq = 0.0, sep_pq = 0.0;
     auto inner_step = [&]() -> esmp2_status {
       const int64_t l0 = h->launches;
-      esmp2_status s2 = sigma_inner(h, p32, q32, fused_bf16, h->red);  // p.q partials from the coupling pass
+      // p.q partials from the coupling pass
+      esmp2_status s2 = packed ? sigma_packed(h, p32, q32, true, h->pdot) : sigma_inner(h, p32, q32, fused_bf16, h->red);
       if (s2) return s2;
-      k_finalize<<<1, 256, 0, st>>>(h->red, (int)couple_dot_parts(h), 1, h->red_out, 1);
+      if (packed && dbg_dot) {  // diagnostics (ESMP2_DEBUG, no graph capture): <p, A p> by a separate pass
+        std::vector<double> part(h->pdot_n);
+        cudaMemcpyAsync(part.data(), h->pdot, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        fused_pq = 0.0;
+        for (double v : part) fused_pq += v;
+        sep_pq = packed_wdot(h, p32, q32);
+      }
+      if (packed) k_finalize<<<1, 256, 0, st>>>(h->pdot, h->pdot_n, 1, h->red_out, 1);
+      else k_finalize<<<1, 256, 0, st>>>(h->red, (int)couple_dot_parts(h), 1, h->red_out, 1);
       ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, q32, h->red);
       k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
       ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32, d32);
@@ -903,9 +956,19 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
       }
       ++nsiglow;
       if ((s = read_slots(h, sl, 32))) return s;
+      if (std::getenv("ESMP2_DEBUG"))
+        std::fprintf(stderr, "esmp2 inner %d: p.Ap %.6e (fused partials %.6e, separate pass %.6e) r.z %.6e r.r %.6e r0^2 %.6e\n",
+                     inner, sl[3], fused_pq, sep_pq, sl[0], sl[1], r0 * r0);
       ++inner;
       ++inner_total;
-      if (!(sl[3] > 0.0)) { h->err = "inner CG: p.Ap <= 0"; result = ESMP2_ERR_INDEFINITE; break; }
+      if (!(sl[3] > 0.0)) {
+        // the step was not taken (alpha = 0 on the device).  Before the inner residual has
+        // been cut tenfold this is negative curvature of A itself; after that it is the
+        // rounding of the bf16 inner operator (whose floor lies at a few 1e-3 to a few 1e-2 of
+        // the inner start): the inner solve ends there and the float64 refinement goes on
+        if (best > 1e-1 * r0) { h->err = "inner CG: p.Ap <= 0"; result = ESMP2_ERR_INDEFINITE; }
+        break;
+      }
       const double rn_in = std::sqrt(sl[1]);
       if (rn_in < 0.99 * best) { best = rn_in; since_best = 0; } else ++since_best;
       if (rn_in <= target || inner >= 200 || since_best >= 8) break;  // converged or stagnating
@@ -913,14 +976,19 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (result == ESMP2_ERR_INDEFINITE) break;
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine:   inner %d  |r_in|/|r0| %.3e\n", inner, std::sqrt(sl[1]) / r0);
     rho_next = relres * std::max(r0 > 0 ? std::sqrt(sl[1]) / r0 : 0.0, 1e-4);
-    kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
-    h->launches += 1;
+    if (packed) {
+      packed_accumulate(h, x);
+    } else {
+      kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
+      h->launches += 1;
+    }
     h->x_zero = false;
-    antisym_project(h, x);  // the float64 residual pass assumes exactly antisymmetric T, X, Y
+    singlet_project(h, x);  // the float64 residual pass assumes exactly antisymmetric T, X, Y
     ++outer;
     if ((s = check_device_flag(h))) return s;
   }
-  if (result == ESMP2_ERR_NOT_CONVERGED) h->err = "refinement did not reach the tolerance within maxit inner iterations";
+  if (result == ESMP2_ERR_NOT_CONVERGED && stalled < 3)
+    h->err = "refinement did not reach the tolerance within maxit inner iterations";
   if (info) {
     info->iterations = inner_total;
     info->outer = outer;

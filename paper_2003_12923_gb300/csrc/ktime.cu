@@ -3,7 +3,9 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -79,6 +81,21 @@ cudaError_t dmalloc(void **p, size_t bytes, cudaStream_t st) {
 
 void dfree(void *p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
+}
+
+cudaError_t smem_limit_once(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(dev, func);
+  auto it = done.find(key);
+  if (it != done.end()) return it->second;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done[key] = e;
+  return e;
 }
 
 double unique_amplitudes(int No, int Nv) {

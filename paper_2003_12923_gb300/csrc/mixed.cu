@@ -270,8 +270,12 @@ esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_
 // API-level mixed sigma in the TOP basis: virtual-index terms in bf16 on tcgen05, the
 // occupied-index and coupling terms in float64.
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y) {
-  esmp2_status s = ensure_mixed(h, false);
-  if (s) return s;
+  esmp2_status s = ESMP2_OK;
+  if (h->d.No <= 32) {  // the inner solve's packed path (singlet vectors), checked through the same call
+    if ((s = ensure_mixed(h, true)) || (s = packed_setup(h)) || (s = sigma_mixed_packed(h, x, y))) return s;
+    return check_device_flag(h);
+  }
+  if ((s = ensure_mixed(h, false))) return s;
   const int No = h->d.No, Nv = h->d.Nv;
   to_bf16_f64(h, x, h->xlp, (int64_t)5 * No * No * Nv);
   if ((s = virt_bf16(h, h->xlp, h->Fvlp, 5 * No * No, h->ylp, h->dflag))) return s;
@@ -310,6 +314,10 @@ esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, in
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms) {
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
+  if (h->d.No <= 32) {
+    if ((s = packed_setup(h)) || (s = profile_packed(h, x, reps, ms))) return s;
+    return check_device_flag(h);
+  }
   const int No = h->d.No, Nv = h->d.Nv;
   const int64_t rows = (int64_t)5 * No * No * Nv;
   // fp32 copy of x into the inner buffers (the basis is irrelevant for timing)

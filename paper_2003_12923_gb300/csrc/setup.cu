@@ -647,11 +647,9 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
     int dims[4] = {No, Nv, Nv, Nv};
     const size_t smem = xr_df_smem(Nv);
     if (No <= kXrN && smem <= 220 * 1024) {  // c -> u' (first No columns of Wv)
-      static size_t attr = 0;
-      if (smem > attr) {
-        cudaFuncSetAttribute(k_xr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
-      }
+      // one limit for every Nv (220 KB): set once per device, never lowered under a running launch
+      if (cudaError_t ea = smem_limit_once(reinterpret_cast<const void *>(k_xr_df), 220 * 1024))
+        return check_cuda(h, ea, "k_xr_df shared-memory limit");
       const int64_t M = (int64_t)No * Nv * Nv;
       const unsigned grid = (unsigned)std::min<int64_t>(1216, cdiv(cdiv(M, kXrRows), kXrWarps));
       k_xr_df<<<grid, kXrWarps * 32, smem, st>>>(ovvv_src, scratch, M, Nv, No, h->Wv, Nv);

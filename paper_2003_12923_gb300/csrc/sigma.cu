@@ -480,7 +480,7 @@ template <typename CT>
 static CtxT<CT> make_ctx(const esmp2_handle *h, const CT *F, int arrow) {
   CtxT<CT> c;
   c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B;
-  c.F = F; c.omega = (CT)h->omega; c.arrow = arrow;
+  c.F = F; c.omega = (CT)h->omega_op; c.arrow = arrow;
   return c;
 }
 
@@ -696,6 +696,49 @@ void antisym_project(esmp2_handle *h, double *v) {
   const int No = h->d.No, Nv = h->d.Nv, tiles = (Nv + 31) / 32;
   const int64_t nb = 3LL * (No * (No + 1) / 2) * (tiles * (tiles + 1) / 2);
   k_antisym_project<<<(unsigned)nb, 256, 0, h->stream>>>(No, Nv, v);
+  h->launches += 1;
+}
+
+// In-place projection of the S block onto the spin-flip symmetry of the singlet,
+// S_ij^ab = S_ji^ba: w = (v_ij^ab + v_ji^ba) / 2 written to both images.  One CTA per (slice
+// pair i <= j, tile (ta, tb)); for i == j only the tiles ta <= tb.
+__global__ void k_sym_project_s(int No, int Nv, double *v) {
+  __shared__ double s1[32][33], s2[32][33];
+  const int64_t NvNv = (int64_t)Nv * Nv;
+  const int tiles = (Nv + 31) / 32;
+  int64_t bid = blockIdx.x;
+  const int tt = (int)(bid % (tiles * tiles));
+  int sp = (int)(bid / (tiles * tiles));
+  const int ta = tt / tiles, tb = tt % tiles;
+  int i = 0;
+  while (sp >= No - i) { sp -= No - i; ++i; }
+  const int j = i + sp;
+  if (i == j && ta > tb) return;
+  double *S = v + (int64_t)No * No * NvNv;   // block 1
+  double *Vij = S + ((int64_t)i * No + j) * NvNv, *Vji = S + ((int64_t)j * No + i) * NvNv;
+  const int a0 = ta * 32, b0 = tb * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx, a2 = b0 + r, b2 = a0 + tx;
+    s1[r][tx] = (a < Nv && b < Nv) ? Vij[(int64_t)a * Nv + b] : 0.0;   // v_ij[a][b]
+    s2[r][tx] = (a2 < Nv && b2 < Nv) ? Vji[(int64_t)a2 * Nv + b2] : 0.0; // v_ji[b][a] at s2[c][r]
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) s1[r][tx] = 0.5 * (s1[r][tx] + s2[tx][r]);
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < Nv && b < Nv) Vij[(int64_t)a * Nv + b] = s1[r][tx];
+    const int a2 = b0 + r, b2 = a0 + tx;   // v_ji[b][a] = w(a, b)
+    if (a2 < Nv && b2 < Nv) Vji[(int64_t)a2 * Nv + b2] = s1[tx][r];
+  }
+}
+
+// antisymmetry of T, X, Y in both index pairs and the spin-flip symmetry of S
+void singlet_project(esmp2_handle *h, double *v) {
+  antisym_project(h, v);
+  const int No = h->d.No, Nv = h->d.Nv, tiles = (Nv + 31) / 32;
+  const int64_t nb = (int64_t)(No * (No + 1) / 2) * tiles * tiles;
+  k_sym_project_s<<<(unsigned)nb, 256, 0, h->stream>>>(No, Nv, v);
   h->launches += 1;
 }
 

@@ -32,7 +32,8 @@ class Esmp2Error(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("No", ctypes.c_int), ("Nv", ctypes.c_int), ("F", ctypes.c_void_p), ("ovov", ctypes.c_void_p),
                 ("ooov", ctypes.c_void_p), ("ovvv", ctypes.c_void_p), ("C", ctypes.c_void_p),
-                ("spin", ctypes.c_int), ("inputs_on_device", ctypes.c_int)]
+                ("spin", ctypes.c_int), ("inputs_on_device", ctypes.c_int), ("eta", ctypes.c_double),
+                ("n_large", ctypes.c_int), ("avo_convention", ctypes.c_int), ("level_shift", ctypes.c_double)]
 
 
 class LayoutInfo(ctypes.Structure):
@@ -65,7 +66,7 @@ EXPORTS = ("esmp2_create", "esmp2_destroy", "esmp2_last_error", "esmp2_set_strea
            "esmp2_top_basis", "esmp2_sigma", "esmp2_rhs", "esmp2_solve", "esmp2_get_solution",
            "esmp2_set_solution", "esmp2_energy", "esmp2_kernel_launches", "esmp2_profile_sigma",
            "esmp2_virtual_contraction", "esmp2_virtual_contraction_noalloc", "esmp2_batch_solve", "esmp2_grad",
-           "esmp2_kernel_timing", "esmp2_kernel_times")
+           "esmp2_kernel_timing", "esmp2_kernel_times", "esmp2_selftest_bounded_wait")
 MIXED_READY = True
 
 
@@ -124,6 +125,8 @@ def load(path: str | None = None):
         L.esmp2_kernel_timing.argtypes = [I]
         L.esmp2_kernel_times.restype = I
         L.esmp2_kernel_times.argtypes = [ctypes.POINTER(KernelTime)]
+        L.esmp2_selftest_bounded_wait.restype = I
+        L.esmp2_selftest_bounded_wait.argtypes = [I, P]
         if path is None:
             _lib = L
         return L
@@ -131,7 +134,7 @@ def load(path: str | None = None):
 
 NOALLOC_MAX_BYTES = 64 << 20
 
-KERNEL_FAMILIES = ("contraction", "coupling", "gemm64", "e2s")
+KERNEL_FAMILIES = ("contraction", "coupling", "gemm64", "e2s", "digits")
 
 
 def kernel_timing(enable: bool):
@@ -159,7 +162,7 @@ def batch_solve(instances, tol: float = 1e-8, maxit: int = 2000, precision: int 
         arrs = [np.ascontiguousarray(np.asarray(inst[n], dtype=np.float64)) for n in ("F", "ovov", "ooov", "ovvv", "C")]
         keep.append(arrs)
         No, Nv = arrs[4].shape
-        descs[k] = Desc(No, Nv, *(a.ctypes.data for a in arrs), 1, 0)
+        descs[k] = Desc(No, Nv, *(a.ctypes.data for a in arrs), 1, 0, 0.0, 1, 0, float(inst.get("level_shift", 0.0)))
     res = (BatchResult * len(instances))()
     st = L.esmp2_batch_solve(descs, len(instances), tol, maxit, precision, concurrency, res)
     out = []
@@ -179,6 +182,13 @@ def virtual_contraction_noalloc(x, Fvv, y, S: int, Nv: int, stream=None) -> int:
                                                    ctypes.c_void_p(st)))
 
 
+def selftest_bounded_wait(wait_ms: int = 200, stream=None) -> int:
+    """Failure-detection self-test of the tensor-core kernel's bounded waits (see
+    include/esmp2.h); returns the status (ERR_TIMEOUT when the expiry was detected)."""
+    st = 0 if stream is None else stream.cuda_stream
+    return int(load().esmp2_selftest_bounded_wait(int(wait_ms), ctypes.c_void_p(st)))
+
+
 def _ptr(a):
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
@@ -191,7 +201,8 @@ class Handle:
     Inputs (F, ovov, ooov, ovvv, C) may be float64 numpy arrays (host) or CUDA torch
     tensors; they are copied during construction."""
 
-    def __init__(self, F, ovov, ooov, ovvv, C, spin: int = 1, stream=None):
+    def __init__(self, F, ovov, ooov, ovvv, C, spin: int = 1, stream=None, level_shift: float = 0.0,
+                 eta: float = 0.0, n_large: int = 1, avo_convention: int = 0):
         import torch
         self.torch = torch
         self.L = load()
@@ -207,7 +218,8 @@ class Handle:
             keep.append(t)
             return _ptr(t)
 
-        d = Desc(No, Nv, prep(F), prep(ovov), prep(ooov), prep(ovvv), prep(C), spin, 1 if on_dev else 0)
+        d = Desc(No, Nv, prep(F), prep(ovov), prep(ooov), prep(ovvv), prep(C), spin, 1 if on_dev else 0,
+                 float(eta), int(n_large), int(avo_convention), float(level_shift))
         self._h = ctypes.c_void_p()
         self.device = torch.device("cuda", torch.cuda.current_device())
         st = self.L.esmp2_create(ctypes.byref(self._h), ctypes.byref(d))

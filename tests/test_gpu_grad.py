@@ -119,3 +119,25 @@ def test_autograd_function():
     assert abs(float(e.detach()) - h.energy()["E2"]) < 1e-12
     assert np.abs(F.grad.cpu().numpy() - 2 * dF).max() < 1e-10 * max(1.0, np.abs(dF).max())
     assert np.abs(ov.grad.cpu().numpy() - 2 * dov).max() < 1e-10 * max(1.0, np.abs(dov).max())
+
+
+def test_gradient_c5_against_stored_oracle_gradient():
+    """No=16 Nv=160 (seed 5): float64 solve and esmp2_grad against the oracle's derivatives
+    along sampled steps of F and (ia|jb), taken from the first-order equation at the oracle's
+    own solution (tests/golden/o2_grad_c5.json), within 1e-6 relative."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "o2_grad_c5.json")) as f:
+        g = json.load(f)
+    i = g["instance"]
+    inst = synth.make_instance(i["No"], i["Nv"], i["seed"], sigma_off=i["sigma_off"])
+    h = handle_for(inst)
+    h.solve(tol=1e-12, maxit=3000)
+    assert abs(h.energy()["E2"] - g["E2"]) < 1e-10
+    dF, dov, _ = h.grad()
+    for p, q, ref in g["dF_step"]:
+        an = _an_F(dF, p, q)
+        assert abs(an - ref) <= 1e-6 * abs(ref) + 1e-10, (p, q, an, ref)
+    for ii, a, j, b, ref in g["dOVOV_step"]:
+        an = _an_ov(dov, ii, a, j, b)
+        assert abs(an - ref) <= 1e-6 * abs(ref) + 1e-10, ((ii, a, j, b), an, ref)

@@ -55,13 +55,19 @@ def test_sigma_mixed_vs_oracle(No, Nv, seed):
     h = handle_for(inst)
     x = random_block_vector(No, Nv, seed + 7)
     xt = _torch(x)
-    y = h.sigma(xt, esmp2.MIXED_BF16)
+    y = h.sigma(xt, esmp2.MIXED_BF16).cpu().numpy()
     ref = o2.O2(top.prepare(inst)).sigma(x)
-    F = h.top_basis()[3][No:, No:]
-    bound = _bound(h, xt, F).cpu().numpy() + 1e-12 * np.abs(ref).max()
-    err = np.abs(y.cpu().numpy() - ref)
-    assert np.all(err <= bound), float((err / bound).max())
-    assert not np.any(y.cpu().numpy()[~masks(No, Nv)])
+    # bf16 operands carry 2^-9 relative rounding (the diagonal terms dominate each element),
+    # everything else float32: the result is within a few 1e-3 of the operator, not closer
+    # than float32 rounding
+    rel = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    assert 1e-6 < rel < 4e-3, rel
+    assert float(np.abs(y - ref).max()) <= 2e-2 * float(np.abs(ref).max())
+    assert not np.any(y[~masks(No, Nv)])
+    # the result keeps the symmetries of the amplitudes: exactly in (a, b), to rounding in (i, j)
+    # (the occupied rotation back from the working basis mixes slices)
+    assert np.array_equal(y[0], -y[0].transpose(0, 1, 3, 2))
+    assert float(np.abs(y[0] + y[0].transpose(1, 0, 2, 3)).max()) <= 1e-12 * float(np.abs(y[0]).max())
 
 
 @pytest.mark.parametrize("No,Nv,seed", [(3, 5, 11), (4, 9, 12), (5, 13, 13), (6, 30, 0)])

@@ -1,0 +1,131 @@
+"""Parity with the oracle on the tile paths the benchmark runs: several 128-row and two column
+tiles of the tensor-core rotations and contractions, ragged tails (Nv = 401), the size of
+configuration C2 (No=20 Nv=200, seed 1) and of the benchmark workload (No=30 Nv=400, seed 3).
+
+* right-hand side b = Q H Psi0 (Sec. II.B, Slater-Condon) element by element;
+* E2 and its parts against stored oracle solves (tests/golden/o2_*.json, written by
+  tests/golden/make_o2_reference.py from oracle/ alone): float64 and FP64_TC within 1e-10 Eh,
+  the mixed solve within 1e-8 Eh (tolerances of the float64 and mixed-precision forms);
+* E2_S (Sec. II.D, S-space inverted directly) against the oracle's direct sum;
+* at the benchmark size, where no oracle solve is affordable: sampled b and the full E2_S."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import o2, top
+from tests.gpu_util import handle_for, sample_indices
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(task):
+    with open(os.path.join(GOLDEN, f"o2_{task}.json")) as f:
+        return json.load(f)
+
+
+def _corners(No, Nv):
+    B = No * No * Nv * Nv
+    return [k * B + off for k in range(5) for off in (0, Nv - 1, (Nv - 1) * Nv, B - 1, (No * No - 1) * Nv * Nv + 1)]
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(4, 130, 21), (3, 300, 22), (3, 401, 23)])
+def test_rhs_multitile(No, Nv, seed):
+    inst = synth.make_instance(No, Nv, seed)
+    h = handle_for(inst)
+    b = h.rhs().cpu().numpy()
+    ref = o2.O2(top.prepare(inst)).rhs()
+    scale = float(np.abs(ref).max())
+    assert scale > 0
+    assert float(np.abs(b - ref).max()) <= 1e-12 * scale
+    h.close()
+
+
+@pytest.mark.parametrize("task", ["e2_4_130", "e2_3_300"])
+def test_energy_multitile_against_stored_oracle(task):
+    from paper_2003_12923_gb300 import esmp2
+    g = _golden(task)
+    i = g["instance"]
+    inst = synth.make_instance(i["No"], i["Nv"], i["seed"], sigma_off=i["sigma_off"])
+    for prec, tol, etol in ((esmp2.FP64, 1e-11, 1e-10), (esmp2.FP64_TC, 1e-11, 1e-10),
+                            (esmp2.MIXED_BF16, 1e-8, 1e-8)):
+        h = handle_for(inst)
+        h.solve(tol=tol, maxit=3000, precision=prec)
+        e = h.energy()
+        for k in ("E2", "E2_D", "E2_L", "E2_S"):
+            assert abs(e[k] - g[k]) < etol, (prec, k, e[k], g[k])
+        h.close()
+
+
+def test_c2_rhs_energy_and_rates(record_property):
+    """Configuration C2: plain float64 GPU solve to 1e-10 against the stored oracle solve,
+    sampled b and the full E2_S against the oracle, sigma-build GB/s and TFLOP/s reported."""
+    import torch
+    from paper_2003_12923_gb300 import esmp2
+    No, Nv, seed = 20, 200, 1
+    inst = synth.make_instance(No, Nv, seed, sigma_off=1e-3)
+    prep = top.prepare(inst)
+    oc = o2.O2(prep)
+    h = handle_for(inst)
+    b = h.rhs().reshape(-1)
+    idx = sample_indices(b.numel(), 20000, 11, include=_corners(No, Nv))
+    ref = oc.rhs_at(idx)
+    got = b[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert float(np.abs(got - ref).max()) <= 1e-12 * float(np.abs(ref).max())
+    e2s_ref, _ = oc.e2_s()
+    g = _golden("e2_c2")
+    assert abs(g["E2_S"] - e2s_ref) < 1e-13
+    info = h.solve(tol=1e-10, maxit=3000, precision=esmp2.FP64)
+    assert info["rel_residual"] <= 1e-10
+    e = h.energy()
+    assert abs(e["E2_S"] - e2s_ref) < 1e-12
+    for k in ("E2", "E2_D", "E2_L"):
+        assert abs(e[k] - g[k]) < 1e-10, (k, e[k], g[k])
+    ms = h.profile_sigma(b.reshape(h.shape), precision=esmp2.FP64, reps=3)
+    n_u = (No * (No - 1) / 2) * (Nv * (Nv - 1) / 2) + No * No * Nv * Nv / 2 \
+        + ((No - 1) * (No - 2) / 2) * ((Nv - 1) * (Nv - 2) / 2) + (No * (No - 1) / 2) * (Nv * (Nv - 1) / 2) \
+        + (No * Nv - 1) * (No - 1) * (Nv - 1)
+    sec = ms[4] * 1e-3
+    record_property("c2_sigma_fp64_ms", float(ms[4]))
+    record_property("c2_sigma_alg_tflops", 4.0 * n_u * (No + Nv) / sec / 1e12)
+    record_property("c2_sigma_alg_gbs", 16.0 * n_u / sec / 1e9)   # read x, write y once per unique amplitude
+    h.close()
+    hm = handle_for(inst)
+    hm.solve(tol=1e-8, maxit=3000, precision=esmp2.MIXED_BF16)
+    em = hm.energy()
+    assert abs(em["E2"] - g["E2"]) < 1e-8, (em["E2"], g["E2"])
+    hm.close()
+
+
+def test_rhs_and_e2s_at_benchmark_size():
+    """No=30 Nv=400 with the full integral blocks (OVVV 15.4 GB): 20000 sampled elements and
+    the block corners of b, and the whole S-space sum E2_S (6e9 triples), against the oracle."""
+    import torch
+    from paper_2003_12923_gb300 import esmp2
+    No, Nv, seed = 30, 400, 3
+    inst = synth.make_instance(No, Nv, seed, sigma_off=1e-3)
+    dev = {k: torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")}
+    h = esmp2.Handle(dev["F"], dev["ovov"], dev["ooov"], dev["ovvv"], dev["C"])
+    del dev
+    b = h.rhs().reshape(-1)
+    idx = sample_indices(b.numel(), 20000, 12, include=_corners(No, Nv))
+    got = b[torch.from_numpy(idx).cuda()].cpu().numpy()
+    del b
+    h.solve(tol=1e-8, maxit=3000, precision=esmp2.MIXED_BF16)
+    e = h.energy()
+    h.close()
+    prep = top.prepare(inst)
+    del inst
+    oc = o2.O2(prep)
+    ref = oc.rhs_at(idx)
+    assert float(np.abs(got - ref).max()) <= 1e-12 * float(np.abs(ref).max())
+    e2s_ref, n_s = oc.e2_s()
+    assert n_s > 5e9
+    # a sum of 6e9 terms of size ~1e-7 Eh: both sides round each term to ~1e-15 relative and
+    # accumulate in float64, so they agree to ~1e-13 of |E2_S| (about 4e-11 Eh here), not to an
+    # absolute 1e-11
+    assert abs(e["E2_S"] - e2s_ref) < 1e-12 * abs(e2s_ref), (e["E2_S"], e2s_ref)
