@@ -276,25 +276,36 @@ __global__ void kp_bf16(const float *src, __nv_bfloat16 *dst, int64_t n) {
     dst[e] = __float2bfloat16_rn(src[e]);
 }
 
-// the transposed Z slices of the bf16 operand: op[ZT(s)][b][a] = op[Z(s)][a][b]
-__global__ void kp_zt(PV pv, __nv_bfloat16 *op) {
+// the transposed Z slices of the bf16 operand: op[ZT(s)][b][a] = op[Z(s)][a][b].  64 x 64 tiles;
+// a lane moves a pair of bf16 values, so a warp reads and writes whole 128-byte rows.
+__global__ void __launch_bounds__(256) kp_zt(PV pv, __nv_bfloat16 *op) {
   const Packed &L = pv.L;
-  __shared__ __nv_bfloat16 t[kT][kT + 2];
-  const int nt = (L.Nv + kT - 1) / kT;
+  __shared__ __nv_bfloat16 t[64][66];
+  const int Nv = L.Nv, Nvp = L.Nvp, nt = (Nv + 63) / 64;
   const int64_t items = (int64_t)L.NN * nt * nt;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int s = (int)(it / (nt * nt)), tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
     const __nv_bfloat16 *src = op + L.boff[BZ] + (int64_t)s * L.SL;
     __nv_bfloat16 *dst = op + L.boff[5] + (int64_t)s * L.SL;
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx;
-      t[r][tx] = (a < L.Nv && b < L.Nv) ? src[(int64_t)a * L.Nvp + b] : __float2bfloat16_rn(0.f);
+    for (int r = w; r < 64; r += 8) {   // rows a = ta*64 + r, columns b = tb*64 + 2 lane (+1)
+      const int a = ta * 64 + r, b = tb * 64 + 2 * lane;
+      __nv_bfloat162 v;
+      if (a < Nv && b + 1 < Nvp) v = *reinterpret_cast<const __nv_bfloat162 *>(src + (int64_t)a * Nvp + b);
+      else v = __halves2bfloat162(zero, zero);
+      t[r][2 * lane] = v.x;
+      t[r][2 * lane + 1] = v.y;
     }
     __syncthreads();
-    for (int r = ty; r < kT; r += 8) {
-      const int b = tb * kT + r, a = ta * kT + tx;
-      if (a < L.Nv && b < L.Nv) dst[(int64_t)b * L.Nvp + a] = t[tx][r];
+    for (int r = w; r < 64; r += 8) {   // rows b = tb*64 + r of the transposed slice, columns a
+      const int b = tb * 64 + r, a = ta * 64 + 2 * lane;
+      if (b < Nv && a + 1 < Nvp) {
+        __nv_bfloat162 v;
+        v.x = a < Nv ? t[2 * lane][r] : zero;
+        v.y = a + 1 < Nv ? t[2 * lane + 1][r] : zero;
+        *reinterpret_cast<__nv_bfloat162 *>(dst + (int64_t)b * Nvp + a) = v;
+      }
     }
     __syncthreads();
   }
@@ -307,36 +318,45 @@ struct ArrowWP {
 };
 
 // T, X, Y (packed i < j): OC1[q][e] = sum_{l>=1} F_lt x_lq[e] (x_lq = -x_ql for l > q), and for X
-// also OX[m][e] = sum_l F_l,t' X_lm[e].  One thread per element e of a slice; the No column sums
-// are shared-memory accumulators indexed [q][thread].
+// also OX[m][e] = sum_l F_l,t' X_lm[e].  One thread per element e of a slice; both occupied
+// indices are unrolled (No <= 32), so every stored pair is read once and both of its
+// contributions go to register accumulators with constant indices.
 template <int BLK>
 __global__ void __launch_bounds__(128) kp_arrow_anti(PV pv, const float *__restrict__ x, float *oc1, float *ox,
                                                       const ArrowWP w) {
   const Packed &L = pv.L;
-  extern __shared__ float acc[];   // [2][32][128]
-  float *a1 = acc, *ax = acc + 32 * 128;
-  const int No = L.No, t = threadIdx.x;
+  const int No = L.No;
   const float *xb = x + L.boff[BLK];
   float *o1 = oc1 + (int64_t)BLK * No * L.SL;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + t; e < L.SL; e += (int64_t)gridDim.x * blockDim.x) {
-    for (int q = 0; q < No; ++q) { a1[q * 128 + t] = 0.f; if (BLK == BX) ax[q * 128 + t] = 0.f; }
-    {
-      int k = 0;
-      for (int p = 0; p < No; ++p) {
-        const float flp = w.fl[p], fkp = w.fk[p];
-        for (int q = p + 1; q < No; ++q, ++k) {
-          const float v = xb[(int64_t)k * L.SL + e];
-          a1[q * 128 + t] += flp * v;
-          a1[p * 128 + t] -= w.fl[q] * v;
-          if (BLK == BX) {
-            ax[q * 128 + t] += fkp * v;
-            ax[p * 128 + t] -= w.fk[q] * v;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.SL; e += (int64_t)gridDim.x * blockDim.x) {
+    float c1[32], cx[BLK == BX ? 32 : 1];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) c1[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < (BLK == BX ? 32 : 1); ++q) cx[q] = 0.f;
+#pragma unroll
+    for (int p = 0; p < 31; ++p) {
+      if (p < No) {
+        const int64_t kb = (int64_t)p * No - p * (p + 1) / 2 - p - 1;   // pair (p, q) = kb + q
+#pragma unroll
+        for (int q = p + 1; q < 32; ++q) {
+          if (q < No) {
+            const float v = xb[(kb + q) * L.SL + e];
+            c1[q] += w.fl[p] * v;
+            c1[p] -= w.fl[q] * v;
+            if constexpr (BLK == BX) {
+              cx[q] += w.fk[p] * v;
+              cx[p] -= w.fk[q] * v;
+            }
           }
         }
       }
-      for (int q = 0; q < No; ++q) {
-        o1[(int64_t)q * L.SL + e] = a1[q * 128 + t];
-        if (BLK == BX) ox[(int64_t)q * L.SL + e] = ax[q * 128 + t];
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      if (q < No) {
+        o1[(int64_t)q * L.SL + e] = c1[q];
+        if constexpr (BLK == BX) ox[(int64_t)q * L.SL + e] = cx[q];
       }
     }
   }
@@ -472,142 +492,135 @@ struct CP {
   const float *OC1, *OC2, *OX, *OZ, *G, *H, *CYZ;
   double *dot;         // per-CTA partials of <x, y>_w, or nullptr
   int64_t dot_base;
-  __device__ __forceinline__ float X(int blk, int i, int j, int a, int b) const { return pv.at(x, blk, i, j, a, b); }
-  // the diagonal and arrow occupied terms common to every block (x_e: the element itself)
-  __device__ __forceinline__ float common(int blk, int i, int j, int a, int b, float xe) const {
-    const int No = pv.L.No;
-    const float cxe = -omega + (blk >= BX ? F.v(0, 0) - F.o(0, 0) : 0.f) - (F.o(i, i) + F.o(j, j));
-    float u = cxe * xe;
-    const int64_t ab = (int64_t)a * pv.L.Nvp + b;
-    const float t1 = i == 0 ? OC1[((int64_t)blk * No + j) * pv.L.SL + ab] : X(blk, 0, j, a, b);
-    const float s1 = i == 0 ? 1.f : F.o(0, i);
-    float t2;
-    if (j == 0) t2 = OC2[((int64_t)(blk == BS ? 0 : 1) * No + i) * pv.L.SL + ab];   // S and Z only
-    else t2 = X(blk, i, 0, a, b);
-    const float s2 = j == 0 ? 1.f : F.o(0, j);
-    return u - s1 * t1 - s2 * t2;
-  }
 };
 
-// N^4 coupling terms of one block element (arrow form; T, X, Y only for i < j)
-__device__ __forceinline__ float couple_T(const CP &c, int i, int j, int a, int b) {
-  const int Nv = c.pv.L.Nv;
-  const int64_t ab = (int64_t)a * c.pv.L.Nvp + b;
-  float u = c.F.ov(0, 0) * (c.X(BX, i, j, a, b) + c.X(BY, i, j, a, b));
-  const int64_t ij = ((int64_t)i * c.pv.L.No + j) * Nv;
-  if (a == 0) u -= c.VX[ij + b];
-  if (b == 0) u += c.VX[ij + a];
-  if (i == 0) {
-    u -= c.OX[(int64_t)j * c.pv.L.SL + ab];
-    if (a == 0) u += c.G[j * Nv + b];
-    if (b == 0) u -= c.G[j * Nv + a];
-  }
-  return u;
-}
-__device__ __forceinline__ float couple_X(const CP &c, int i, int j, int a, int b) {
-  const FF &F = c.F;
-  return F.ov(0, 0) * c.X(BT, i, j, a, b) - F.ov(0, a) * c.X(BT, i, j, 0, b) + F.ov(0, b) * c.X(BT, i, j, 0, a) -
-         F.ov(i, 0) * c.X(BT, 0, j, a, b) + F.ov(j, 0) * c.X(BT, 0, i, a, b) + F.ov(i, a) * c.X(BT, 0, j, 0, b) -
-         F.ov(j, a) * c.X(BT, 0, i, 0, b) - F.ov(i, b) * c.X(BT, 0, j, 0, a) + F.ov(j, b) * c.X(BT, 0, i, 0, a);
-}
-__device__ __forceinline__ float couple_Y(const CP &c, int i, int j, int a, int b) {
-  const FF &F = c.F;
-  const int Nv = c.pv.L.Nv;
-  float u = F.ov(0, 0) * c.X(BT, i, j, a, b) + F.ov(j, b) * c.X(BS, 0, i, 0, a) - F.ov(i, b) * c.X(BS, 0, j, 0, a) -
-            F.ov(j, a) * c.X(BS, 0, i, 0, b) + F.ov(i, a) * c.X(BS, 0, j, 0, b);
-  if (i == 0) {
-    if (a == 0) u += c.CYZ[j * Nv + b];
-    if (b == 0) u -= c.CYZ[j * Nv + a];
-  }
-  return u;
-}
-__device__ __forceinline__ float couple_Z(const CP &c, int i, int j, int a, int b) {
-  const FF &F = c.F;
-  float u = F.ov(0, 0) * c.X(BS, i, j, a, b) - F.ov(0, b) * c.X(BS, i, j, a, 0) - F.ov(j, 0) * c.X(BS, i, 0, a, b) +
-            F.ov(j, b) * c.X(BS, i, 0, a, 0) + F.ov(i, a) * c.X(BT, 0, j, 0, b);
-  const float y0 = c.X(BY, 0, j, 0, b);
-  if (i == 0) u += F.v(a, 0) * y0;
-  if (a == 0) u -= F.o(0, i) * y0;
-  return u;
-}
-// S without the transposed-operand terms (Z_ji^ba and, for i == 0, OZ[j]^ba come from the caller)
-__device__ __forceinline__ float couple_S(const CP &c, int i, int j, int a, int b, float zji_ba, float ozj_ba) {
-  const int Nv = c.pv.L.Nv;
-  const int64_t ab = (int64_t)a * c.pv.L.Nvp + b;
-  float u = c.F.ov(0, 0) * (c.X(BZ, i, j, a, b) + zji_ba);
-  const int No = c.pv.L.No;
-  if (a == 0) u -= c.WZ[((int64_t)j * No + i) * Nv + b];
-  if (b == 0) u -= c.WZ[((int64_t)i * No + j) * Nv + a];
-  if (j == 0) {
-    u -= c.OZ[(int64_t)i * c.pv.L.SL + ab];
-    if (b == 0) u += c.H[i * Nv + a];
-  }
-  if (i == 0) {
-    u -= ozj_ba;
-    if (a == 0) u += c.H[j * Nv + b];
-  }
-  return u;
+// a slice of the packed vector through its storage: element (a, b) = sg p[a Nvp + b]; p == nullptr
+// for the identically zero slices i == j of T, X, Y
+struct SV {
+  const float *p;
+  float sg;
+  __device__ __forceinline__ float at(int64_t ab) const { return p ? sg * p[ab] : 0.f; }
+};
+__device__ __forceinline__ SV sv(const PV &pv, const float *v, int blk, int i, int j) {
+  float sg;
+  const float *p = pv.sl(v, blk, i, j, sg);
+  return {p, sg};
 }
 
-// T, X, Y: work item = (slice i < j, tile pair ta <= tb); y on tile (ta, tb) and -y on (tb, ta)
+// items [first, last) of the blocked assignment of `items` work items to this CTA
+__device__ __forceinline__ void cta_items(int64_t items, int64_t &first, int64_t &last) {
+  const int64_t per = (items + gridDim.x - 1) / gridDim.x;
+  first = (int64_t)blockIdx.x * per;
+  last = min(items, first + per);
+}
+
+// T, X, Y: work item = (slice i < j, tile pair ta <= tb); y on tile (ta, tb) and -y on
+// (tb, ta).  Every slice pointer of the item is resolved once.  The element formulas are the
+// full-storage coupling pass's (sigma.cu k_couple, arrow form) with i < j.
 template <int BLK>
 __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Ys[kT][kT + 1];
   const int nt = (L.Nv + kT - 1) / kT, npairs = nt * (nt + 1) / 2;
-  const int64_t items = (int64_t)L.nh * npairs;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const FF &F = c.F;
+  int64_t first, last;
+  cta_items((int64_t)L.nh * npairs, first, last);
   float dsum = 0.f;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int64_t it = first; it < last; ++it) {
     const int k = (int)(it / npairs);
     int tp = (int)(it % npairs), ta = 0;
     while (tp >= nt - ta) { tp -= nt - ta; ++ta; }
     const int tb = ta + tp;
     int i, j;
-    pair_decode(L.No, k, i, j);
+    pair_decode(No, k, i, j);
     const int64_t so = L.boff[BLK] + (int64_t)k * L.SL;
     const float *P = c.P + so, *x = c.x + so;
     float *y = c.y + so;
+    // the item's slices and scalars (j >= 1 since i < j)
+    const bool i0 = i == 0;
+    const float cxe = -c.omega + (BLK == BT ? 0.f : F.v(0, 0) - F.o(0, 0)) - (F.o(i, i) + F.o(j, j));
+    const float s1 = i0 ? 1.f : F.o(0, i), s2 = F.o(0, j);
+    const float *t1p = i0 ? c.OC1 + ((int64_t)BLK * No + j) * L.SL : c.x + L.boff[BLK] + (int64_t)pair_ij(No, 0, j) * L.SL;
+    const float *t2p = i0 ? nullptr : c.x + L.boff[BLK] + (int64_t)pair_ij(No, 0, i) * L.SL;   // x_i0 = -x_0i
+    const float f00 = F.ov(0, 0);
+    SV A1{}, A2{}, A3{};
+    const float *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;
+    if (BLK == BT) {
+      A1 = sv(c.pv, c.x, BX, i, j); A2 = sv(c.pv, c.x, BY, i, j);
+      r1 = c.VX + ((int64_t)i * No + j) * Nv;
+      if (i0) { r2 = c.OX + (int64_t)j * L.SL; r3 = c.G + (int64_t)j * Nv; }
+    } else if (BLK == BX) {
+      A1 = sv(c.pv, c.x, BT, i, j); A2 = sv(c.pv, c.x, BT, 0, j); A3 = sv(c.pv, c.x, BT, 0, i);
+    } else {
+      A1 = sv(c.pv, c.x, BT, i, j); A2 = sv(c.pv, c.x, BS, 0, i); A3 = sv(c.pv, c.x, BS, 0, j);
+      if (i0) r1 = c.CYZ + (int64_t)j * Nv;
+    }
     for (int r = ty; r < kT; r += 8) {
       const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
-      Pa[r][tx] = (a < L.Nv && b < L.Nv) ? P[(int64_t)a * L.Nvp + b] : 0.f;
-      Pb[r][tx] = (a2 < L.Nv && b2 < L.Nv) ? P[(int64_t)a2 * L.Nvp + b2] : 0.f;
+      Pa[r][tx] = (a < Nv && b < Nv) ? P[(int64_t)a * Nvp + b] : 0.f;
+      Pb[r][tx] = (a2 < Nv && b2 < Nv) ? P[(int64_t)a2 * Nvp + b2] : 0.f;
     }
     __syncthreads();
+    const int b = tb * kT + tx;
+    const float fob0 = b < Nv ? F.ov(0, b) : 0.f, fobi = b < Nv ? F.ov(i, b) : 0.f, fobj = b < Nv ? F.ov(j, b) : 0.f;
     for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx;
+      const int a = ta * kT + r;
       float yv = 0.f;
       const bool upper = ta < tb || r < tx;
-      if (a < L.Nv && b < L.Nv && upper && valid_elem(BLK, i, j, a, b)) {
-        const float xe = x[(int64_t)a * L.Nvp + b];
-        float u = c.common(BLK, i, j, a, b, xe);
-        u += BLK == BT ? couple_T(c, i, j, a, b) : BLK == BX ? couple_X(c, i, j, a, b) : couple_Y(c, i, j, a, b);
+      if (a < Nv && b < Nv && upper && valid_elem(BLK, i, j, a, b)) {
+        const int64_t ab = (int64_t)a * Nvp + b;
+        const float xe = x[ab];
+        float u = cxe * xe - s1 * t1p[ab] + (t2p ? s2 * t2p[ab] : 0.f);
+        if (BLK == BT) {
+          u += f00 * (A1.at(ab) + A2.at(ab));
+          if (a == 0) u -= r1[b];
+          if (b == 0) u += r1[a];
+          if (i0) {
+            u -= r2[ab];
+            if (a == 0) u += r3[b];
+            if (b == 0) u -= r3[a];
+          }
+        } else if (BLK == BX) {
+          const float foa0 = F.ov(0, a), foai = F.ov(i, a), foaj = F.ov(j, a);
+          u += f00 * A1.at(ab) - foa0 * A1.at(b) + fob0 * A1.at(a) - F.ov(i, 0) * A2.at(ab) + F.ov(j, 0) * A3.at(ab) +
+               foai * A2.at(b) - foaj * A3.at(b) - fobi * A2.at(a) + fobj * A3.at(a);
+        } else {
+          u += f00 * A1.at(ab) + fobj * A2.at(a) - fobi * A3.at(a) - F.ov(j, a) * A2.at(b) + F.ov(i, a) * A3.at(b);
+          if (i0) {
+            if (a == 0) u += r1[b];
+            if (b == 0) u -= r1[a];
+          }
+        }
         yv = Pa[r][tx] - Pb[tx][r] + u;
         dsum += 2.f * xe * yv;
       }
-      if (a < L.Nv && b < L.Nv && (ta < tb || r <= tx)) y[(int64_t)a * L.Nvp + b] = yv;
+      if (a < Nv && b < Nv && (ta < tb || r <= tx)) y[(int64_t)a * Nvp + b] = yv;
       Ys[r][tx] = -yv;
     }
     __syncthreads();
     for (int r = ty; r < kT; r += 8) {   // element (tb*32 + r, ta*32 + tx) = -y(ta*32 + tx, tb*32 + r)
-      const int a = tb * kT + r, b = ta * kT + tx;
-      if (a < L.Nv && b < L.Nv && (ta < tb || r > tx)) y[(int64_t)a * L.Nvp + b] = Ys[tx][r];
+      const int a = tb * kT + r, bb = ta * kT + tx;
+      if (a < Nv && bb < Nv && (ta < tb || r > tx)) y[(int64_t)a * Nvp + bb] = Ys[tx][r];
     }
     __syncthreads();
   }
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
 
-// S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb) and y_ji = y_ij^T
+// S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb), y_ji = y_ij^T
 __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Zt[kT][kT + 1], Ot[kT][kT + 1], Ys[kT][kT + 1];
-  const int nt = (L.Nv + kT - 1) / kT, No = L.No;
+  const int nt = (L.Nv + kT - 1) / kT, No = L.No, Nv = L.Nv, Nvp = L.Nvp;
   const int npair = No * (No + 1) / 2;
-  const int64_t items = (int64_t)npair * nt * nt;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const FF &F = c.F;
+  int64_t first, last;
+  cta_items((int64_t)npair * nt * nt, first, last);
   float dsum = 0.f;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int64_t it = first; it < last; ++it) {
     int pi = (int)(it / (nt * nt));
     const int tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
     int i = 0;
@@ -615,64 +628,124 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
     const int j = i + pi;   // i <= j
     if (i == j && ta > tb) continue;
     const int64_t sij = L.boff[BS] + ((int64_t)i * No + j) * L.SL, sji = L.boff[BS] + ((int64_t)j * No + i) * L.SL;
+    const float *Zij = c.x + L.boff[BZ] + ((int64_t)i * No + j) * L.SL;
     const float *Zji = c.x + L.boff[BZ] + ((int64_t)j * No + i) * L.SL;
-    const float *OZj = c.OZ + (int64_t)j * L.SL;
+    const float *OZj = c.OZ + (int64_t)j * L.SL, *OZi = c.OZ + (int64_t)i * L.SL;
+    const bool i0 = i == 0, j0 = j == 0;
+    const float cxe = -c.omega - (F.o(i, i) + F.o(j, j));
+    const float s1 = i0 ? 1.f : F.o(0, i), s2 = j0 ? 1.f : F.o(0, j), f00 = F.ov(0, 0);
+    const float *t1p = i0 ? c.OC1 + ((int64_t)BS * No + j) * L.SL : c.x + L.boff[BS] + (int64_t)j * L.SL;
+    const float *t2p = j0 ? c.OC2 + (int64_t)i * L.SL : c.x + L.boff[BS] + (int64_t)i * No * L.SL;
+    const float *WZji = c.WZ + ((int64_t)j * No + i) * Nv, *WZij = c.WZ + ((int64_t)i * No + j) * Nv;
+    const float *Hj = c.H + (int64_t)j * Nv, *Hi = c.H + (int64_t)i * Nv;
     for (int r = ty; r < kT; r += 8) {
       const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
-      const bool in1 = a < L.Nv && b < L.Nv, in2 = a2 < L.Nv && b2 < L.Nv;
-      Pa[r][tx] = in1 ? c.P[sij + (int64_t)a * L.Nvp + b] : 0.f;
-      Pb[r][tx] = in2 ? c.P[sji + (int64_t)a2 * L.Nvp + b2] : 0.f;
-      Zt[r][tx] = in2 ? Zji[(int64_t)a2 * L.Nvp + b2] : 0.f;
-      if (i == 0) Ot[r][tx] = in2 ? OZj[(int64_t)a2 * L.Nvp + b2] : 0.f;
+      const bool in1 = a < Nv && b < Nv, in2 = a2 < Nv && b2 < Nv;
+      const int64_t e2 = (int64_t)a2 * Nvp + b2;
+      Pa[r][tx] = in1 ? c.P[sij + (int64_t)a * Nvp + b] : 0.f;
+      Pb[r][tx] = in2 ? c.P[sji + e2] : 0.f;
+      Zt[r][tx] = in2 ? Zji[e2] : 0.f;
+      if (i0) Ot[r][tx] = in2 ? OZj[e2] : 0.f;
     }
     __syncthreads();
     const bool diag = i == j && ta == tb;
+    const int b = tb * kT + tx;
     for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx;
+      const int a = ta * kT + r;
       float yv = 0.f;
-      if (a < L.Nv && b < L.Nv && (!diag || r <= tx)) {
-        const float xe = c.x[sij + (int64_t)a * L.Nvp + b];
-        float u = c.common(BS, i, j, a, b, xe);
-        u += couple_S(c, i, j, a, b, Zt[tx][r], i == 0 ? Ot[tx][r] : 0.f);
+      if (a < Nv && b < Nv && (!diag || r <= tx)) {
+        const int64_t ab = (int64_t)a * Nvp + b;
+        const float xe = c.x[sij + ab];
+        float u = cxe * xe - s1 * t1p[ab] - s2 * t2p[ab] + f00 * (Zij[ab] + Zt[tx][r]);
+        if (a == 0) u -= WZji[b];
+        if (b == 0) u -= WZij[a];
+        if (j0) {
+          u -= OZi[ab];
+          if (b == 0) u += Hi[a];
+        }
+        if (i0) {
+          u -= Ot[tx][r];
+          if (a == 0) u += Hj[b];
+        }
         yv = Pa[r][tx] + Pb[tx][r] + u;
         dsum += (diag && r == tx ? 1.f : 2.f) * xe * yv;
-        c.y[sij + (int64_t)a * L.Nvp + b] = yv;
+        c.y[sij + ab] = yv;
       }
       Ys[r][tx] = yv;
     }
     __syncthreads();
     for (int r = ty; r < kT; r += 8) {   // y_ji[tb*32 + r][ta*32 + tx] = y_ij[ta*32 + tx][tb*32 + r]
-      const int a = tb * kT + r, b = ta * kT + tx;
-      if (a < L.Nv && b < L.Nv && (!diag || r > tx)) c.y[sji + (int64_t)a * L.Nvp + b] = Ys[tx][r];
+      const int a = tb * kT + r, bb = ta * kT + tx;
+      if (a < Nv && bb < Nv && (!diag || r > tx)) c.y[sji + (int64_t)a * Nvp + bb] = Ys[tx][r];
     }
     __syncthreads();
   }
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
 
-// Z: work item = (slice (i, j), tile (ta, tb)); y = P + F Z + couplings
+// Z: work item = (slice (i, j), strip of 32 rows); a warp takes rows ty, ty + 8, ... and each
+// lane four consecutive columns (16-byte vectors).  y = P + F Z + couplings.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float g4(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+
 __global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
   const Packed &L = c.pv.L;
-  const int nt = (L.Nv + kT - 1) / kT, No = L.No;
-  const int64_t items = (int64_t)L.NN * nt * nt;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, nstrip = (Nv + 31) / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const FF &F = c.F;
+  int64_t first, last;
+  cta_items((int64_t)L.NN * nstrip, first, last);
   float dsum = 0.f;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int s = (int)(it / (nt * nt)), tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+  for (int64_t it = first; it < last; ++it) {
+    const int s = (int)(it / nstrip), a0 = (int)(it % nstrip) * 32;
     const int i = s / No, j = s % No;
     const int64_t so = L.boff[BZ] + (int64_t)s * L.SL;
-    const float *FZ = c.FZ + (int64_t)s * L.SL;
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx;
-      if (a >= L.Nv || b >= L.Nv) continue;
-      const int64_t ab = (int64_t)a * L.Nvp + b;
-      float yv = 0.f;
-      if (valid_elem(BZ, i, j, a, b)) {
-        const float xe = c.x[so + ab];
-        yv = c.P[so + ab] + FZ[ab] + c.common(BZ, i, j, a, b, xe) + couple_Z(c, i, j, a, b);
-        dsum += 2.f * xe * yv;
+    float *ys = c.y + so;
+    if (j == 0) {   // not amplitudes (the down t hole twice)
+      for (int a = a0 + w; a < min(Nv, a0 + 32); a += 8)
+        for (int b = lane; b < Nv; b += 32) ys[(int64_t)a * Nvp + b] = 0.f;
+      continue;
+    }
+    const float *xs = c.x + so, *Ps = c.P + so, *FZs = c.FZ + (int64_t)s * L.SL;
+    const float *Sij = c.x + L.boff[BS] + (int64_t)s * L.SL, *Si0 = c.x + L.boff[BS] + (int64_t)i * No * L.SL;
+    const float *T0j = c.x + L.boff[BT] + (int64_t)pair_ij(No, 0, j) * L.SL;   // row 0 used
+    const float *Y0j = c.x + L.boff[BY] + (int64_t)pair_ij(No, 0, j) * L.SL;
+    const bool i0 = i == 0;
+    const float *t1p = i0 ? c.OC1 + ((int64_t)BZ * No + j) * L.SL : c.x + L.boff[BZ] + (int64_t)j * L.SL;
+    const float *t2p = c.x + L.boff[BZ] + (int64_t)i * No * L.SL;   // Z_i0
+    const float cxe = -c.omega + (F.v(0, 0) - F.o(0, 0)) - (F.o(i, i) + F.o(j, j));
+    const float s1 = i0 ? 1.f : F.o(0, i), s2 = F.o(0, j), f00 = F.ov(0, 0), fj0 = F.ov(j, 0), foi = F.o(0, i);
+    for (int b = 4 * lane; b < Nvp; b += 128) {
+      const float4 t0 = ld4(T0j + b), y0 = ld4(Y0j + b);
+      float fob0[4], fobj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        fob0[q] = b + q < Nv ? F.ov(0, b + q) : 0.f;
+        fobj[q] = b + q < Nv ? F.ov(j, b + q) : 0.f;
       }
-      c.y[so + ab] = yv;
+      for (int a = a0 + w; a < min(Nv, a0 + 32); a += 8) {
+        const int64_t ab = (int64_t)a * Nvp + b;
+        const float4 xe = ld4(xs + ab), p4 = ld4(Ps + ab), fz = ld4(FZs + ab), t1 = ld4(t1p + ab), t2 = ld4(t2p + ab);
+        const float4 sa = ld4(Sij + ab), s0 = ld4(Si0 + ab);
+        const float sija0 = Sij[(int64_t)a * Nvp], si0a0 = Si0[(int64_t)a * Nvp];
+        const float foai = F.ov(i, a), fva = F.v(a, 0);
+        float out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int bq = b + q;
+          float yv = 0.f;
+          if (bq < Nv && bq != 0 && !(i0 && a == 0)) {
+            const float x0 = g4(xe, q), yb = g4(y0, q);
+            yv = g4(p4, q) + g4(fz, q) + cxe * x0 - s1 * g4(t1, q) - s2 * g4(t2, q) + f00 * g4(sa, q) -
+                 fob0[q] * sija0 - fj0 * g4(s0, q) + fobj[q] * si0a0 + foai * g4(t0, q);
+            if (i0) yv += fva * yb;
+            if (a == 0) yv -= foi * yb;
+            dsum += 2.f * x0 * yv;
+          }
+          out[q] = yv;
+        }
+        *reinterpret_cast<float4 *>(ys + ab) = make_float4(out[0], out[1], out[2], out[3]);
+      }
     }
   }
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
@@ -783,10 +856,9 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
   for (int l = 0; l < 32; ++l) { w.fl[l] = h->arrow_w[l]; w.fk[l] = h->arrow_w[32 + l]; }
   {
     const unsigned ga = (unsigned)std::min<int64_t>(cdiv(L.SL, 128), 4096);
-    const size_t sm = 2 * 32 * 128 * sizeof(float);
-    kp_arrow_anti<BT><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
-    kp_arrow_anti<BX><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
-    kp_arrow_anti<BY><<<ga, 128, sm, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_anti<BT><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_anti<BX><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOX, w);
+    kp_arrow_anti<BY><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOX, w);
     kp_arrow_full<BS><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
     kp_arrow_full<BZ><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
   }
