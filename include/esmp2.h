@@ -55,7 +55,11 @@ typedef enum {
 typedef enum {
   ESMP2_FP64 = 0,        /* every contraction in float64 */
   ESMP2_MIXED_BF16 = 1,  /* sigma contractions bf16 x bf16 -> fp32 (tcgen05) inside fp64 refinement */
-  ESMP2_MIXED_TF32 = 2,  /* reserved: tf32 inner contractions (returns ESMP2_ERR_UNSUPPORTED) */
+  ESMP2_MIXED_TF32 = 2,  /* as ESMP2_MIXED_BF16 with the inner contraction on float32 operands read as
+                            tf32 by the tensor cores (kind::tf32: 10 explicit mantissa bits, low bits
+                            of each float32 operand ignored) with fp32 accumulation; the inner PCG
+                            vector p is itself the operand.  Packed inner solve only: No <= 32, else
+                            ESMP2_ERR_UNSUPPORTED. */
   ESMP2_FP64_TC = 3      /* float64-accurate virtual-index terms: x and F_vv split into exact 6-bit
                             bf16 digits (per-slice power-of-two scale), digit products summed exactly
                             in fp32 on tcgen05 level by level (levels 2..10) and combined in float64;
@@ -140,15 +144,18 @@ esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv
  * basis whose occupied orbitals other than t diagonalise F_oo; for No <= 32 it needs x to
  * have the spin-flip symmetry of the singlet, S_ij^ab = S_ji^ba (every vector of the problem
  * has it: b, the solution and every Krylov vector), and returns y with that symmetry and the
- * antisymmetry of T, X, Y exactly.  x and y must not overlap. */
+ * antisymmetry of T, X, Y exactly.  ESMP2_MIXED_TF32: the same with the virtual-index
+ * contraction on tf32 operands (No <= 32).  x and y must not overlap. */
 esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
 
 /* Per-stage device timing of `reps` sigma builds y = A x (same arguments as esmp2_sigma),
  * measured with CUDA events on the handle's stream; ms[0..7] receives average
  * milliseconds per build.  ESMP2_FP64: [0] virtual-index contractions, [1] occupied-index
  * contractions, [2] coupling intermediates, [3] element-wise coupling pass, [4] total.
- * ESMP2_MIXED_BF16: [0] bf16 rounding of x, [1] virtual-index tcgen05 contraction,
- * [2] occupied-index pass, [3] coupling + fp32->fp64 pass, [4] total.  Not part of the
+ * ESMP2_MIXED_BF16 / ESMP2_MIXED_TF32 (No <= 32, the packed inner sigma on float32 vectors):
+ * [0] operand conversion (bf16 rounding; tf32: none, the vector is the operand), [1] transposed Z
+ * slices + virtual-index tcgen05 GEMM, [2] 0, [3] arrow sums, intermediates and coupling pass,
+ * [4] total.  Not part of the
  * method: it exists so that benchmarks can attribute time to kernels. */
 esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p, int reps,
                                  double *ms);
@@ -166,7 +173,8 @@ esmp2_status esmp2_rhs(esmp2_handle *h, double *b);
 /* Solve (H0 - E0) x = -b on D+L by Jacobi-preconditioned conjugate gradients
  * (Sec. III.A uses CG).  ESMP2_FP64: plain fp64 PCG.  ESMP2_MIXED_BF16: fp64
  * iterative refinement, each step solving the correction with bf16/fp32 inner
- * PCG.  Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
+ * PCG.  ESMP2_MIXED_TF32: the same with tf32 inner contractions (No <= 32, else
+ * UNSUPPORTED).  Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
  * (Mixed: intermediate true residuals far from tol take fewer exact digit levels and a
  * float32 coupling pass, accurate relative to their own size; the residual that stops
  * the solve, and that the energy reuses, is float64-accurate throughout.)
@@ -193,7 +201,7 @@ esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
  * instances in order from a shared counter, so small instances overlap; device memory in
  * use is that of `concurrency` instances at a time.  In the mixed solve of an instance of
  * at most 64M amplitudes the inner PCG iteration is captured once and replayed as a CUDA
- * graph.  p: ESMP2_FP64, ESMP2_FP64_TC or ESMP2_MIXED_BF16.  Returns ESMP2_OK if every
+ * graph.  p: ESMP2_FP64, ESMP2_FP64_TC, ESMP2_MIXED_BF16 or ESMP2_MIXED_TF32.  Returns ESMP2_OK if every
  * instance succeeded, else the first failing status (every instance is still attempted). */
 typedef struct {
   esmp2_status status;

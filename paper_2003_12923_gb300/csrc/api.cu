@@ -33,7 +33,7 @@ void free_handle(esmp2_handle *h) {
                   h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
                   h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
-                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig, h->pr, h->pp, h->pq, h->pd, h->pdinv, h->pop, h->pW,
+                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig, h->pr, h->pp, h->pq, h->pd, h->pdinv, h->pop, h->pW, h->pop32, h->pW32,
                   h->pP, h->pVX, h->pGP, h->pWZ, h->pHP, h->pOC, h->pOC2, h->pOX, h->pOZ, h->pG, h->pH, h->pCYZ, h->pdot};
   for (void *p : ptrs)
     if (p) dfree(p, h->stream);
@@ -207,7 +207,11 @@ esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_prec
     if (!split_supported(h, kFp64TcLevels)) { h->err = "ESMP2_FP64_TC needs Nv < 910"; return ESMP2_ERR_UNSUPPORTED; }
     return sigma64(h, x, y, kFp64TcLevels);
   }
-  if (p == ESMP2_MIXED_BF16) return sigma_mixed(h, x, y);
+  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32) {
+    if (p == ESMP2_MIXED_TF32 && h->d.No > 32) { h->err = "ESMP2_MIXED_TF32 needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
+    h->tf32 = p == ESMP2_MIXED_TF32;
+    return sigma_mixed(h, x, y);
+  }
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
 }
@@ -217,7 +221,11 @@ esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, es
   if (!h || !x || !y || !ms || x == y || reps < 1) return ESMP2_ERR_INVALID_ARG;
   if (p == ESMP2_FP64) return profile64(h, x, y, reps, ms);
   if (p == ESMP2_FP64_TC && split_supported(h, kFp64TcLevels)) return profile64(h, x, y, reps, ms, kFp64TcLevels);
-  if (p == ESMP2_MIXED_BF16) return profile_mixed(h, x, y, reps, ms);
+  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32) {
+    if (p == ESMP2_MIXED_TF32 && h->d.No > 32) { h->err = "ESMP2_MIXED_TF32 needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
+    h->tf32 = p == ESMP2_MIXED_TF32;
+    return profile_mixed(h, x, y, reps, ms);
+  }
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
 }
@@ -245,6 +253,7 @@ esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision
     return solve64(h, tol, maxit, info, 1);
   }
   if (p == ESMP2_MIXED_BF16) return solve_mixed(h, tol, maxit, info);
+  if (p == ESMP2_MIXED_TF32) return solve_mixed(h, tol, maxit, info, true);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
 }

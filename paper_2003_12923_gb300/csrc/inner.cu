@@ -158,7 +158,7 @@ __device__ __forceinline__ void cta_partials(double (&v)[NQ], double *red) {
 __device__ __forceinline__ float blk_w(int blk) { return blk == BZ ? 2.f : 1.f; }
 
 // ---------------------------------------------------------------- layout conversions
-// r = r64 (full storage) on the packed slots, p = M^-1 r, d = 0, pb = bf16(p); partials
+// r = r64 (full storage) on the packed slots, p = M^-1 r, d = 0, pb = bf16(p) (if kept); partials
 // <r, M^-1 r>_w, <r, r>_w.  One CTA iteration per packed row (slice, a).
 __global__ void kp_init(PV pv, const double *r64, const __half *dinv, float *r, float *p, float *d,
                         __nv_bfloat16 *pb, double *red) {
@@ -179,7 +179,7 @@ __global__ void kp_init(PV pv, const double *r64, const __half *dinv, float *r, 
       r[e] = ri;
       p[e] = z;
       d[e] = 0.f;
-      pb[e] = __float2bfloat16_rn(z);
+      if (pb) pb[e] = __float2bfloat16_rn(z);
       a0 += w * ri * z;
       a1 += w * ri * ri;
     }
@@ -311,6 +311,35 @@ __global__ void __launch_bounds__(256) kp_zt(PV pv, __nv_bfloat16 *op) {
   }
 }
 
+// the same for the float32 operand of the tf32 contraction: a lane moves two floats (8 bytes)
+__global__ void __launch_bounds__(256) kp_zt32(PV pv, float *op) {
+  const Packed &L = pv.L;
+  __shared__ float t[64][65];
+  const int Nv = L.Nv, Nvp = L.Nvp, nt = (Nv + 63) / 64;
+  const int64_t items = (int64_t)L.NN * nt * nt;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int s = (int)(it / (nt * nt)), tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    const float *src = op + L.boff[BZ] + (int64_t)s * L.SL;
+    float *dst = op + L.boff[5] + (int64_t)s * L.SL;
+    for (int r = w; r < 64; r += 8) {
+      const int a = ta * 64 + r, b = tb * 64 + 2 * lane;
+      float2 v = make_float2(0.f, 0.f);
+      if (a < Nv && b + 1 < Nvp) v = *reinterpret_cast<const float2 *>(src + (int64_t)a * Nvp + b);
+      t[r][2 * lane] = v.x;
+      t[r][2 * lane + 1] = v.y;
+    }
+    __syncthreads();
+    for (int r = w; r < 64; r += 8) {
+      const int b = tb * 64 + r, a = ta * 64 + 2 * lane;
+      if (b < Nv && a + 1 < Nvp)
+        *reinterpret_cast<float2 *>(dst + (int64_t)b * Nvp + a) =
+            make_float2(a < Nv ? t[2 * lane][r] : 0.f, a + 1 < Nv ? t[2 * lane + 1][r] : 0.f);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- arrow sums over slices
 struct ArrowWP {
   float fl[32];  // F_l,t for 1 <= l < No, else 0
@@ -318,46 +347,48 @@ struct ArrowWP {
 };
 
 // T, X, Y (packed i < j): OC1[q][e] = sum_{l>=1} F_lt x_lq[e] (x_lq = -x_ql for l > q), and for X
-// also OX[m][e] = sum_l F_l,t' X_lm[e].  One thread per element e of a slice; both occupied
-// indices are unrolled (No <= 32), so every stored pair is read once and both of its
-// contributions go to register accumulators with constant indices.
+// also OX[q][e] = sum_l F_l,t' X_lq[e].  One thread per element e; rows p of stored pairs
+// (p, q > p) in turn, q unrolled: x_pq adds to the column sums of q in registers and to the row
+// sum of p, and output p is complete at the end of row p (its column part came from rows < p).
 template <int BLK>
-__global__ void __launch_bounds__(128) kp_arrow_anti(PV pv, const float *__restrict__ x, float *oc1, float *ox,
-                                                      const ArrowWP w) {
+__global__ void __launch_bounds__(128, 4) kp_arrow_anti(PV pv, const float *__restrict__ x, float *oc1, float *ox,
+                                                         const ArrowWP w) {
   const Packed &L = pv.L;
   const int No = L.No;
+  constexpr bool WX = BLK == BX;
   const float *xb = x + L.boff[BLK];
   float *o1 = oc1 + (int64_t)BLK * No * L.SL;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.SL; e += (int64_t)gridDim.x * blockDim.x) {
-    float c1[32], cx[BLK == BX ? 32 : 1];
+    float c1[32], cx[WX ? 32 : 1];
 #pragma unroll
     for (int q = 0; q < 32; ++q) c1[q] = 0.f;
 #pragma unroll
-    for (int q = 0; q < (BLK == BX ? 32 : 1); ++q) cx[q] = 0.f;
+    for (int q = 0; q < (WX ? 32 : 1); ++q) cx[q] = 0.f;
+    for (int p = 0; p < No; ++p) {
+      const float *row = xb + (int64_t)(p * No - p * (p + 1) / 2 - p - 1) * L.SL + e;   // pair (p, q): row + q SL
+      const float flp = w.fl[p], fkp = w.fk[p];
+      float r1 = 0.f, rx = 0.f;
 #pragma unroll
-    for (int p = 0; p < 31; ++p) {
-      if (p < No) {
-        const int64_t kb = (int64_t)p * No - p * (p + 1) / 2 - p - 1;   // pair (p, q) = kb + q
-#pragma unroll
-        for (int q = p + 1; q < 32; ++q) {
-          if (q < No) {
-            const float v = xb[(kb + q) * L.SL + e];
-            c1[q] += w.fl[p] * v;
-            c1[p] -= w.fl[q] * v;
-            if constexpr (BLK == BX) {
-              cx[q] += w.fk[p] * v;
-              cx[p] -= w.fk[q] * v;
-            }
+      for (int q = 1; q < 32; ++q) {
+        if (q > p && q < No) {
+          const float v = __ldg(row + (int64_t)q * L.SL);
+          c1[q] += flp * v;
+          r1 += w.fl[q] * v;
+          if constexpr (WX) {
+            cx[q] += fkp * v;
+            rx += w.fk[q] * v;
           }
         }
       }
-    }
+      float cp = 0.f, cxp = 0.f;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (q < No) {
-        o1[(int64_t)q * L.SL + e] = c1[q];
-        if constexpr (BLK == BX) ox[(int64_t)q * L.SL + e] = cx[q];
-      }
+      for (int m = 0; m < 32; ++m)
+        if (m == p) {
+          cp = c1[m];
+          if constexpr (WX) cxp = cx[m];
+        }
+      o1[(int64_t)p * L.SL + e] = cp - r1;
+      if constexpr (WX) ox[(int64_t)p * L.SL + e] = cxp - rx;
     }
   }
 }
@@ -436,6 +467,7 @@ __global__ void kp_inter_c(PV pv, FF F, const float *__restrict__ x, float *WZ, 
     const float *Zr = x + L.boff[BZ] + (int64_t)ij * L.SL + (int64_t)a * L.Nvp;
     const float *Yr = Y ? Y + (int64_t)a * L.Nvp : nullptr;
     float wz = 0.f, hp = 0.f;
+#pragma unroll 4
     for (int c = lane; c < Nv; c += 32) {
       const float zv = Zr[c], yv = Yr ? sg * Yr[c] : 0.f;
       wz += F.ov(0, c) * zv;
@@ -515,8 +547,9 @@ __device__ __forceinline__ void cta_items(int64_t items, int64_t &first, int64_t
 }
 
 // T, X, Y: work item = (slice i < j, tile pair ta <= tb); y on tile (ta, tb) and -y on
-// (tb, ta).  Every slice pointer of the item is resolved once.  The element formulas are the
-// full-storage coupling pass's (sigma.cu k_couple, arrow form) with i < j.
+// (tb, ta).  Every slice pointer of the item is resolved once; the product tiles of the next
+// item are loaded into registers while the current one is computed.  The element formulas are
+// the full-storage coupling pass's (sigma.cu k_couple, arrow form) with i < j.
 template <int BLK>
 __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
   const Packed &L = c.pv.L;
@@ -527,16 +560,41 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
   const FF &F = c.F;
   int64_t first, last;
   cta_items((int64_t)L.nh * npairs, first, last);
-  float dsum = 0.f;
-  for (int64_t it = first; it < last; ++it) {
-    const int k = (int)(it / npairs);
-    int tp = (int)(it % npairs), ta = 0;
+  auto decode = [&](int64_t it, int &k, int &ta, int &tb) {
+    k = (int)(it / npairs);
+    int tp = (int)(it % npairs);
+    ta = 0;
     while (tp >= nt - ta) { tp -= nt - ta; ++ta; }
-    const int tb = ta + tp;
+    tb = ta + tp;
+  };
+  float pa[4], pb[4];   // tiles (ta, tb) and (tb, ta) of the item in flight, rows ty + 8 rr
+  auto fetch = [&](int64_t it) {
+    int k, ta, tb;
+    decode(it, k, ta, tb);
+    const float *P = c.P + L.boff[BLK] + (int64_t)k * L.SL;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr, a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
+      pa[rr] = (a < Nv && b < Nv) ? __ldg(P + (int64_t)a * Nvp + b) : 0.f;
+      pb[rr] = (a2 < Nv && b2 < Nv) ? __ldg(P + (int64_t)a2 * Nvp + b2) : 0.f;
+    }
+  };
+  float dsum = 0.f;
+  if (first < last) fetch(first);
+  for (int64_t it = first; it < last; ++it) {
+    int k, ta, tb;
+    decode(it, k, ta, tb);
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      Pa[ty + 8 * rr][tx] = pa[rr];
+      Pb[ty + 8 * rr][tx] = pb[rr];
+    }
+    __syncthreads();
+    if (it + 1 < last) fetch(it + 1);
     int i, j;
     pair_decode(No, k, i, j);
     const int64_t so = L.boff[BLK] + (int64_t)k * L.SL;
-    const float *P = c.P + so, *x = c.x + so;
+    const float *x = c.x + so;
     float *y = c.y + so;
     // the item's slices and scalars (j >= 1 since i < j)
     const bool i0 = i == 0;
@@ -557,22 +615,17 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
       A1 = sv(c.pv, c.x, BT, i, j); A2 = sv(c.pv, c.x, BS, 0, i); A3 = sv(c.pv, c.x, BS, 0, j);
       if (i0) r1 = c.CYZ + (int64_t)j * Nv;
     }
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
-      Pa[r][tx] = (a < Nv && b < Nv) ? P[(int64_t)a * Nvp + b] : 0.f;
-      Pb[r][tx] = (a2 < Nv && b2 < Nv) ? P[(int64_t)a2 * Nvp + b2] : 0.f;
-    }
-    __syncthreads();
     const int b = tb * kT + tx;
     const float fob0 = b < Nv ? F.ov(0, b) : 0.f, fobi = b < Nv ? F.ov(i, b) : 0.f, fobj = b < Nv ? F.ov(j, b) : 0.f;
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr, a = ta * kT + r;
       float yv = 0.f;
       const bool upper = ta < tb || r < tx;
       if (a < Nv && b < Nv && upper && valid_elem(BLK, i, j, a, b)) {
         const int64_t ab = (int64_t)a * Nvp + b;
-        const float xe = x[ab];
-        float u = cxe * xe - s1 * t1p[ab] + (t2p ? s2 * t2p[ab] : 0.f);
+        const float xe = __ldg(x + ab);
+        float u = cxe * xe - s1 * __ldg(t1p + ab) + (t2p ? s2 * __ldg(t2p + ab) : 0.f);
         if (BLK == BT) {
           u += f00 * (A1.at(ab) + A2.at(ab));
           if (a == 0) u -= r1[b];
@@ -600,8 +653,9 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
       Ys[r][tx] = -yv;
     }
     __syncthreads();
-    for (int r = ty; r < kT; r += 8) {   // element (tb*32 + r, ta*32 + tx) = -y(ta*32 + tx, tb*32 + r)
-      const int a = tb * kT + r, bb = ta * kT + tx;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {   // element (tb*32 + r, ta*32 + tx) = -y(ta*32 + tx, tb*32 + r)
+      const int r = ty + 8 * rr, a = tb * kT + r, bb = ta * kT + tx;
       if (a < Nv && bb < Nv && (ta < tb || r > tx)) y[(int64_t)a * Nvp + bb] = Ys[tx][r];
     }
     __syncthreads();
@@ -609,7 +663,9 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
 
-// S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb), y_ji = y_ij^T
+// S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb), y_ji = y_ij^T.  The
+// tiles read transposed (P_ji, Z_ji and, for i = 0, OZ_j) of the next item are loaded into
+// registers while the current one is computed.
 __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Zt[kT][kT + 1], Ot[kT][kT + 1], Ys[kT][kT + 1];
@@ -619,18 +675,54 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
   const FF &F = c.F;
   int64_t first, last;
   cta_items((int64_t)npair * nt * nt, first, last);
-  float dsum = 0.f;
-  for (int64_t it = first; it < last; ++it) {
+  auto decode = [&](int64_t it, int &i, int &j, int &ta, int &tb) {
     int pi = (int)(it / (nt * nt));
-    const int tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
-    int i = 0;
+    const int tt = (int)(it % (nt * nt));
+    ta = tt / nt;
+    tb = tt % nt;
+    i = 0;
     while (pi >= No - i) { pi -= No - i; ++i; }
-    const int j = i + pi;   // i <= j
-    if (i == j && ta > tb) continue;
+    j = i + pi;   // i <= j
+  };
+  float pa[4], pb[4], zt[4], ot[4];
+  auto fetch = [&](int64_t it) {
+    int i, j, ta, tb;
+    decode(it, i, j, ta, tb);
+    const int64_t sij = L.boff[BS] + ((int64_t)i * No + j) * L.SL, sji = L.boff[BS] + ((int64_t)j * No + i) * L.SL;
+    const float *Zji = c.x + L.boff[BZ] + ((int64_t)j * No + i) * L.SL, *OZj = c.OZ + (int64_t)j * L.SL;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr, a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
+      const bool in1 = a < Nv && b < Nv, in2 = a2 < Nv && b2 < Nv;
+      const int64_t e2 = (int64_t)a2 * Nvp + b2;
+      pa[rr] = in1 ? __ldg(c.P + sij + (int64_t)a * Nvp + b) : 0.f;
+      pb[rr] = in2 ? __ldg(c.P + sji + e2) : 0.f;
+      zt[rr] = in2 ? __ldg(Zji + e2) : 0.f;
+      ot[rr] = (in2 && i == 0) ? __ldg(OZj + e2) : 0.f;
+    }
+  };
+  float dsum = 0.f;
+  if (first < last) fetch(first);
+  for (int64_t it = first; it < last; ++it) {
+    int i, j, ta, tb;
+    decode(it, i, j, ta, tb);
+    if (i == j && ta > tb) {   // the mirror of an item already covered (uniform over the CTA)
+      if (it + 1 < last) fetch(it + 1);
+      continue;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr;
+      Pa[r][tx] = pa[rr];
+      Pb[r][tx] = pb[rr];
+      Zt[r][tx] = zt[rr];
+      Ot[r][tx] = ot[rr];
+    }
+    __syncthreads();
+    if (it + 1 < last) fetch(it + 1);
     const int64_t sij = L.boff[BS] + ((int64_t)i * No + j) * L.SL, sji = L.boff[BS] + ((int64_t)j * No + i) * L.SL;
     const float *Zij = c.x + L.boff[BZ] + ((int64_t)i * No + j) * L.SL;
-    const float *Zji = c.x + L.boff[BZ] + ((int64_t)j * No + i) * L.SL;
-    const float *OZj = c.OZ + (int64_t)j * L.SL, *OZi = c.OZ + (int64_t)i * L.SL;
+    const float *OZi = c.OZ + (int64_t)i * L.SL;
     const bool i0 = i == 0, j0 = j == 0;
     const float cxe = -c.omega - (F.o(i, i) + F.o(j, j));
     const float s1 = i0 ? 1.f : F.o(0, i), s2 = j0 ? 1.f : F.o(0, j), f00 = F.ov(0, 0);
@@ -638,25 +730,16 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
     const float *t2p = j0 ? c.OC2 + (int64_t)i * L.SL : c.x + L.boff[BS] + (int64_t)i * No * L.SL;
     const float *WZji = c.WZ + ((int64_t)j * No + i) * Nv, *WZij = c.WZ + ((int64_t)i * No + j) * Nv;
     const float *Hj = c.H + (int64_t)j * Nv, *Hi = c.H + (int64_t)i * Nv;
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
-      const bool in1 = a < Nv && b < Nv, in2 = a2 < Nv && b2 < Nv;
-      const int64_t e2 = (int64_t)a2 * Nvp + b2;
-      Pa[r][tx] = in1 ? c.P[sij + (int64_t)a * Nvp + b] : 0.f;
-      Pb[r][tx] = in2 ? c.P[sji + e2] : 0.f;
-      Zt[r][tx] = in2 ? Zji[e2] : 0.f;
-      if (i0) Ot[r][tx] = in2 ? OZj[e2] : 0.f;
-    }
-    __syncthreads();
     const bool diag = i == j && ta == tb;
     const int b = tb * kT + tx;
-    for (int r = ty; r < kT; r += 8) {
-      const int a = ta * kT + r;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty + 8 * rr, a = ta * kT + r;
       float yv = 0.f;
       if (a < Nv && b < Nv && (!diag || r <= tx)) {
         const int64_t ab = (int64_t)a * Nvp + b;
-        const float xe = c.x[sij + ab];
-        float u = cxe * xe - s1 * t1p[ab] - s2 * t2p[ab] + f00 * (Zij[ab] + Zt[tx][r]);
+        const float xe = __ldg(c.x + sij + ab);
+        float u = cxe * xe - s1 * __ldg(t1p + ab) - s2 * __ldg(t2p + ab) + f00 * (__ldg(Zij + ab) + Zt[tx][r]);
         if (a == 0) u -= WZji[b];
         if (b == 0) u -= WZij[a];
         if (j0) {
@@ -674,8 +757,9 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
       Ys[r][tx] = yv;
     }
     __syncthreads();
-    for (int r = ty; r < kT; r += 8) {   // y_ji[tb*32 + r][ta*32 + tx] = y_ij[ta*32 + tx][tb*32 + r]
-      const int a = tb * kT + r, bb = ta * kT + tx;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {   // y_ji[tb*32 + r][ta*32 + tx] = y_ij[ta*32 + tx][tb*32 + r]
+      const int r = ty + 8 * rr, a = tb * kT + r, bb = ta * kT + tx;
       if (a < Nv && bb < Nv && (!diag || r > tx)) c.y[sji + (int64_t)a * Nvp + bb] = Ys[tx][r];
     }
     __syncthreads();
@@ -683,70 +767,53 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
 
-// Z: work item = (slice (i, j), strip of 32 rows); a warp takes rows ty, ty + 8, ... and each
-// lane four consecutive columns (16-byte vectors).  y = P + F Z + couplings.
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+// Z: one thread per 16-byte group of four columns of one row (slice (i, j), row a); no shared
+// memory, every load of a group issued before its arithmetic.  y = P + F Z + couplings.
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ float g4(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
 __global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
   const Packed &L = c.pv.L;
-  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, nstrip = (Nv + 31) / 32;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, nb4 = Nvp >> 2;
   const FF &F = c.F;
-  int64_t first, last;
-  cta_items((int64_t)L.NN * nstrip, first, last);
+  const int64_t units = (int64_t)L.NN * Nv * nb4;
   float dsum = 0.f;
-  for (int64_t it = first; it < last; ++it) {
-    const int s = (int)(it / nstrip), a0 = (int)(it % nstrip) * 32;
-    const int i = s / No, j = s % No;
-    const int64_t so = L.boff[BZ] + (int64_t)s * L.SL;
-    float *ys = c.y + so;
-    if (j == 0) {   // not amplitudes (the down t hole twice)
-      for (int a = a0 + w; a < min(Nv, a0 + 32); a += 8)
-        for (int b = lane; b < Nv; b += 32) ys[(int64_t)a * Nvp + b] = 0.f;
-      continue;
-    }
-    const float *xs = c.x + so, *Ps = c.P + so, *FZs = c.FZ + (int64_t)s * L.SL;
-    const float *Sij = c.x + L.boff[BS] + (int64_t)s * L.SL, *Si0 = c.x + L.boff[BS] + (int64_t)i * No * L.SL;
-    const float *T0j = c.x + L.boff[BT] + (int64_t)pair_ij(No, 0, j) * L.SL;   // row 0 used
-    const float *Y0j = c.x + L.boff[BY] + (int64_t)pair_ij(No, 0, j) * L.SL;
-    const bool i0 = i == 0;
-    const float *t1p = i0 ? c.OC1 + ((int64_t)BZ * No + j) * L.SL : c.x + L.boff[BZ] + (int64_t)j * L.SL;
-    const float *t2p = c.x + L.boff[BZ] + (int64_t)i * No * L.SL;   // Z_i0
-    const float cxe = -c.omega + (F.v(0, 0) - F.o(0, 0)) - (F.o(i, i) + F.o(j, j));
-    const float s1 = i0 ? 1.f : F.o(0, i), s2 = F.o(0, j), f00 = F.ov(0, 0), fj0 = F.ov(j, 0), foi = F.o(0, i);
-    for (int b = 4 * lane; b < Nvp; b += 128) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = u / nb4;
+    const int b = (int)(u - row * nb4) * 4;
+    const int s = (int)(row / Nv), a = (int)(row - (int64_t)s * Nv);
+    const int i = s / No, j = s - i * No;
+    const int64_t so = L.boff[BZ] + (int64_t)s * L.SL, ab = (int64_t)a * Nvp + b;
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j != 0) {   // j == 0: not amplitudes (the down t hole twice)
+      const bool i0 = i == 0;
+      const float *Sij = c.x + L.boff[BS] + (int64_t)s * L.SL, *Si0 = c.x + L.boff[BS] + (int64_t)i * No * L.SL;
+      const float *T0j = c.x + L.boff[BT] + (int64_t)pair_ij(No, 0, j) * L.SL;   // row 0 used
+      const float *Y0j = c.x + L.boff[BY] + (int64_t)pair_ij(No, 0, j) * L.SL;
+      const float *t1p = i0 ? c.OC1 + ((int64_t)BZ * No + j) * L.SL : c.x + L.boff[BZ] + (int64_t)j * L.SL;
+      const float *t2p = c.x + L.boff[BZ] + (int64_t)i * No * L.SL;   // Z_i0
+      const float4 xe = ld4(c.x + so + ab), p4 = ld4(c.P + so + ab), fz = ld4(c.FZ + (int64_t)s * L.SL + ab);
+      const float4 t1 = ld4(t1p + ab), t2 = ld4(t2p + ab), sa = ld4(Sij + ab), s0 = ld4(Si0 + ab);
       const float4 t0 = ld4(T0j + b), y0 = ld4(Y0j + b);
-      float fob0[4], fobj[4];
+      const float sija0 = __ldg(Sij + (int64_t)a * Nvp), si0a0 = __ldg(Si0 + (int64_t)a * Nvp);
+      const float cxe = -c.omega + (F.v(0, 0) - F.o(0, 0)) - (F.o(i, i) + F.o(j, j));
+      const float s1 = i0 ? 1.f : F.o(0, i), s2 = F.o(0, j), f00 = F.ov(0, 0), fj0 = F.ov(j, 0), foi = F.o(0, i);
+      const float foai = F.ov(i, a), fva = F.v(a, 0);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        fob0[q] = b + q < Nv ? F.ov(0, b + q) : 0.f;
-        fobj[q] = b + q < Nv ? F.ov(j, b + q) : 0.f;
-      }
-      for (int a = a0 + w; a < min(Nv, a0 + 32); a += 8) {
-        const int64_t ab = (int64_t)a * Nvp + b;
-        const float4 xe = ld4(xs + ab), p4 = ld4(Ps + ab), fz = ld4(FZs + ab), t1 = ld4(t1p + ab), t2 = ld4(t2p + ab);
-        const float4 sa = ld4(Sij + ab), s0 = ld4(Si0 + ab);
-        const float sija0 = Sij[(int64_t)a * Nvp], si0a0 = Si0[(int64_t)a * Nvp];
-        const float foai = F.ov(i, a), fva = F.v(a, 0);
-        float out[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int bq = b + q;
-          float yv = 0.f;
-          if (bq < Nv && bq != 0 && !(i0 && a == 0)) {
-            const float x0 = g4(xe, q), yb = g4(y0, q);
-            yv = g4(p4, q) + g4(fz, q) + cxe * x0 - s1 * g4(t1, q) - s2 * g4(t2, q) + f00 * g4(sa, q) -
-                 fob0[q] * sija0 - fj0 * g4(s0, q) + fobj[q] * si0a0 + foai * g4(t0, q);
-            if (i0) yv += fva * yb;
-            if (a == 0) yv -= foi * yb;
-            dsum += 2.f * x0 * yv;
-          }
+        const int bq = b + q;
+        if (bq < Nv && bq != 0 && !(i0 && a == 0)) {
+          const float x0 = g4(xe, q), yb = g4(y0, q);
+          float yv = g4(p4, q) + g4(fz, q) + cxe * x0 - s1 * g4(t1, q) - s2 * g4(t2, q) + f00 * g4(sa, q) -
+                     F.ov(0, bq) * sija0 - fj0 * g4(s0, q) + F.ov(j, bq) * si0a0 + foai * g4(t0, q);
+          if (i0) yv += fva * yb;
+          if (a == 0) yv -= foi * yb;
+          dsum += 2.f * x0 * yv;
           out[q] = yv;
         }
-        *reinterpret_cast<float4 *>(ys + ab) = make_float4(out[0], out[1], out[2], out[3]);
       }
     }
+    *reinterpret_cast<float4 *>(c.y + so + ab) = make_float4(out[0], out[1], out[2], out[3]);
   }
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
@@ -767,88 +834,127 @@ constexpr int kCoupleGrid = 1216;
 
 int64_t packed_dot_parts(const esmp2_handle *h) { (void)h; return 5LL * kCoupleGrid; }
 
-// Buffers of the packed inner solve; F32 / Fsemi must be ready (ensure_mixed).
-esmp2_status packed_setup(esmp2_handle *h) {
-  if (h->pr) return ESMP2_OK;
-  const Packed L = make_packed(h->d.No, h->d.Nv);
-  h->pk = L;
+// The right operand W = F_vv of the contraction (rows b, columns c, row pitch Nvp; F_vv is
+// symmetric) in bf16 or float32, from the float64 Fock matrix of the working basis.
+static esmp2_status packed_right_operand(esmp2_handle *h, bool f32, void *dst) {
+  const Packed &L = h->pk;
   const int No = L.No, N = h->d.N;
-  const int64_t op_rows = (int64_t)(L.nslices + L.NN) * L.Nv;
+  std::vector<double> hF((size_t)N * N);
+  cudaError_t e = cudaMemcpyAsync(hF.data(), h->Fsemi, sizeof(double) * hF.size(), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "packed set-up");
+  const size_t n = (size_t)L.Nv * L.Nvp;
+  std::vector<float> W32(f32 ? n : 0, 0.f);
+  std::vector<__nv_bfloat16> W16(f32 ? 0 : n, __float2bfloat16_rn(0.f));
+  for (int b = 0; b < L.Nv; ++b)
+    for (int cc = 0; cc < L.Nv; ++cc) {
+      const double v = hF[(size_t)(No + b) * N + No + cc];
+      if (f32) W32[(size_t)b * L.Nvp + cc] = (float)v;
+      else W16[(size_t)b * L.Nvp + cc] = __float2bfloat16_rn((float)v);
+    }
+  e = f32 ? cudaMemcpyAsync(dst, W32.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream)
+          : cudaMemcpyAsync(dst, W16.data(), sizeof(__nv_bfloat16) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? ESMP2_OK : check_cuda(h, e, "packed set-up");
+}
+
+// Buffers of the packed inner solve; F32 / Fsemi must be ready (ensure_mixed).  The operand
+// of the kind h->tf32 asks for (bf16 copy, or float32 holding p itself) is allocated on first
+// use; both kinds can live on one handle.
+esmp2_status packed_setup(esmp2_handle *h) {
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, h->stream);
   };
-  A(reinterpret_cast<void **>(&h->pr), sizeof(float) * (size_t)L.n);
-  A(reinterpret_cast<void **>(&h->pp), sizeof(float) * (size_t)L.n);
-  A(reinterpret_cast<void **>(&h->pq), sizeof(float) * (size_t)L.n);
-  A(reinterpret_cast<void **>(&h->pd), sizeof(float) * (size_t)L.n);
-  A(reinterpret_cast<void **>(&h->pdinv), sizeof(__half) * (size_t)L.n);
-  A(&h->pop, sizeof(__nv_bfloat16) * (size_t)(L.n + (int64_t)L.NN * L.SL));
-  A(&h->pW, sizeof(__nv_bfloat16) * (size_t)L.Nv * L.Nvp);
-  A(reinterpret_cast<void **>(&h->pP), sizeof(float) * (size_t)(L.n + (int64_t)L.NN * L.SL));
-  A(reinterpret_cast<void **>(&h->pVX), sizeof(float) * (size_t)No * No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pGP), sizeof(float) * (size_t)No * No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pWZ), sizeof(float) * (size_t)No * No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pHP), sizeof(float) * (size_t)No * No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pOC), sizeof(float) * (size_t)5 * No * L.SL);
-  A(reinterpret_cast<void **>(&h->pOC2), sizeof(float) * (size_t)2 * No * L.SL);
-  A(reinterpret_cast<void **>(&h->pOX), sizeof(float) * (size_t)No * L.SL);
-  A(reinterpret_cast<void **>(&h->pOZ), sizeof(float) * (size_t)No * L.SL);
-  A(reinterpret_cast<void **>(&h->pG), sizeof(float) * (size_t)No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pH), sizeof(float) * (size_t)No * L.Nv);
-  A(reinterpret_cast<void **>(&h->pCYZ), sizeof(float) * (size_t)No * L.Nv);
-  h->pdot_n = (int)packed_dot_parts(h);
-  A(reinterpret_cast<void **>(&h->pdot), sizeof(double) * (size_t)h->pdot_n);
-  if (e != cudaSuccess) return check_cuda(h, e, "packed inner buffers");
-  // pad columns and the transposed-Z part of the operand start (and stay) zero; q's pad too
-  cudaMemsetAsync(h->pop, 0, sizeof(__nv_bfloat16) * (size_t)(L.n + (int64_t)L.NN * L.SL), h->stream);
-  cudaMemsetAsync(h->pq, 0, sizeof(float) * (size_t)L.n, h->stream);
-  cudaMemsetAsync(h->pp, 0, sizeof(float) * (size_t)L.n, h->stream);
-  // right operand W = F_vv (rows b, columns c; symmetric)
-  {
-    std::vector<double> hF((size_t)N * N);
-    e = cudaMemcpyAsync(hF.data(), h->Fsemi, sizeof(double) * hF.size(), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return check_cuda(h, e, "packed set-up");
-    std::vector<__nv_bfloat16> W((size_t)L.Nv * L.Nvp, __float2bfloat16_rn(0.f));
-    for (int b = 0; b < L.Nv; ++b)
-      for (int cc = 0; cc < L.Nv; ++cc)
-        W[(size_t)b * L.Nvp + cc] = __float2bfloat16_rn((float)hF[(size_t)(No + b) * N + No + cc]);
-    e = cudaMemcpyAsync(h->pW, W.data(), sizeof(__nv_bfloat16) * W.size(), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return check_cuda(h, e, "packed set-up");
+  if (!h->pr) {
+    const Packed L = make_packed(h->d.No, h->d.Nv);
+    h->pk = L;
+    const int No = L.No, N = h->d.N;
+    A(reinterpret_cast<void **>(&h->pr), sizeof(float) * (size_t)L.n);
+    A(reinterpret_cast<void **>(&h->pp), sizeof(float) * (size_t)L.n);
+    A(reinterpret_cast<void **>(&h->pq), sizeof(float) * (size_t)L.n);
+    A(reinterpret_cast<void **>(&h->pd), sizeof(float) * (size_t)L.n);
+    A(reinterpret_cast<void **>(&h->pdinv), sizeof(__half) * (size_t)L.n);
+    A(reinterpret_cast<void **>(&h->pP), sizeof(float) * (size_t)(L.n + (int64_t)L.NN * L.SL));
+    A(reinterpret_cast<void **>(&h->pVX), sizeof(float) * (size_t)No * No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pGP), sizeof(float) * (size_t)No * No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pWZ), sizeof(float) * (size_t)No * No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pHP), sizeof(float) * (size_t)No * No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pOC), sizeof(float) * (size_t)5 * No * L.SL);
+    A(reinterpret_cast<void **>(&h->pOC2), sizeof(float) * (size_t)2 * No * L.SL);
+    A(reinterpret_cast<void **>(&h->pOX), sizeof(float) * (size_t)No * L.SL);
+    A(reinterpret_cast<void **>(&h->pOZ), sizeof(float) * (size_t)No * L.SL);
+    A(reinterpret_cast<void **>(&h->pG), sizeof(float) * (size_t)No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pH), sizeof(float) * (size_t)No * L.Nv);
+    A(reinterpret_cast<void **>(&h->pCYZ), sizeof(float) * (size_t)No * L.Nv);
+    h->pdot_n = (int)packed_dot_parts(h);
+    A(reinterpret_cast<void **>(&h->pdot), sizeof(double) * (size_t)h->pdot_n);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed inner buffers");
+    // q's and p's pad columns start (and stay) zero
+    cudaMemsetAsync(h->pq, 0, sizeof(float) * (size_t)L.n, h->stream);
+    cudaMemsetAsync(h->pp, 0, sizeof(float) * (size_t)L.n, h->stream);
+    PV pv{L};
+    FF F{h->F32, N, No};
+    kp_dinv<<<2432, 128, 0, h->stream>>>(pv, F, (float)h->omega_op, h->pdinv);
+    h->launches += 1;
+    h->packed = true;
+    if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(h, e, "packed set-up");
   }
-  PV pv{L};
-  FF F{h->F32, N, No};
-  kp_dinv<<<2432, 128, 0, h->stream>>>(pv, F, (float)h->omega_op, h->pdinv);
-  h->launches += 1;
-  h->packed = true;
+  const Packed &L = h->pk;
+  const size_t op_elems = (size_t)(L.n + (int64_t)L.NN * L.SL);
+  if (h->tf32 && !h->pop32) {
+    A(reinterpret_cast<void **>(&h->pop32), sizeof(float) * op_elems);
+    A(reinterpret_cast<void **>(&h->pW32), sizeof(float) * (size_t)L.Nv * L.Nvp);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed tf32 operand");
+    // pad columns and the transposed-Z part start (and stay) zero
+    cudaMemsetAsync(h->pop32, 0, sizeof(float) * op_elems, h->stream);
+    if (esmp2_status s = packed_right_operand(h, true, h->pW32)) return s;
+  } else if (!h->tf32 && !h->pop) {
+    A(&h->pop, sizeof(__nv_bfloat16) * op_elems);
+    A(&h->pW, sizeof(__nv_bfloat16) * (size_t)L.Nv * L.Nvp);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed bf16 operand");
+    cudaMemsetAsync(h->pop, 0, sizeof(__nv_bfloat16) * op_elems, h->stream);
+    if (esmp2_status s = packed_right_operand(h, false, h->pW)) return s;
+  }
   return check_cuda(h, cudaGetLastError(), "packed set-up");
 }
 
-esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
-                   float *PT, int ldp, double alg_flops);
+// the inner PCG's p: the float32 operand itself for tf32, else its own vector
+float *packed_p(esmp2_handle *h) { return h->tf32 ? h->pop32 : h->pp; }
 
-// q = A p on the packed layout (bf16 virtual-index terms, float32 everything else); pb_ready:
-// the PCG update already wrote bf16(p) into the operand; dot: per-CTA partials of <p, q>_w
-// (packed_dot_parts(h) doubles) or nullptr.
+esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
+                   float *PT, int ldp, double alg_flops, bool tf32);
+
+// q = A p on the packed layout (bf16 or tf32 virtual-index terms, float32 everything else);
+// pb_ready: the PCG update already wrote the operand (bf16(p), or p itself in the float32
+// operand for tf32); dot: per-CTA partials of <p, q>_w (packed_dot_parts(h) doubles) or nullptr.
 // stages (profiling): bit 0 operand conversion, bit 1 contraction, bit 2 coupling pass.
 esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_ready, double *dot, int stages) {
   const Packed &L = h->pk;
   const int No = L.No, N = h->d.N;
   PV pv{L};
   cudaStream_t st = h->stream;
+  const bool tf32 = h->tf32;
   __nv_bfloat16 *op = static_cast<__nv_bfloat16 *>(h->pop);
-  if (!pb_ready && (stages & 1)) {  // the packed p to bf16 (pad columns are zero in p)
-    kp_bf16<<<1216, 256, 0, st>>>(p, op, L.n);
-    h->launches += 1;
+  if (!pb_ready && (stages & 1)) {  // the packed p to the operand (pad columns are zero in p)
+    if (tf32) {
+      if (p != h->pop32) {
+        if (cudaError_t e = cudaMemcpyAsync(h->pop32, p, sizeof(float) * (size_t)L.n, cudaMemcpyDeviceToDevice, st))
+          return check_cuda(h, e, "sigma_packed operand");
+      }
+    } else {
+      kp_bf16<<<1216, 256, 0, st>>>(p, op, L.n);
+      h->launches += 1;
+    }
   }
   const int64_t rows_n = (int64_t)L.nslices * L.Nv, rows = rows_n + (int64_t)L.NN * L.Nv;
   if (stages & 2) {
-    kp_zt<<<1216, 256, 0, st>>>(pv, op);
+    if (tf32) kp_zt32<<<1216, 256, 0, st>>>(pv, h->pop32);
+    else kp_zt<<<1216, 256, 0, st>>>(pv, op);
     h->launches += 1;
-    if (esmp2_status s = vgemm(h, op, rows, rows_n, h->pW, h->pP, h->pP + L.n, L.Nvp,
-                               alg_virtual_flops(No, L.Nv)))
+    if (esmp2_status s = vgemm(h, tf32 ? static_cast<const void *>(h->pop32) : static_cast<const void *>(op), rows,
+                               rows_n, tf32 ? static_cast<const void *>(h->pW32) : h->pW, h->pP, h->pP + L.n, L.Nvp,
+                               alg_virtual_flops(No, L.Nv), tf32))
       return s;
   }
   if (!(stages & 4)) return check_cuda(h, cudaGetLastError(), "sigma_packed");
@@ -901,8 +1007,8 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
 // d = 0, bf16(p); partials of <r, M^-1 r>_w and <r, r>_w in h->red
 void packed_init(esmp2_handle *h, const double *r64, int grid) {
   const Packed &L = h->pk;
-  kp_init<<<grid, 128, 0, h->stream>>>(PV{L}, r64, h->pdinv, h->pr, h->pp, h->pd,
-                                       static_cast<__nv_bfloat16 *>(h->pop), h->red);
+  kp_init<<<grid, 128, 0, h->stream>>>(PV{L}, r64, h->pdinv, h->pr, packed_p(h), h->pd,
+                                       h->tf32 ? nullptr : static_cast<__nv_bfloat16 *>(h->pop), h->red);
   h->launches += 1;
 }
 
@@ -928,7 +1034,8 @@ void packed_accumulate(esmp2_handle *h, double *x64) {
 // ms[0] operand conversion, [1] contraction (transposed Z slices + GEMM), [2] 0, [3] coupling
 // pass (arrow sums, intermediates, couplings), [4] total
 esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *ms) {
-  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x, h->pp);
+  float *p = packed_p(h);
+  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x, p);
   h->launches += 1;
   cudaEvent_t ev[4];
   for (auto &e : ev) cudaEventCreate(&e);
@@ -936,11 +1043,11 @@ esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *
   esmp2_status s = ESMP2_OK;
   for (int r = 0; r < reps && !s; ++r) {
     cudaEventRecord(ev[0], h->stream);
-    s = sigma_packed(h, h->pp, h->pq, false, nullptr, 1);
+    s = sigma_packed(h, p, h->pq, false, nullptr, 1);
     cudaEventRecord(ev[1], h->stream);
-    if (!s) s = sigma_packed(h, h->pp, h->pq, true, nullptr, 2);
+    if (!s) s = sigma_packed(h, p, h->pq, true, nullptr, 2);
     cudaEventRecord(ev[2], h->stream);
-    if (!s) s = sigma_packed(h, h->pp, h->pq, true, h->pdot, 4);
+    if (!s) s = sigma_packed(h, p, h->pq, true, h->pdot, 4);
     cudaEventRecord(ev[3], h->stream);
     cudaEventSynchronize(ev[3]);
     for (int k = 0; k < 3; ++k) {
@@ -962,14 +1069,15 @@ esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *
   return check_cuda(h, cudaGetLastError(), "profile_packed");
 }
 
-// API-level bf16 sigma of a singlet vector on the packed path: y = A x (x, y full-storage
-// float64 in the TOP basis), through the working basis of the inner solve.
+// API-level bf16 / tf32 sigma of a singlet vector on the packed path: y = A x (x, y
+// full-storage float64 in the TOP basis), through the working basis of the inner solve.
 esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y) {
   double *t1 = h->s64.w ? h->s64.w : h->s64.p;
   rotate_occ(h, x, y, t1, true);                 // y: x in the working basis
-  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, y, h->pp);
+  float *p = packed_p(h);
+  kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, y, p);
   h->launches += 1;
-  if (esmp2_status s = sigma_packed(h, h->pp, h->pq, false, nullptr, 7)) return s;
+  if (esmp2_status s = sigma_packed(h, p, h->pq, false, nullptr, 7)) return s;
   kp_to64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, h->pq, y);
   h->launches += 1;
   rotate_occ(h, y, y, t1, false);

@@ -152,6 +152,12 @@ struct esmp2_handle {
   __half *pdinv = nullptr;  // Jacobi preconditioner (packed)
   void *pop = nullptr;      // bf16 operand: packed p and the transposed Z slices
   void *pW = nullptr;       // bf16 right operand F_vv
+  // ESMP2_MIXED_TF32: the operand is float32 read as tf32 by the tensor cores, and the inner
+  // PCG's p lives in its first n elements (no separate operand copy)
+  bool tf32 = false;        // inner operand kind of the current call
+  bool graph_tf32 = false;  // operand kind the captured inner iteration was built with
+  float *pop32 = nullptr;   // float32 operand: packed p, then the transposed Z slices
+  float *pW32 = nullptr;    // float32 right operand F_vv
   float *pP = nullptr;      // products: P (T .. Z slices, row pitch Nvp) then F Z (transposed part)
   float *pVX = nullptr, *pGP = nullptr, *pWZ = nullptr, *pHP = nullptr;  // [No][No][Nv] coupling sums
   float *pOC = nullptr;     // [5][No][SL] arrow sums over the first occupied index (OC1)
@@ -180,7 +186,7 @@ esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels = 0);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc = 0);
-esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32 = false);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
@@ -192,6 +198,7 @@ esmp2_status packed_setup(esmp2_handle *h);
 esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_ready, double *dot, int stages = 7);
 esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *ms);
 void packed_init(esmp2_handle *h, const double *r64, int grid);
+float *packed_p(esmp2_handle *h);
 void packed_accumulate(esmp2_handle *h, double *x64);
 double packed_wdot(esmp2_handle *h, const float *u, const float *v);
 esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y);
@@ -224,11 +231,11 @@ void dfree(void *p, cudaStream_t st);
 // that one cudaFuncSetAttribute call.
 cudaError_t smem_limit_once(const void *func, int bytes);
 
-// 2-D bf16 tensor map (inner dimension first; rows of row_bytes), box box_inner x box_outer,
-// shared-memory swizzle of 128, 64, 32 or 0 bytes, zero fill out of bounds.  False when the
-// driver's encoder is unavailable or rejects the description.
-bool tma_map_bf16_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-                     uint32_t box_inner, uint32_t box_outer, int swizzle_bytes);
+// 2-D tensor map of bf16 (f32 = false) or float32 elements (inner dimension first; rows of
+// row_bytes), box box_inner x box_outer, shared-memory swizzle of 128, 64, 32 or 0 bytes, zero
+// fill out of bounds.  False when the driver's encoder is unavailable or rejects the description.
+bool tma_map_2d(CUtensorMap *m, const void *base, bool f32, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                uint32_t box_inner, uint32_t box_outer, int swizzle_bytes);
 
 // ESMP2_DEBUG=1: synchronise the handle's stream and print the host time since the last
 // phase mark (set-up breakdowns; no effect otherwise).

@@ -786,11 +786,16 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
 //           contraction (fp32 accumulation); x += d.
 // Everything runs in the basis whose occupied orbitals other than t diagonalise F_oo
 // (the solution is rotated back to the TOP basis on request).
-esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32) {
   auto t0 = std::chrono::steady_clock::now();
   debug_phase(h, "solve: start");
+  if (tf32 && h->d.No > 32) {
+    h->err = "ESMP2_MIXED_TF32 needs the packed inner solve (No <= 32)";
+    return ESMP2_ERR_UNSUPPORTED;
+  }
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
+  h->tf32 = tf32;
   debug_phase(h, "solve: semicanonical set-up");
   if (!h->x_semi) {
     if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);  // zero in every basis
@@ -814,7 +819,8 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     const float wp[5] = {1.f, 1.f, 1.f, 1.f, 2.f};
     for (int k = 0; k < 5; ++k) ic.w[k] = wp[k];
     ic.dinv = h->pdinv;
-    ic.pb = static_cast<__nv_bfloat16 *>(h->pop);
+    // bf16: the p update also writes the operand copy; tf32: p is the operand
+    ic.pb = tf32 ? nullptr : static_cast<__nv_bfloat16 *>(h->pop);
     ic.vec = 1;   // blocks start on multiples of Nv * Nvp elements, Nvp a multiple of 8
   } else {
     if (!h->dinv32) {
@@ -835,12 +841,12 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   debug_phase(h, "solve: preconditioner");
   // small instances are launch-bound: replay the inner iteration as a CUDA graph
   bool use_graph = h->d.n <= (64LL << 20) && st != nullptr;
-  if (h->inner_graph && !use_graph) {
+  if (h->inner_graph && (!use_graph || h->graph_tf32 != tf32)) {
     cudaGraphExecDestroy(h->inner_graph);
     h->inner_graph = nullptr;
   }
   double *x = h->s64.x, *r = h->s64.r, *q = h->s64.q;
-  float *r32 = packed ? h->pr : h->r32, *p32 = packed ? h->pp : h->p32, *q32 = packed ? h->pq : h->q32,
+  float *r32 = packed ? h->pr : h->r32, *p32 = packed ? packed_p(h) : h->p32, *q32 = packed ? h->pq : h->q32,
         *d32 = packed ? h->pd : h->x32;
   int outer = 0, inner_total = 0, nsig64 = 0, nsiglow = 0;
   double relres = 1.0, sl[32];
@@ -850,7 +856,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // the float64 true residual takes its virtual-index terms from exact digit products on
   // the tensor cores when that is exact for this Nv, else from float64 GEMMs
   const int lv = split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
-  h->last_precision = ESMP2_MIXED_BF16;
+  h->last_precision = tf32 ? ESMP2_MIXED_TF32 : ESMP2_MIXED_BF16;
   h->r_true = false;
   const double eta = 1e-2;
   // An intermediate true residual only has to be accurate relative to itself: its digit
@@ -944,6 +950,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
         h->launches = l0;
         if (ok) {
           h->inner_graph_launches = h->inner_graph_launches_pending;
+          h->graph_tf32 = tf32;
           if ((s = check_cuda(h, cudaGraphLaunch(h->inner_graph, st), "inner graph"))) return s;
           h->launches += h->inner_graph_launches;
         } else {

@@ -490,8 +490,8 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
 }
 }  // namespace
 
-bool tma_map_bf16_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-                     uint32_t box_inner, uint32_t box_outer, int swizzle_bytes) {
+bool tma_map_2d(CUtensorMap *m, const void *base, bool f32, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                uint32_t box_inner, uint32_t box_outer, int swizzle_bytes) {
   if (!get_encode()) return false;
   const uint64_t dims[2] = {inner, outer};
   const uint64_t strides[1] = {row_bytes};
@@ -501,10 +501,11 @@ bool tma_map_bf16_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t 
                                 : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                 : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                                       : CU_TENSOR_MAP_SWIZZLE_NONE;
-  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
-                        reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides),
-                        reinterpret_cast<const cuuint32_t *>(box), estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = g_encode(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void *>(base), reinterpret_cast<const cuuint64_t *>(dims),
+                        reinterpret_cast<const cuuint64_t *>(strides), reinterpret_cast<const cuuint32_t *>(box), estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

@@ -1,5 +1,6 @@
-// Virtual-index contraction of the inner (bf16) sigma as one dense GEMM on the 5th-generation
-// tensor cores (the N_o^2 N_v^3 terms of Table 1, Eq. qfq_replacement).
+// Virtual-index contraction of the inner sigma as one dense GEMM on the 5th-generation tensor
+// cores (the N_o^2 N_v^3 terms of Table 1, Eq. qfq_replacement): bf16 operands (kind::f16) or
+// float32 operands read as tf32 (kind::tf32), fp32 accumulation in TMEM.
 //
 // Every slice s of the packed inner vector is an Nv x Nv matrix X_s with rows a and columns
 // c; the terms of a slice are X_s F and F X_s (F = F_vv, symmetric).  Stacking the rows of
@@ -14,9 +15,11 @@
 // Structure (persistent, 320 threads):
 //   each CTA owns one column tile b0 .. b0 + Nt - 1 of the result (columns split over nN
 //   tiles) and keeps that tile's panel W[b][c] (all K) resident in shared memory;
-//   warp 0      TMA producer: 2-D tiled bulk copies of 128-row x 32-column A chunks
-//               (64-byte swizzle) into a ring of 5 to 8 slots (what the panel leaves)
-//   warp 1      one thread issues tcgen05.mma (M = 128, N = Nt, K = 16), commits to mbarriers
+//   warp 0      TMA producer: 2-D tiled bulk copies of 128-row x 64-byte A chunks (32 bf16 or
+//               16 float32 columns; 64-byte swizzle) into a ring of 5 to 8 slots (what the
+//               panel leaves)
+//   warp 1      one thread issues tcgen05.mma (M = 128, N = Nt, K = 16 bf16 or 8 tf32, 32 bytes
+//               of each operand row per instruction), commits to mbarriers
 //   warps 2..9  epilogue: tcgen05.ld 32x32b from one of two TMEM accumulators (2 x Nt
 //               columns), fp32 stores of P rows (16-byte vectors) or of transposed rows (one
 //               128-byte segment per column and warp)
@@ -33,9 +36,14 @@ namespace esmp2 {
 namespace vg {
 
 constexpr int BM = 128;                 // accumulator rows (TMEM lanes)
-constexpr int BK = 32;                  // K elements per chunk: 64 bytes of bf16
+constexpr int CHUNK_B = 64;             // bytes of one operand row per K chunk (the swizzle span)
 constexpr int MAX_STAGES = 8;
-constexpr int A_STAGE = BM * BK * 2;    // 8 KB
+constexpr int A_STAGE = BM * CHUNK_B;   // 8 KB
+// K elements per chunk and per MMA: bf16 32 and 16, tf32 16 and 8 (both 32 bytes per MMA)
+template <bool TF32> struct Kind {
+  static constexpr int BK = TF32 ? 16 : 32;
+  static constexpr int KMMA = TF32 ? 8 : 16;
+};
 constexpr int NTHREADS = 320;
 // dynamic shared memory per CTA: the 232448-byte opt-in limit less room for the kernel's
 // static shared memory (barriers, TMEM address, flags)
@@ -95,15 +103,27 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
          (4ull << 61);
 }
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, N >> 3, M >> 4.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: D fp32 (bits 4-5 = 1); A and B format (bits 7-9, 10-12) bf16 = 1 of
+// kind::f16 or tf32 = 2 of kind::tf32; both K-major; N >> 3 at bit 17, M >> 4 at bit 24.
+template <bool TF32>
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+  const uint32_t fmt = TF32 ? 2u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+template <bool TF32>
 __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+  if constexpr (TF32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -125,7 +145,7 @@ struct Args {
   int64_t rows;         // rows of A and of the result, r = (slice, a)
   int64_t rows_normal;  // rows [0, rows_normal) go to P[r][b]; later rows to PT (transposed)
   int Nv;               // rows per slice (transposed part) and columns of the result
-  int nk;               // K chunks of BK (nk * BK >= Nv)
+  int nk;               // K chunks (nk * BK >= Nv)
   int nN;               // column tiles; CTA c works on tile c % nN
   int Nt;               // columns of a column tile (multiple of 16, <= 256)
   int stages;           // ring slots (<= MAX_STAGES)
@@ -136,8 +156,10 @@ struct Args {
   int *err;             // device error flag
 };
 
+template <bool TF32>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_vgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tF, Args g) {
+  constexpr int BK = Kind<TF32>::BK, KMMA = Kind<TF32>::KMMA;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int STAGES = g.stages;
@@ -149,7 +171,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x % g.nN, group = gridDim.x / g.nN, gi = blockIdx.x / g.nN;
   const int b0 = nt * g.Nt, nvalid = min(g.Nt, g.Nv - b0), nmma = (nvalid + 15) & ~15;
-  const uint32_t chunk_bytes = (uint32_t)g.Nt * 64u;
+  const uint32_t chunk_bytes = (uint32_t)g.Nt * CHUNK_B;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int s = 0; s < 2; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], 8); }
@@ -194,7 +216,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {  // ------------------------------------------------ MMA issuer
       bool ok = mbar_wait(&pbar, 0);
       tc_after();
-      const uint32_t id = idesc_bf16(BM, nmma);
+      const uint32_t id = idesc<TF32>(BM, nmma);
       const uint32_t pan = smem_u32(panel), rg = smem_u32(ring);
       int64_t it = 0;
       int lt = 0;
@@ -209,10 +231,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t rnd = (uint32_t)(it / STAGES);
           if (!mbar_wait(&full[st], rnd & 1)) { ok = false; break; }
           tc_after();
-          const int ksteps = min(BK / 16, (g.Nv - kc * BK + 15) / 16);   // skip 16-wide steps past Nv
+          const int ksteps = min(BK / KMMA, (g.Nv - kc * BK + KMMA - 1) / KMMA);   // skip K steps past Nv
           for (int k = 0; k < ksteps; ++k)
-            umma(d, sdesc64(rg + st * A_STAGE + 32 * k), sdesc64(pan + kc * chunk_bytes + 32 * k), id,
-                 (kc > 0 || k > 0) ? 1u : 0u);
+            umma<TF32>(d, sdesc64(rg + st * A_STAGE + 32 * k), sdesc64(pan + kc * chunk_bytes + 32 * k), id,
+                       (kc > 0 || k > 0) ? 1u : 0u);
           umma_commit(&empty[st]);
         }
         if (!ok) break;
@@ -275,12 +297,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // Column tiling of the GEMM: the fewest column tiles (each at most 256 columns, a multiple of
 // 16) whose resident panel and an operand ring of at least 5 slots fit the shared memory of
-// one CTA; the ring takes what is left, up to MAX_STAGES slots.
-static bool vgemm_tiling(int ncols, int Kc, int *nN, int *Nt, int *nk, int *stages, int *smem) {
-  const int k = (Kc + vg::BK - 1) / vg::BK;
+// one CTA; the ring takes what is left, up to MAX_STAGES slots.  bk: K elements per chunk.
+static bool vgemm_tiling(int ncols, int Kc, int bk, int *nN, int *Nt, int *nk, int *stages, int *smem) {
+  const int k = (Kc + bk - 1) / bk;
   for (int n = 1; n <= 64; ++n) {
     const int t = (((ncols + n - 1) / n) + 15) & ~15;
-    const int fixed = 1024 + k * t * 64;
+    const int fixed = 1024 + k * t * vg::CHUNK_B;
     if (t > 256 || fixed + 5 * vg::A_STAGE > vg::SMEM_MAX) continue;
     const int st = std::min(vg::MAX_STAGES, (vg::SMEM_MAX - fixed) / vg::A_STAGE);
     // at least 120 KB, so one CTA per SM: each CTA holds all 512 TMEM columns
@@ -290,11 +312,14 @@ static bool vgemm_tiling(int ncols, int Kc, int *nN, int *Nt, int *nk, int *stag
   return false;
 }
 
+// P = A W on the tensor cores.  A: rows x Nvp (row pitch Nvp elements), W: Nv x Nvp (row b of
+// W is column b of the right factor), both bf16, or both float32 read as tf32 (tf32 = true).
 esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
-                   float *PT, int ldp, double alg_flops) {
+                   float *PT, int ldp, double alg_flops, bool tf32) {
   const int Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
+  const int bk = tf32 ? vg::Kind<true>::BK : vg::Kind<false>::BK, esz = tf32 ? 4 : 2;
   int nN = 0, Nt = 0, nk = 0, stages = 0, smem = 0;
-  if (!vgemm_tiling(Nv, Nv, &nN, &Nt, &nk, &stages, &smem) || (ldp & 3) || rows <= 0) {
+  if (!vgemm_tiling(Nv, Nv, bk, &nN, &Nt, &nk, &stages, &smem) || (ldp & 3) || rows <= 0) {
     h->err = "vgemm: unsupported shape";
     return ESMP2_ERR_UNSUPPORTED;
   }
@@ -303,13 +328,14 @@ esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_no
     return ESMP2_ERR_UNSUPPORTED;
   }
   CUtensorMap mA, mW;
-  if (!tma_map_bf16_2d(&mA, A, (uint64_t)Nvp, (uint64_t)rows, (uint64_t)Nvp * 2, vg::BK, vg::BM, 64) ||
-      !tma_map_bf16_2d(&mW, W, (uint64_t)Nvp, (uint64_t)Nv, (uint64_t)Nvp * 2, vg::BK, (uint32_t)Nt, 64)) {
+  if (!tma_map_2d(&mA, A, tf32, (uint64_t)Nvp, (uint64_t)rows, (uint64_t)Nvp * esz, (uint32_t)bk, vg::BM, 64) ||
+      !tma_map_2d(&mW, W, tf32, (uint64_t)Nvp, (uint64_t)Nv, (uint64_t)Nvp * esz, (uint32_t)bk, (uint32_t)Nt, 64)) {
     h->err = "vgemm: tensor map encoding failed";
     return ESMP2_ERR_CUDA;
   }
-  if (cudaError_t e = smem_limit_once(reinterpret_cast<const void *>(vg::k_vgemm), vg::SMEM_MAX))
-    return check_cuda(h, e, "vgemm shared-memory limit");
+  const void *fn = tf32 ? reinterpret_cast<const void *>(vg::k_vgemm<true>)
+                        : reinterpret_cast<const void *>(vg::k_vgemm<false>);
+  if (cudaError_t e = smem_limit_once(fn, vg::SMEM_MAX)) return check_cuda(h, e, "vgemm shared-memory limit");
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -331,7 +357,8 @@ esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_no
   const double exec = 2.0 * (double)g.m_tiles * vg::BM * (double)Nv * (double)nN * Nt;
   {
     KScope ks(h->stream, ESMP2_KT_CONTRACTION, alg_flops, exec);
-    vg::k_vgemm<<<grid, vg::NTHREADS, smem, h->stream>>>(mA, mW, g);
+    if (tf32) vg::k_vgemm<true><<<grid, vg::NTHREADS, smem, h->stream>>>(mA, mW, g);
+    else vg::k_vgemm<false><<<grid, vg::NTHREADS, smem, h->stream>>>(mA, mW, g);
   }
   h->launches += 1;
   return check_cuda(h, cudaGetLastError(), "vgemm");

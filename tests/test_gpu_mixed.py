@@ -113,3 +113,56 @@ def test_solve_mixed_graph_replay_matches_oracle(No, Nv, seed):
     plain = handle_for(inst)
     info3 = plain.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
     assert info3["iterations"] == info["iterations"]
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(4, 9, 31), (6, 30, 0), (3, 300, 32)])
+def test_sigma_tf32_vs_oracle(No, Nv, seed):
+    """The tf32 inner sigma: operands keep 10 explicit mantissa bits (the low 13 bits of each
+    float32 are ignored, a relative error below 2^-10 per operand), so the result is closer
+    to the operator than the bf16 form on the same input and no closer than float32 rounding."""
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed, sigma_off=0.02)
+    h = handle_for(inst)
+    x = random_block_vector(No, Nv, seed + 7)
+    xt = _torch(x)
+    y32 = h.sigma(xt, esmp2.MIXED_TF32).cpu().numpy()
+    y16 = h.sigma(xt, esmp2.MIXED_BF16).cpu().numpy()
+    ref = o2.O2(top.prepare(inst)).sigma(x)
+    rel32 = float(np.linalg.norm(y32 - ref) / np.linalg.norm(ref))
+    rel16 = float(np.linalg.norm(y16 - ref) / np.linalg.norm(ref))
+    assert 1e-7 < rel32 < 1.5e-3, rel32
+    assert rel32 < 0.5 * rel16, (rel32, rel16)
+    assert float(np.abs(y32 - ref).max()) <= 5e-3 * float(np.abs(ref).max())
+    assert not np.any(y32[~masks(No, Nv)])
+    assert np.array_equal(y32[0], -y32[0].transpose(0, 1, 3, 2))
+
+
+@pytest.mark.parametrize("No,Nv,seed", [(3, 5, 11), (6, 30, 0), (5, 64, 14)])
+def test_solve_tf32_matches_oracle(No, Nv, seed):
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(No, Nv, seed)
+    h = handle_for(inst)
+    info = h.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_TF32)
+    e = h.energy()
+    ref = o2.solve(top.prepare(inst), tol=1e-12)
+    assert info["rel_residual"] <= 1e-11 and info["outer"] >= 1 and info["sigma_lowp"] > 0
+    assert abs(e["E2"] - ref["E2"]) < 1e-10
+    x = h.solution().cpu().numpy()
+    assert np.abs(x - ref["x"]).max() < 1e-8 * np.abs(ref["x"]).max()
+    # bf16 and tf32 solves alternate on one handle (separate operands, graph rebuilt)
+    import torch
+    h.set_solution(torch.zeros(h.shape, dtype=torch.float64, device="cuda"))
+    info2 = h.solve(tol=1e-11, maxit=2000, precision=esmp2.MIXED_BF16)
+    assert info2["rel_residual"] <= 1e-11
+    assert abs(h.energy()["E2"] - ref["E2"]) < 1e-10
+    ms = h.profile_sigma(h.rhs(), precision=esmp2.MIXED_TF32, reps=1)
+    assert ms[0] >= 0.0 and ms[1] > 0.0 and ms[4] > 0.0
+
+
+def test_tf32_needs_packed_inner_solve():
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(33, 34, 5)
+    h = handle_for(inst)
+    with pytest.raises(esmp2.Esmp2Error) as ei:
+        h.solve(tol=1e-8, maxit=10, precision=esmp2.MIXED_TF32)
+    assert ei.value.status == esmp2.ERR_UNSUPPORTED
