@@ -60,6 +60,14 @@ typedef enum {
                             of each float32 operand ignored) with fp32 accumulation; the inner PCG
                             vector p is itself the operand.  Packed inner solve only: No <= 32, else
                             ESMP2_ERR_UNSUPPORTED. */
+  ESMP2_REDUCED_MIXED = 4, /* the D + L solve in the reduced-cost basis: occupied orbitals other than t
+                            and virtual orbitals other than t' diagonalise their blocks of F (D and L
+                            are unchanged by rotations that fix t and t', Sec. II.C), so both blocks
+                            are a diagonal plus the t / t' row and column and every virtual-index
+                            term is element-wise (no N_o^2 N_v^3 contraction).  Float32 inner PCG
+                            inside float64 refinement; the right-hand side is rotated once
+                            (float64-exact digit-split products).  E2 equals the other forms' to
+                            the solve tolerance; E2_S stays in the TOP basis.  No <= 32, Nv <= 1024. */
   ESMP2_FP64_TC = 3      /* float64-accurate virtual-index terms: x and F_vv split into exact 6-bit
                             bf16 digits (per-slice power-of-two scale), digit products summed exactly
                             in fp32 on tcgen05 level by level (levels 2..10) and combined in float64;
@@ -145,7 +153,8 @@ esmp2_status esmp2_top_basis(esmp2_handle *h, double *U, double *lam, double *Wv
  * have the spin-flip symmetry of the singlet, S_ij^ab = S_ji^ba (every vector of the problem
  * has it: b, the solution and every Krylov vector), and returns y with that symmetry and the
  * antisymmetry of T, X, Y exactly.  ESMP2_MIXED_TF32: the same with the virtual-index
- * contraction on tf32 operands (No <= 32).  x and y must not overlap. */
+ * contraction on tf32 operands (No <= 32).  ESMP2_REDUCED_MIXED: the inner float32 sigma of the
+ * reduced-cost basis (x rotated in, y rotated back; No <= 32).  x and y must not overlap. */
 esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_precision p);
 
 /* Per-stage device timing of `reps` sigma builds y = A x (same arguments as esmp2_sigma),
@@ -174,7 +183,8 @@ esmp2_status esmp2_rhs(esmp2_handle *h, double *b);
  * (Sec. III.A uses CG).  ESMP2_FP64: plain fp64 PCG.  ESMP2_MIXED_BF16: fp64
  * iterative refinement, each step solving the correction with bf16/fp32 inner
  * PCG.  ESMP2_MIXED_TF32: the same with tf32 inner contractions (No <= 32, else
- * UNSUPPORTED).  Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
+ * UNSUPPORTED).  ESMP2_REDUCED_MIXED: the same in the reduced-cost basis (see the enum).
+ * Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
  * (Mixed: intermediate true residuals far from tol take fewer exact digit levels and a
  * float32 coupling pass, accurate relative to their own size; the residual that stops
  * the solve, and that the energy reuses, is float64-accurate throughout.)
@@ -201,7 +211,8 @@ esmp2_status esmp2_energy(esmp2_handle *h, esmp2_energy_parts *parts);
  * instances in order from a shared counter, so small instances overlap; device memory in
  * use is that of `concurrency` instances at a time.  In the mixed solve of an instance of
  * at most 64M amplitudes the inner PCG iteration is captured once and replayed as a CUDA
- * graph.  p: ESMP2_FP64, ESMP2_FP64_TC, ESMP2_MIXED_BF16 or ESMP2_MIXED_TF32.  Returns ESMP2_OK if every
+ * graph.  p: ESMP2_FP64, ESMP2_FP64_TC, ESMP2_MIXED_BF16, ESMP2_MIXED_TF32 or ESMP2_REDUCED_MIXED.
+ * Returns ESMP2_OK if every
  * instance succeeded, else the first failing status (every instance is still attempted). */
 typedef struct {
   esmp2_status status;

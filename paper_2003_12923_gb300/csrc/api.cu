@@ -207,9 +207,10 @@ esmp2_status esmp2_sigma(esmp2_handle *h, const double *x, double *y, esmp2_prec
     if (!split_supported(h, kFp64TcLevels)) { h->err = "ESMP2_FP64_TC needs Nv < 910"; return ESMP2_ERR_UNSUPPORTED; }
     return sigma64(h, x, y, kFp64TcLevels);
   }
-  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32) {
-    if (p == ESMP2_MIXED_TF32 && h->d.No > 32) { h->err = "ESMP2_MIXED_TF32 needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
+  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32 || p == ESMP2_REDUCED_MIXED) {
+    if (p != ESMP2_MIXED_BF16 && h->d.No > 32) { h->err = "precision needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
     h->tf32 = p == ESMP2_MIXED_TF32;
+    h->arrowv = p == ESMP2_REDUCED_MIXED;
     return sigma_mixed(h, x, y);
   }
   h->err = "precision not supported";
@@ -221,9 +222,10 @@ esmp2_status esmp2_profile_sigma(esmp2_handle *h, const double *x, double *y, es
   if (!h || !x || !y || !ms || x == y || reps < 1) return ESMP2_ERR_INVALID_ARG;
   if (p == ESMP2_FP64) return profile64(h, x, y, reps, ms);
   if (p == ESMP2_FP64_TC && split_supported(h, kFp64TcLevels)) return profile64(h, x, y, reps, ms, kFp64TcLevels);
-  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32) {
-    if (p == ESMP2_MIXED_TF32 && h->d.No > 32) { h->err = "ESMP2_MIXED_TF32 needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
+  if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32 || p == ESMP2_REDUCED_MIXED) {
+    if (p != ESMP2_MIXED_BF16 && h->d.No > 32) { h->err = "precision needs No <= 32"; return ESMP2_ERR_UNSUPPORTED; }
     h->tf32 = p == ESMP2_MIXED_TF32;
+    h->arrowv = p == ESMP2_REDUCED_MIXED;
     return profile_mixed(h, x, y, reps, ms);
   }
   h->err = "precision not supported";
@@ -254,23 +256,30 @@ esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision
   }
   if (p == ESMP2_MIXED_BF16) return solve_mixed(h, tol, maxit, info);
   if (p == ESMP2_MIXED_TF32) return solve_mixed(h, tol, maxit, info, true);
+  if (p == ESMP2_REDUCED_MIXED) return solve_mixed(h, tol, maxit, info, false, true);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
 }
 
 esmp2_status esmp2_get_solution(esmp2_handle *h, double *x) {
   if (!h || !x) return ESMP2_ERR_INVALID_ARG;
-  if (h->x_semi)
-    rotate_occ(h, h->s64.x, x, h->s64.p, false);
-  else
+  if (h->x_basis == 0) {
     cudaMemcpyAsync(x, h->s64.x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
+  } else {   // rotated back to the TOP basis (the stored solution keeps its basis)
+    const double *src = h->s64.x;
+    if (h->x_basis == 2) {
+      if (esmp2_status s = rotate_virt(h, src, x, h->s64.p, false)) return s;
+      src = x;
+    }
+    rotate_occ(h, src, x, h->s64.p, false);
+  }
   return check_cuda(h, cudaGetLastError(), "get_solution");
 }
 
 esmp2_status esmp2_set_solution(esmp2_handle *h, const double *x) {
   if (!h || !x) return ESMP2_ERR_INVALID_ARG;
   cudaMemcpyAsync(h->s64.x, x, sizeof(double) * h->d.n, cudaMemcpyDeviceToDevice, h->stream);
-  h->x_semi = 0;
+  h->x_basis = 0;
   h->x_zero = false;
   h->r_true = false;
   return check_cuda(h, cudaGetLastError(), "set_solution");

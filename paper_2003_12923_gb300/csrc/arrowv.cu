@@ -1,0 +1,387 @@
+// The reduced-cost basis of the D + L solve (ESMP2_REDUCED_MIXED).
+//
+// The doubles and the L-triples are unchanged by any rotation of the occupied orbitals that
+// fixes t and of the virtual orbitals that fixes t' (Sec. II.C: the first-order space is
+// defined by the large TOP pair alone).  In the basis whose occupied orbitals other than t
+// diagonalise F_oo and whose virtual orbitals other than t' diagonalise F_vv, both blocks of
+// F are "arrow" shaped: a diagonal plus the t (t') row and column.  Then the virtual-index
+// terms of the sigma build (the N_o^2 N_v^3 contractions of Table 1 in the TOP basis) become
+//     (X F)_ab = F_bb X_ab + X_a0 F_0b  (b >= 1),   (X F)_a0 = sum_c X_ac F_c0,
+//     (F X)_ab = F_aa X_ab + F_a0 X_0b  (a >= 1),   (F X)_0b = sum_c F_0c X_cb,
+// streaming work with one row sum and one column sum per slice.  E2_D + E2_L is the same in
+// exact arithmetic; E2_S (Sec. II.D) stays in the TOP basis.  The price is the one-time
+// rotation of the right-hand side (and of the solution, when it is asked for), two float64-
+// exact digit-split products per slice.
+//
+// The eigenvectors of the virtual block come from the cyclic Jacobi method (Golub and Van
+// Loan, Sec. 8.5) with the round-robin ordering of disjoint pairs: one launch per round, all
+// n/2 rotations of a round applied at once as A' = J^T A J, V' = V J.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace esmp2 {
+namespace {
+
+__global__ void k_to_f32(const double *src, float *dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
+// A (m x m) = the virtual block of F without t' (rows and columns 1 .. Nv-1); V = I
+__global__ void k_vblock(const double *F, int N, int No, int m, double *A, double *V) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    A[e] = F[(int64_t)(No + 1 + i) * N + No + 1 + j];
+    V[e] = i == j ? 1.0 : 0.0;
+  }
+}
+
+// One round r of the cyclic Jacobi method: rotations of the disjoint pairs (p, q) of the
+// round-robin ordering of n = m (+1 if m is odd) indices, each chosen to zero A_pq
+// (tau = (A_qq - A_pp) / (2 A_pq), t the smaller root of t^2 + 2 tau t - 1 = 0,
+// c = 1 / sqrt(1 + t^2), s = t c; J_pp = J_qq = c, J_pq = s, J_qp = -s); then
+// A2 = J^T A J and V2 = V J.  Column i of J has two entries: J_ii = al[i] and
+// J_{partner(i), i} = be[i].  Every CTA forms the round's table in shared memory.
+__global__ void __launch_bounds__(512) k_jacobi_round(const double *A, double *A2, const double *V, double *V2,
+                                                      int m, int r) {
+  __shared__ int part[1024];
+  __shared__ double al[1024], be[1024];
+  const int n = m + (m & 1);
+  for (int pi = threadIdx.x; pi < n / 2; pi += blockDim.x) {
+    int p, q;
+    if (pi == 0) {
+      p = 0;
+      q = 1 + (r % (n - 1));
+    } else {
+      p = 1 + ((pi + r) % (n - 1));
+      q = 1 + ((n - 1 - pi + r) % (n - 1));
+    }
+    if (p > q) { const int t = p; p = q; q = t; }
+    if (q >= m) {   // p is paired with the padding index
+      part[p] = p; al[p] = 1.0; be[p] = 0.0;
+      continue;
+    }
+    double c = 1.0, s = 0.0;
+    const double apq = A[(int64_t)p * m + q];
+    if (apq != 0.0) {
+      const double tau = (A[(int64_t)q * m + q] - A[(int64_t)p * m + p]) / (2.0 * apq);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      c = 1.0 / sqrt(1.0 + t * t);
+      s = t * c;
+    }
+    part[p] = q; al[p] = c; be[p] = -s;
+    part[q] = p; al[q] = c; be[q] = s;
+  }
+  __syncthreads();
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * mm; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < mm) {
+      const int i = (int)(e / m), j = (int)(e % m), pi = part[i], pj = part[j];
+      const double ri = al[j] * A[(int64_t)i * m + j] + be[j] * A[(int64_t)i * m + pj];
+      const double rp = al[j] * A[(int64_t)pi * m + j] + be[j] * A[(int64_t)pi * m + pj];
+      A2[e] = al[i] * ri + be[i] * rp;
+    } else {
+      const int64_t f = e - mm;
+      const int k = (int)(f / m), j = (int)(f % m), pj = part[j];
+      V2[f] = al[j] * V[(int64_t)k * m + j] + be[j] * V[(int64_t)k * m + pj];
+    }
+  }
+}
+
+// out[0] = sum of squares of the off-diagonal elements, out[1] = of all elements (one CTA)
+__global__ void __launch_bounds__(1024) k_offnorm(const double *A, int m, double *out) {
+  __shared__ double s0[32], s1[32];
+  double off = 0.0, tot = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const double v = A[e] * A[e];
+    tot += v;
+    if (e / m != e % m) off += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  }
+  if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = off; s1[threadIdx.x >> 5] = tot; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s0[w]; b += s1[w]; }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// Rv = diag(1, V) (Nv x Nv), Rvt = Rv^T, W3 = diag(I_No, Rv) (N x N)
+__global__ void k_build_rv(const double *V, int No, int Nv, double *Rv, double *Rvt, double *W3) {
+  const int N = No + Nv, m = Nv - 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / N), q = (int)(e % N);
+    double v = p == q ? 1.0 : 0.0;
+    if (p > No && q > No) v = V[(int64_t)(p - No - 1) * m + (q - No - 1)];
+    else if (p >= No && q >= No && p != q) v = 0.0;
+    W3[e] = p < No || q < No ? (p == q ? 1.0 : 0.0) : v;
+    if (p >= No && q >= No) {
+      Rv[(int64_t)(p - No) * Nv + (q - No)] = v;
+      Rvt[(int64_t)(q - No) * Nv + (p - No)] = v;
+    }
+  }
+}
+
+// the virtual block of F made exactly arrow shaped: elements (c, d), c != d, both >= 1 (of the
+// order of the Jacobi tolerance) set to zero, and the t' row and column made symmetric
+__global__ void k_clean_arrow(double *F, int No, int Nv) {
+  const int N = No + Nv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)Nv * Nv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / Nv), d = (int)(e % Nv);
+    if (c != d && c >= 1 && d >= 1) F[(int64_t)(No + c) * N + No + d] = 0.0;
+    if (c == 0 && d > 0) {
+      const double v = 0.5 * (F[(int64_t)No * N + No + d] + F[(int64_t)(No + d) * N + No]);
+      F[(int64_t)No * N + No + d] = v;
+      F[(int64_t)(No + d) * N + No] = v;
+    }
+  }
+}
+
+// out[s] = in[s]^T for S slices of Nv x Nv (32 x 32 tiles through shared memory)
+__global__ void __launch_bounds__(256) k_tr64(const double *in, double *out, int64_t S, int Nv) {
+  __shared__ double t[32][33];
+  const int nt = (Nv + 31) / 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t items = S * nt * nt, NvNv = (int64_t)Nv * Nv;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t s = it / (nt * nt);
+    const int tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    const double *src = in + s * NvNv;
+    double *dst = out + s * NvNv;
+    for (int r = ty; r < 32; r += 8) {
+      const int a = ta * 32 + r, b = tb * 32 + tx;
+      t[r][tx] = (a < Nv && b < Nv) ? src[(int64_t)a * Nv + b] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int b = tb * 32 + r, a = ta * 32 + tx;
+      if (a < Nv && b < Nv) dst[(int64_t)b * Nv + a] = t[tx][r];
+    }
+    __syncthreads();
+  }
+}
+
+// float64 virtual-index terms in the reduced-cost basis, every slice s of the block vector:
+// rho[s][a] = sum_c x_s[a][c] F_t'c (warp per row), kap[s][b] = sum_c F_t'c x_s[c][b] (thread per
+// column), then y = X F + F X element-wise.
+__global__ void k_rowsum64(const double *x, const double *F, int No, int Nv, int64_t rows, double *rho) {
+  const int N = No + Nv, lane = threadIdx.x & 31;
+  const double *f = F + (int64_t)No * N + No;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double *xr = x + r * Nv;
+    double s = 0.0;
+    for (int c = lane; c < Nv; c += 32) s += xr[c] * f[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) rho[r] = s;
+  }
+}
+__global__ void k_colsum64(const double *x, const double *F, int No, int Nv, int64_t S, double *kap) {
+  const int N = No + Nv;
+  const double *f = F + (int64_t)No * N + No;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < S * Nv; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / Nv;
+    const int b = (int)(e % Nv);
+    const double *xs = x + s * Nv * Nv + b;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int c = 0; c < Nv; ++c) acc += f[c] * xs[(int64_t)c * Nv];
+    kap[e] = acc;
+  }
+}
+__global__ void k_varrow64(const double *x, const double *F, const double *rho, const double *kap, int No, int Nv,
+                           int64_t n, double *y) {
+  const int N = No + Nv;
+  const int64_t NvNv = (int64_t)Nv * Nv;
+  const double *f = F + (int64_t)No * N + No;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / NvNv;
+    const int ab = (int)(e % NvNv), a = ab / Nv, b = ab % Nv;
+    const double *xs = x + s * NvNv;
+    const double xab = xs[ab];
+    double v;
+    if (b >= 1) v = F[(int64_t)(No + b) * N + No + b] * xab + xs[(int64_t)a * Nv] * f[b];
+    else v = rho[s * Nv + a];
+    if (a >= 1) v += F[(int64_t)(No + a) * N + No + a] * xab + f[a] * xs[b];
+    else v += kap[s * Nv + b];
+    y[e] = v;
+  }
+}
+
+}  // namespace
+
+esmp2_status ensure_arrow(esmp2_handle *h) {
+  if (h->arrow_ready) return ESMP2_OK;
+  esmp2_status s = ensure_mixed(h, true);
+  if (s) return s;
+  const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, m = Nv - 1;
+  if (Nv > 1024) {
+    h->err = "the reduced-cost basis supports Nv <= 1024";
+    return ESMP2_ERR_UNSUPPORTED;
+  }
+  const size_t n = (size_t)h->d.n, S = (size_t)5 * No * No;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, st);
+  };
+  A(reinterpret_cast<void **>(&h->Rv), sizeof(double) * (size_t)Nv * Nv);
+  A(reinterpret_cast<void **>(&h->Rvt), sizeof(double) * (size_t)Nv * Nv);
+  A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
+  A(reinterpret_cast<void **>(&h->barr), sizeof(double) * n);
+  A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
+  A(reinterpret_cast<void **>(&h->rho64), sizeof(double) * S * Nv);
+  A(reinterpret_cast<void **>(&h->kap64), sizeof(double) * S * Nv);
+  double *A0 = nullptr, *A1 = nullptr, *V0 = nullptr, *V1 = nullptr, *W3 = nullptr, *T1 = nullptr, *nrm = nullptr;
+  const size_t mm = (size_t)std::max(1, m * m);
+  A(reinterpret_cast<void **>(&A0), sizeof(double) * mm);
+  A(reinterpret_cast<void **>(&A1), sizeof(double) * mm);
+  A(reinterpret_cast<void **>(&V0), sizeof(double) * mm);
+  A(reinterpret_cast<void **>(&V1), sizeof(double) * mm);
+  A(reinterpret_cast<void **>(&W3), sizeof(double) * (size_t)N * N);
+  A(reinterpret_cast<void **>(&T1), sizeof(double) * (size_t)N * N);
+  A(reinterpret_cast<void **>(&nrm), sizeof(double) * 2);
+  auto release = [&]() {
+    dfree(A0, st); dfree(A1, st); dfree(V0, st); dfree(V1, st); dfree(W3, st); dfree(T1, st); dfree(nrm, st);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return check_cuda(h, e, "reduced-cost basis buffers");
+  }
+  // eigenvectors of F_vv without t'
+  if (m >= 1) {
+    k_vblock<<<256, 256, 0, st>>>(h->Fsemi, N, No, m, A0, V0);
+    h->launches += 1;
+    const int rounds = m + (m & 1) - 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(2LL * m * m, 512), 304);
+    double prev = -1.0;
+    // sweeps until the off-diagonal part is at the rounding level: below 1e-15 of the norm,
+    // or no longer shrinking (after quadratic convergence the rotations only move rounding
+    // noise around)
+    for (int sweep = 0; sweep < 20; ++sweep) {
+      for (int r = 0; r < rounds; ++r) {
+        k_jacobi_round<<<grid, 512, 0, st>>>(A0, A1, V0, V1, m, r);
+        std::swap(A0, A1);
+        std::swap(V0, V1);
+      }
+      h->launches += rounds + 1;
+      k_offnorm<<<1, 1024, 0, st>>>(A0, m, nrm);
+      double hn[2] = {0.0, 0.0};
+      e = cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        release();
+        return check_cuda(h, e, "reduced-cost basis (Jacobi)");
+      }
+      if (!(hn[0] > 1e-30 * hn[1])) break;
+      if (sweep >= 2 && hn[0] > 0.25 * prev) break;
+      prev = hn[0];
+    }
+    debug_phase(h, "  reduced basis: Jacobi eigenvectors of the virtual block");
+  }
+  k_build_rv<<<256, 256, 0, st>>>(V0, No, Nv, h->Rv, h->Rvt, W3);
+  // Farr = W3^T Fsemi W3
+  Gemm64 g{};
+  g.alpha = 1.0; g.beta = 0.0; g.batch = 1; g.M = N; g.N = N; g.K = N;
+  g.A = h->Fsemi; g.sAm = N; g.sAk = 1; g.B = W3; g.sBk = N; g.sBn = 1; g.C = T1; g.sCm = N; g.sCn = 1;
+  gemm64(g, st);
+  g.A = W3; g.sAm = 1; g.sAk = N; g.B = T1; g.sBk = N; g.sBn = 1; g.C = h->Farr; g.sCm = N; g.sCn = 1;
+  gemm64(g, st);
+  k_clean_arrow<<<256, 256, 0, st>>>(h->Farr, No, Nv);
+  k_to_f32<<<64, 256, 0, st>>>(h->Farr, h->F32arr, (int64_t)N * N);
+  h->launches += 5;
+  // the right-hand side in the reduced-cost basis (float64-exact digit-split rotations)
+  s = rotate_virt(h, h->bsemi, h->barr, h->s64.w ? h->s64.w : h->s64.p, true);
+  release();
+  if (s) return s;
+  debug_phase(h, "  reduced basis: F and rhs rotation");
+  h->arrow_ready = true;
+  return check_cuda(h, cudaGetLastError(), "reduced-cost basis");
+}
+
+// out = R~^T X R~ (to_arrow) or R~ X R~^T for every slice X of a full-storage block vector:
+// X R (digit-split product), transpose, X R again, transpose.  in may equal out; tmp: n doubles.
+esmp2_status rotate_virt(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_arrow) {
+  const int No = h->d.No, Nv = h->d.Nv;
+  const int64_t S = 5LL * No * No, rows = S * Nv;
+  const double *M = to_arrow ? h->Rv : h->Rvt;
+  void **dig = to_arrow ? &h->Rvdig : &h->Rvtdig;
+  int *eM = to_arrow ? &h->eRv : &h->eRvt;
+  const int slot = to_arrow ? 2 : 3;
+  const unsigned gt = (unsigned)std::min<int64_t>(S * ((Nv + 31) / 32) * ((Nv + 31) / 32), 4864);
+  esmp2_status s = xwm_split(h, in, rows, tmp, M, dig, eM, slot);
+  if (s) return s;
+  k_tr64<<<gt, 256, 0, h->stream>>>(tmp, out, S, Nv);
+  if ((s = xwm_split(h, out, rows, tmp, M, dig, eM, slot))) return s;
+  k_tr64<<<gt, 256, 0, h->stream>>>(tmp, out, S, Nv);
+  h->launches += 2;
+  if ((s = check_device_flag(h))) return s;
+  return check_cuda(h, cudaGetLastError(), "rotate_virt");
+}
+
+// Move the stored solution to `target` (0 TOP, 1 semicanonical-occupied, 2 reduced-cost basis).
+esmp2_status x_to_basis(esmp2_handle *h, int target) {
+  if (h->x_basis == target) return ESMP2_OK;
+  if (h->x_zero) {   // zero in every basis
+    h->x_basis = target;
+    return ESMP2_OK;
+  }
+  double *x = h->s64.x, *tmp = h->s64.w ? h->s64.w : h->s64.p;
+  esmp2_status s = ESMP2_OK;
+  h->r_true = false;
+  if (h->x_basis == 2) {
+    if ((s = rotate_virt(h, x, x, tmp, false))) return s;
+    h->x_basis = 1;
+  }
+  if (target == 0 && h->x_basis == 1) {
+    rotate_occ(h, x, x, tmp, false);
+    h->x_basis = 0;
+  }
+  if (target >= 1 && h->x_basis == 0) {
+    if ((s = ensure_mixed(h, true))) return s;
+    rotate_occ(h, x, x, tmp, true);
+    h->x_basis = 1;
+  }
+  if (target == 2 && h->x_basis == 1) {
+    if ((s = ensure_arrow(h))) return s;
+    if ((s = rotate_virt(h, x, x, tmp, true))) return s;
+    h->x_basis = 2;
+  }
+  return check_cuda(h, cudaGetLastError(), "x_to_basis");
+}
+
+void virt_arrow64(esmp2_handle *h, const double *x, double *y) {
+  const int No = h->d.No, Nv = h->d.Nv;
+  const int64_t S = 5LL * No * No;
+  cudaStream_t st = h->stream;
+  KScope ks(st, ESMP2_KT_CONTRACTION, alg_virtual_flops(No, Nv), 6.0 * (double)h->d.n);
+  k_rowsum64<<<1216, 256, 0, st>>>(x, h->Farr, No, Nv, S * Nv, h->rho64);
+  k_colsum64<<<(unsigned)std::min<int64_t>(cdiv(S * Nv, 256), 4864), 256, 0, st>>>(x, h->Farr, No, Nv, S, h->kap64);
+  k_varrow64<<<1216, 256, 0, st>>>(x, h->Farr, h->rho64, h->kap64, No, Nv, h->d.n, y);
+  h->launches += 3;
+}
+
+// float64 sigma in the reduced-cost basis: the virtual-index terms element-wise, the
+// occupied-index terms and couplings by the arrow-form coupling pass (Farr).
+esmp2_status sigma64_arrow(esmp2_handle *h, const double *x, double *y, int couplings) {
+  virt_arrow64(h, x, y);
+  if (couplings) {
+    launch_intermediates64(h, h->Farr, 1, x);
+    launch_couple64(h, h->Farr, 1, x, y);
+  }
+  return check_cuda(h, cudaGetLastError(), "sigma64_arrow");
+}
+
+}  // namespace esmp2

@@ -20,7 +20,8 @@ extern "C" esmp2_status esmp2_batch_solve(const esmp2_desc *descs, int count, do
                                           esmp2_precision p, int concurrency, esmp2_batch_result *results) {
   using namespace esmp2;
   if (!descs || !results || count < 0 || concurrency < 1 || !(tol > 0) || maxit < 1) return ESMP2_ERR_INVALID_ARG;
-  if (p != ESMP2_FP64 && p != ESMP2_MIXED_BF16 && p != ESMP2_MIXED_TF32 && p != ESMP2_FP64_TC)
+  if (p != ESMP2_FP64 && p != ESMP2_MIXED_BF16 && p != ESMP2_MIXED_TF32 && p != ESMP2_FP64_TC &&
+      p != ESMP2_REDUCED_MIXED)
     return ESMP2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ESMP2_ERR_CUDA;
@@ -35,7 +36,8 @@ extern "C" esmp2_status esmp2_batch_solve(const esmp2_desc *descs, int count, do
       esmp2_handle *h = nullptr;
       esmp2_status s = create_impl(&h, &descs[k], st);
       if (!s) {
-        if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32) s = solve_mixed(h, tol, maxit, &r.info, p == ESMP2_MIXED_TF32);
+        if (p == ESMP2_MIXED_BF16 || p == ESMP2_MIXED_TF32 || p == ESMP2_REDUCED_MIXED)
+          s = solve_mixed(h, tol, maxit, &r.info, p == ESMP2_MIXED_TF32, p == ESMP2_REDUCED_MIXED);
         else s = solve64(h, tol, maxit, &r.info, p == ESMP2_FP64_TC ? 1 : 0);
       }
       if (!s) s = energy(h, &r.e2);

@@ -390,10 +390,7 @@ esmp2_status gradient(esmp2_handle *h, double *dF_host, double *dOVOV_host, int 
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N;
   const int64_t nov = (int64_t)No * Nv * No * Nv, n = h->d.n;
   cudaStream_t st = h->stream;
-  if (h->x_semi) {
-    rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
-    h->x_semi = 0;
-  }
+  if (esmp2_status s0 = x_to_basis(h, 0)) return s0;
   if (adj_diff) *adj_diff = 0.0;
   if (adjoint) {  // A is symmetric: the adjoint solve A^T lambda = -b must return x itself
     double *xs = nullptr;

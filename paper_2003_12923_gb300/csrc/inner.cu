@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -522,6 +523,8 @@ struct CP {
   const float *FZ;     // F Z_s (normal orientation) for every Z slice
   const float *VX, *WZ;  // [No][No][Nv]
   const float *OC1, *OC2, *OX, *OZ, *G, *H, *CYZ;
+  const float *rho;    // reduced-cost basis: [packed slice][a] sum_c x[a][c] F_t'c
+  const float *kap;    // reduced-cost basis: [Z slice][b] sum_c F_t'c Z[c][b]
   double *dot;         // per-CTA partials of <x, y>_w, or nullptr
   int64_t dot_base;
 };
@@ -539,6 +542,41 @@ __device__ __forceinline__ SV sv(const PV &pv, const float *v, int blk, int i, i
   return {p, sg};
 }
 
+// (X F)_ab of the packed slice X (row pitch Nvp, row sums rs) in the reduced-cost basis, where
+// F_vv is a diagonal plus the t' row and column: F_bb X_ab + X_a0 F_t'b for b >= 1, rs[a] for b = 0
+__device__ __forceinline__ float xf_arrow(const FF &F, const float *xs, const float *rs, int Nvp, int a, int b) {
+  return b == 0 ? rs[a] : F.v(b, b) * __ldg(xs + (int64_t)a * Nvp + b) + __ldg(xs + (int64_t)a * Nvp) * F.v(0, b);
+}
+
+// Reduced-cost basis: row sums rho[s][a] = sum_c x_s[a][c] F_t'c of every packed slice (warp per
+// row) and column sums kap[z][b] = sum_c F_t'c Z_z[c][b] of the Z slices (thread per column)
+__global__ void kp_vsum(PV pv, FF F, const float *__restrict__ x, float *rho, float *kap) {
+  const Packed &L = pv.L;
+  const int Nv = L.Nv, Nvp = L.Nvp, lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)L.nslices * Nv, cols = (int64_t)L.NN * Nv;
+  const int64_t nw = rows, tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = tid >> 5; r < nw; r += nth >> 5) {
+    const int64_t s = r / Nv, a = r % Nv;
+    const float *xr = x + s * L.SL + a * Nvp;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int c = lane; c < Nv; c += 32) acc += __ldg(xr + c) * F.v(0, c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) rho[r] = acc;
+  }
+  const float *Zb = x + L.boff[BZ];
+  for (int64_t e = tid; e < cols; e += nth) {
+    const int64_t z = e / Nv;
+    const int b = (int)(e % Nv);
+    const float *zc = Zb + z * L.SL + b;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < Nv; ++c) acc += F.v(0, c) * __ldg(zc + (int64_t)c * Nvp);
+    kap[e] = acc;
+  }
+}
+
 // items [first, last) of the blocked assignment of `items` work items to this CTA
 __device__ __forceinline__ void cta_items(int64_t items, int64_t &first, int64_t &last) {
   const int64_t per = (items + gridDim.x - 1) / gridDim.x;
@@ -550,7 +588,7 @@ __device__ __forceinline__ void cta_items(int64_t items, int64_t &first, int64_t
 // (tb, ta).  Every slice pointer of the item is resolved once; the product tiles of the next
 // item are loaded into registers while the current one is computed.  The element formulas are
 // the full-storage coupling pass's (sigma.cu k_couple, arrow form) with i < j.
-template <int BLK>
+template <int BLK, bool AV>
 __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Ys[kT][kT + 1];
@@ -572,11 +610,18 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
     int k, ta, tb;
     decode(it, k, ta, tb);
     const float *P = c.P + L.boff[BLK] + (int64_t)k * L.SL;
+    const float *xs = c.x + L.boff[BLK] + (int64_t)k * L.SL;
+    const float *rs = AV ? c.rho + (int64_t)(slice0(L, BLK) + k) * Nv : nullptr;
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int r = ty + 8 * rr, a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
-      pa[rr] = (a < Nv && b < Nv) ? __ldg(P + (int64_t)a * Nvp + b) : 0.f;
-      pb[rr] = (a2 < Nv && b2 < Nv) ? __ldg(P + (int64_t)a2 * Nvp + b2) : 0.f;
+      if constexpr (AV) {
+        pa[rr] = (a < Nv && b < Nv) ? xf_arrow(c.F, xs, rs, Nvp, a, b) : 0.f;
+        pb[rr] = (a2 < Nv && b2 < Nv) ? xf_arrow(c.F, xs, rs, Nvp, a2, b2) : 0.f;
+      } else {
+        pa[rr] = (a < Nv && b < Nv) ? __ldg(P + (int64_t)a * Nvp + b) : 0.f;
+        pb[rr] = (a2 < Nv && b2 < Nv) ? __ldg(P + (int64_t)a2 * Nvp + b2) : 0.f;
+      }
     }
   };
   float dsum = 0.f;
@@ -666,6 +711,7 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
 // S: work item = (slice pair i <= j, tile (ta, tb)); y_ij on tile (ta, tb), y_ji = y_ij^T.  The
 // tiles read transposed (P_ji, Z_ji and, for i = 0, OZ_j) of the next item are loaded into
 // registers while the current one is computed.
+template <bool AV>
 __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Zt[kT][kT + 1], Ot[kT][kT + 1], Ys[kT][kT + 1];
@@ -690,13 +736,20 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
     decode(it, i, j, ta, tb);
     const int64_t sij = L.boff[BS] + ((int64_t)i * No + j) * L.SL, sji = L.boff[BS] + ((int64_t)j * No + i) * L.SL;
     const float *Zji = c.x + L.boff[BZ] + ((int64_t)j * No + i) * L.SL, *OZj = c.OZ + (int64_t)j * L.SL;
+    const float *rij = AV ? c.rho + (int64_t)(slice0(L, BS) + i * No + j) * Nv : nullptr;
+    const float *rji = AV ? c.rho + (int64_t)(slice0(L, BS) + j * No + i) * Nv : nullptr;
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int r = ty + 8 * rr, a = ta * kT + r, b = tb * kT + tx, a2 = tb * kT + r, b2 = ta * kT + tx;
       const bool in1 = a < Nv && b < Nv, in2 = a2 < Nv && b2 < Nv;
       const int64_t e2 = (int64_t)a2 * Nvp + b2;
-      pa[rr] = in1 ? __ldg(c.P + sij + (int64_t)a * Nvp + b) : 0.f;
-      pb[rr] = in2 ? __ldg(c.P + sji + e2) : 0.f;
+      if constexpr (AV) {
+        pa[rr] = in1 ? xf_arrow(c.F, c.x + sij, rij, Nvp, a, b) : 0.f;
+        pb[rr] = in2 ? xf_arrow(c.F, c.x + sji, rji, Nvp, a2, b2) : 0.f;
+      } else {
+        pa[rr] = in1 ? __ldg(c.P + sij + (int64_t)a * Nvp + b) : 0.f;
+        pb[rr] = in2 ? __ldg(c.P + sji + e2) : 0.f;
+      }
       zt[rr] = in2 ? __ldg(Zji + e2) : 0.f;
       ot[rr] = (in2 && i == 0) ? __ldg(OZj + e2) : 0.f;
     }
@@ -772,6 +825,7 @@ __global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ float g4(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
+template <bool AV>
 __global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
   const Packed &L = c.pv.L;
   const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, nb4 = Nvp >> 2;
@@ -792,7 +846,27 @@ __global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
       const float *Y0j = c.x + L.boff[BY] + (int64_t)pair_ij(No, 0, j) * L.SL;
       const float *t1p = i0 ? c.OC1 + ((int64_t)BZ * No + j) * L.SL : c.x + L.boff[BZ] + (int64_t)j * L.SL;
       const float *t2p = c.x + L.boff[BZ] + (int64_t)i * No * L.SL;   // Z_i0
-      const float4 xe = ld4(c.x + so + ab), p4 = ld4(c.P + so + ab), fz = ld4(c.FZ + (int64_t)s * L.SL + ab);
+      const float4 xe = ld4(c.x + so + ab);
+      float4 p4, fz;
+      if constexpr (AV) {   // X F and F X of the slice from the arrow form of F_vv
+        const float *xs = c.x + so;
+        const float xa0 = __ldg(xs + (int64_t)a * Nvp), ra = c.rho[(int64_t)(slice0(L, BZ) + s) * Nv + a];
+        const float4 x0b = ld4(xs + b);
+        const float fa = F.v(0, a), da = F.v(a, a);
+        float pv[4], fv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int bq = b + q;
+          const bool in = bq < Nv;
+          pv[q] = !in ? 0.f : bq == 0 ? ra : F.v(bq, bq) * g4(xe, q) + xa0 * F.v(0, bq);
+          fv[q] = !in ? 0.f : a == 0 ? c.kap[(int64_t)s * Nv + bq] : da * g4(xe, q) + fa * g4(x0b, q);
+        }
+        p4 = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        fz = make_float4(fv[0], fv[1], fv[2], fv[3]);
+      } else {
+        p4 = ld4(c.P + so + ab);
+        fz = ld4(c.FZ + (int64_t)s * L.SL + ab);
+      }
       const float4 t1 = ld4(t1p + ab), t2 = ld4(t2p + ab), sa = ld4(Sij + ab), s0 = ld4(Si0 + ab);
       const float4 t0 = ld4(T0j + b), y0 = ld4(Y0j + b);
       const float sija0 = __ldg(Sij + (int64_t)a * Nvp), si0a0 = __ldg(Si0 + (int64_t)a * Nvp);
@@ -893,16 +967,27 @@ esmp2_status packed_setup(esmp2_handle *h) {
     // q's and p's pad columns start (and stay) zero
     cudaMemsetAsync(h->pq, 0, sizeof(float) * (size_t)L.n, h->stream);
     cudaMemsetAsync(h->pp, 0, sizeof(float) * (size_t)L.n, h->stream);
-    PV pv{L};
-    FF F{h->F32, N, No};
-    kp_dinv<<<2432, 128, 0, h->stream>>>(pv, F, (float)h->omega_op, h->pdinv);
-    h->launches += 1;
     h->packed = true;
     if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(h, e, "packed set-up");
   }
   const Packed &L = h->pk;
+  // the preconditioner of the basis of this call (semicanonical-occupied or reduced-cost)
+  const int basis = h->arrowv ? 2 : 1;
+  if (h->pdinv_basis != basis) {
+    FF F{h->arrowv ? h->F32arr : h->F32, h->d.N, L.No};
+    kp_dinv<<<2432, 128, 0, h->stream>>>(PV{L}, F, (float)h->omega_op, h->pdinv);
+    h->launches += 1;
+    h->pdinv_basis = basis;
+  }
+  if (h->arrowv && !h->pRho) {
+    A(reinterpret_cast<void **>(&h->pRho), sizeof(float) * (size_t)L.nslices * L.Nv);
+    A(reinterpret_cast<void **>(&h->pKap), sizeof(float) * (size_t)L.NN * L.Nv);
+    if (e != cudaSuccess) return check_cuda(h, e, "packed reduced-basis sums");
+  }
   const size_t op_elems = (size_t)(L.n + (int64_t)L.NN * L.SL);
-  if (h->tf32 && !h->pop32) {
+  if (h->arrowv) {
+    // no contraction operand in the reduced-cost basis
+  } else if (h->tf32 && !h->pop32) {
     A(reinterpret_cast<void **>(&h->pop32), sizeof(float) * op_elems);
     A(reinterpret_cast<void **>(&h->pW32), sizeof(float) * (size_t)L.Nv * L.Nvp);
     if (e != cudaSuccess) return check_cuda(h, e, "packed tf32 operand");
@@ -920,7 +1005,7 @@ esmp2_status packed_setup(esmp2_handle *h) {
 }
 
 // the inner PCG's p: the float32 operand itself for tf32, else its own vector
-float *packed_p(esmp2_handle *h) { return h->tf32 ? h->pop32 : h->pp; }
+float *packed_p(esmp2_handle *h) { return h->tf32 && !h->arrowv ? h->pop32 : h->pp; }
 
 esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
                    float *PT, int ldp, double alg_flops, bool tf32);
@@ -934,9 +1019,15 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
   const int No = L.No, N = h->d.N;
   PV pv{L};
   cudaStream_t st = h->stream;
-  const bool tf32 = h->tf32;
+  const bool av = h->arrowv, tf32 = h->tf32 && !av;
+  FF F{av ? h->F32arr : h->F32, N, No};
   __nv_bfloat16 *op = static_cast<__nv_bfloat16 *>(h->pop);
-  if (!pb_ready && (stages & 1)) {  // the packed p to the operand (pad columns are zero in p)
+  if (av) {   // reduced-cost basis: the virtual-index terms need only row / column sums
+    if (stages & 2) {
+      kp_vsum<<<1216, 256, 0, st>>>(pv, F, p, h->pRho, h->pKap);
+      h->launches += 1;
+    }
+  } else if (!pb_ready && (stages & 1)) {  // the packed p to the operand (pad columns are zero in p)
     if (tf32) {
       if (p != h->pop32) {
         if (cudaError_t e = cudaMemcpyAsync(h->pop32, p, sizeof(float) * (size_t)L.n, cudaMemcpyDeviceToDevice, st))
@@ -948,7 +1039,7 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
     }
   }
   const int64_t rows_n = (int64_t)L.nslices * L.Nv, rows = rows_n + (int64_t)L.NN * L.Nv;
-  if (stages & 2) {
+  if (!av && (stages & 2)) {
     if (tf32) kp_zt32<<<1216, 256, 0, st>>>(pv, h->pop32);
     else kp_zt<<<1216, 256, 0, st>>>(pv, op);
     h->launches += 1;
@@ -968,7 +1059,6 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
     kp_arrow_full<BS><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
     kp_arrow_full<BZ><<<ga, 128, 0, st>>>(pv, p, h->pOC, h->pOC2, h->pOZ, w);
   }
-  FF F{h->F32, N, No};
   kp_inter_a<<<1216, 256, 0, st>>>(pv, F, p, h->pGP, h->pVX);
   kp_inter_c<<<1216, 256, 0, st>>>(pv, F, p, h->pWZ, h->pHP);
   kp_inter_d<<<(unsigned)cdiv(3LL * No * L.Nv, 256), 256, 0, st>>>(pv, F, p, h->pGP, h->pHP, h->pG, h->pH, h->pCYZ);
@@ -984,20 +1074,27 @@ esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_rea
   c.WZ = h->pWZ;
   c.OC1 = h->pOC; c.OC2 = h->pOC2; c.OX = h->pOX; c.OZ = h->pOZ;
   c.G = h->pG; c.H = h->pH; c.CYZ = h->pCYZ;
+  c.rho = h->pRho;
+  c.kap = h->pKap;
   c.dot = dot;
   {
     KScope ks(st, ESMP2_KT_COUPLING, 12.0 * (double)L.n + 4.0 * (double)(L.n + (int64_t)L.NN * L.SL),
               12.0 * (double)L.n);
-    c.dot_base = 0;
-    kp_couple_anti<BT><<<kCoupleGrid, kThreads, 0, st>>>(c);
-    c.dot_base = kCoupleGrid;
-    kp_couple_anti<BX><<<kCoupleGrid, kThreads, 0, st>>>(c);
-    c.dot_base = 2 * kCoupleGrid;
-    kp_couple_anti<BY><<<kCoupleGrid, kThreads, 0, st>>>(c);
-    c.dot_base = 3 * kCoupleGrid;
-    kp_couple_s<<<kCoupleGrid, kThreads, 0, st>>>(c);
-    c.dot_base = 4 * kCoupleGrid;
-    kp_couple_z<<<kCoupleGrid, kThreads, 0, st>>>(c);
+    auto run = [&](auto av_tag) {
+      constexpr bool AV = decltype(av_tag)::value;
+      c.dot_base = 0;
+      kp_couple_anti<BT, AV><<<kCoupleGrid, kThreads, 0, st>>>(c);
+      c.dot_base = kCoupleGrid;
+      kp_couple_anti<BX, AV><<<kCoupleGrid, kThreads, 0, st>>>(c);
+      c.dot_base = 2 * kCoupleGrid;
+      kp_couple_anti<BY, AV><<<kCoupleGrid, kThreads, 0, st>>>(c);
+      c.dot_base = 3 * kCoupleGrid;
+      kp_couple_s<AV><<<kCoupleGrid, kThreads, 0, st>>>(c);
+      c.dot_base = 4 * kCoupleGrid;
+      kp_couple_z<AV><<<kCoupleGrid, kThreads, 0, st>>>(c);
+    };
+    if (av) run(std::true_type{});
+    else run(std::false_type{});
   }
   h->launches += 12;
   return check_cuda(h, cudaGetLastError(), "sigma_packed");
@@ -1074,12 +1171,18 @@ esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *
 esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y) {
   double *t1 = h->s64.w ? h->s64.w : h->s64.p;
   rotate_occ(h, x, y, t1, true);                 // y: x in the working basis
+  if (h->arrowv) {
+    if (esmp2_status s = ensure_arrow(h)) return s;
+    if (esmp2_status s = rotate_virt(h, y, y, t1, true)) return s;
+  }
   float *p = packed_p(h);
   kp_from64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, y, p);
   h->launches += 1;
   if (esmp2_status s = sigma_packed(h, p, h->pq, false, nullptr, 7)) return s;
   kp_to64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, h->pq, y);
   h->launches += 1;
+  if (h->arrowv)
+    if (esmp2_status s = rotate_virt(h, y, y, t1, false)) return s;
   rotate_occ(h, y, y, t1, false);
   // the rotation back mixes slices: the non-amplitude slots (i == j of T, X, Y, ...) carry
   // rounding-level values, cleared here

@@ -131,7 +131,20 @@ struct esmp2_handle {
   double *Rocc = nullptr, *Rocct = nullptr;  // No x No rotation and its transpose
   double *Fsemi = nullptr;  // N x N
   double *bsemi = nullptr;  // right-hand side in that basis (n)
-  int x_semi = 0;           // 1: s64.x is stored in that basis
+  int x_basis = 0;          // basis of s64.x: 0 TOP, 1 semicanonical-occupied, 2 reduced-cost
+  // reduced-cost basis (occupied orbitals other than t and virtual orbitals other than t'
+  // diagonalise their blocks; F is "arrow" shaped in both): ESMP2_REDUCED_MIXED
+  bool arrow_ready = false;
+  bool arrowv = false;      // the current call works in the reduced-cost basis
+  double *Rv = nullptr, *Rvt = nullptr;  // Nv x Nv virtual rotation (t' fixed) and its transpose
+  void *Rvdig = nullptr, *Rvtdig = nullptr;  // their digit planes (float64-exact rotations)
+  int eRv = 0, eRvt = 0;
+  double *Farr = nullptr;   // N x N Fock matrix in that basis
+  double *barr = nullptr;   // right-hand side in that basis (n)
+  float *F32arr = nullptr;  // float copy of Farr (inner solve)
+  double *rho64 = nullptr, *kap64 = nullptr;  // [5 No^2][Nv] row / column sums against F_t'c
+  float *pRho = nullptr, *pKap = nullptr;     // packed inner: [slices][Nv] row sums, [No^2][Nv] Z column sums
+  int pdinv_basis = -1;     // basis the packed preconditioner was built for
   bool x_zero = true;       // s64.x is known to be zero (its sigma is zero, no build needed)
   bool r_true = false;      // s64.r holds the true residual -b - A x of s64.x (same basis)
   // float64-accurate virtual-index terms from exact bf16 digit products (tcgen05)
@@ -155,7 +168,7 @@ struct esmp2_handle {
   // ESMP2_MIXED_TF32: the operand is float32 read as tf32 by the tensor cores, and the inner
   // PCG's p lives in its first n elements (no separate operand copy)
   bool tf32 = false;        // inner operand kind of the current call
-  bool graph_tf32 = false;  // operand kind the captured inner iteration was built with
+  int graph_kind = -1;      // inner sigma kind (tf32 + 2 reduced basis) the captured iteration was built with
   float *pop32 = nullptr;   // float32 operand: packed p, then the transposed Z slices
   float *pW32 = nullptr;    // float32 right operand F_vv
   float *pP = nullptr;      // products: P (T .. Z slices, row pitch Nvp) then F Z (transposed part)
@@ -176,6 +189,8 @@ esmp2_status sigma64(esmp2_handle *h, const double *x, double *y, int tc_levels 
 esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels = 0,
                        int couplings = 1);
 void couple_f32_into(esmp2_handle *h, const double *x, double *y);
+void launch_intermediates64(esmp2_handle *h, const double *F, int arrow, const double *x);
+void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
 esmp2_status sigma64_tail(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
 esmp2_status virtual_contraction(esmp2_handle *h, const double *x, double *y, int mode);
 void contractions64(esmp2_handle *h, const double *F, const double *x, double *y, int stage);
@@ -186,7 +201,8 @@ esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels = 0);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc = 0);
-esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32 = false);
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32 = false,
+                         bool arrowv = false);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);
 esmp2_status gradient(esmp2_handle *h, double *dF, double *dOVOV, int adjoint, double *adj_diff);
 esmp2_status check_cuda(esmp2_handle *h, cudaError_t e, const char *what);
@@ -212,6 +228,14 @@ esmp2_status ensure_split(esmp2_handle *h);
 esmp2_status ensure_slist(esmp2_handle *h);
 esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64, int sym, int levels);
 esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y);
+esmp2_status xwm_split(esmp2_handle *h, const double *X, int64_t rows, double *Y, const double *M, void **dig,
+                       int *eM, int eslot);
+// reduced-cost basis (arrowv.cu)
+esmp2_status ensure_arrow(esmp2_handle *h);
+esmp2_status rotate_virt(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_arrow);
+esmp2_status x_to_basis(esmp2_handle *h, int target);
+esmp2_status sigma64_arrow(esmp2_handle *h, const double *x, double *y, int couplings = 1);
+void virt_arrow64(esmp2_handle *h, const double *x, double *y);
 void rotate_occ(esmp2_handle *h, const double *in, double *out, double *tmp, bool to_semi);
 void mode_product_small(const double *in, double *out, int64_t P, int K, int64_t Q, const double *R,
                         cudaStream_t st);

@@ -645,9 +645,9 @@ double dot_w(esmp2_handle *h, const double *u, const double *v) {
 
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc) {
   auto t0 = std::chrono::steady_clock::now();
-  if (h->x_semi) {  // the plain fp64 solve works in the TOP basis
-    if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, false);
-    h->x_semi = 0;
+  {  // the plain fp64 solve works in the TOP basis
+    esmp2_status s0 = x_to_basis(h, 0);
+    if (s0) return s0;
   }
   const VCtx c = vctx(h);
   double *x = h->s64.x, *r = h->s64.r, *p = h->s64.p, *q = h->s64.q;
@@ -722,8 +722,9 @@ esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *i
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   if (!h->solved) { h->err = "esmp2_energy needs a previous esmp2_solve"; return ESMP2_ERR_STATE; }
   cudaStream_t st = h->stream;
-  const double *F = h->x_semi ? h->Fsemi : h->F;
-  const double *bb = h->x_semi ? h->bsemi : h->b;
+  const int basis = h->x_basis;
+  const double *F = basis == 2 ? h->Farr : basis == 1 ? h->Fsemi : h->F;
+  const double *bb = basis == 2 ? h->barr : basis == 1 ? h->bsemi : h->b;
   esmp2_status s = ESMP2_OK;
   if (h->r_true) {
     // the solve ended on a true residual r = -b - A x of this x: A x = -b - r, no sigma build
@@ -731,7 +732,9 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   } else {
     // after a tensor-core solve the Hylleraas sigma uses the float64-exact digit levels
     const int lv = (h->last_precision != ESMP2_FP64 && split_supported(h, kFp64TcLevels)) ? kFp64TcLevels : 0;
-    if ((s = sigma64_F(h, F, h->x_semi, h->s64.x, h->s64.q, lv))) return s;
+    if (basis == 2) s = sigma64_arrow(h, h->s64.x, h->s64.q);
+    else s = sigma64_F(h, F, basis, h->s64.x, h->s64.q, lv);
+    if (s) return s;
     k_hylleraas<<<kRedBlocks, kRedThreads, 0, st>>>(vctx(h, F), bb, h->s64.x, h->s64.q, 0, h->red);
   }
   k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 10, h->red_out, 3);
@@ -786,27 +789,27 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
 //           contraction (fp32 accumulation); x += d.
 // Everything runs in the basis whose occupied orbitals other than t diagonalise F_oo
 // (the solution is rotated back to the TOP basis on request).
-esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32) {
+esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32, bool arrowv) {
   auto t0 = std::chrono::steady_clock::now();
   debug_phase(h, "solve: start");
-  if (tf32 && h->d.No > 32) {
-    h->err = "ESMP2_MIXED_TF32 needs the packed inner solve (No <= 32)";
+  if ((tf32 || arrowv) && h->d.No > 32) {
+    h->err = "ESMP2_MIXED_TF32 and ESMP2_REDUCED_MIXED need the packed inner solve (No <= 32)";
     return ESMP2_ERR_UNSUPPORTED;
   }
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
+  if (arrowv && (s = ensure_arrow(h))) return s;
   h->tf32 = tf32;
-  debug_phase(h, "solve: semicanonical set-up");
-  if (!h->x_semi) {
-    if (!h->x_zero) rotate_occ(h, h->s64.x, h->s64.x, h->s64.p, true);  // zero in every basis
-    h->x_semi = 1;
-  }
+  h->arrowv = arrowv;
+  debug_phase(h, "solve: basis set-up");
+  if ((s = x_to_basis(h, arrowv ? 2 : 1))) return s;
   cudaStream_t st = h->stream;
   // the singlet solution lies in the symmetric subspace (antisymmetric T, X, Y; S_ij^ab =
   // S_ji^ba); the packed inner solve acts on that subspace only, so x and every residual
   // handed to it are projected onto it (removing the rounding-level components outside)
   singlet_project(h, h->s64.x);
-  const VCtx c = vctx(h, h->Fsemi);
+  const VCtx c = vctx(h, arrowv ? h->Farr : h->Fsemi);
+  const double *bsel = arrowv ? h->barr : h->bsemi;
   debug_phase(h, "solve: x rotation + projection");
   // inner vectors: the packed layout (T, X, Y slices i < j, rows padded; the contraction as one
   // tensor-core GEMM) when the arrow sums fit their register tiles (No <= 32), else full storage
@@ -841,7 +844,8 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   debug_phase(h, "solve: preconditioner");
   // small instances are launch-bound: replay the inner iteration as a CUDA graph
   bool use_graph = h->d.n <= (64LL << 20) && st != nullptr;
-  if (h->inner_graph && (!use_graph || h->graph_tf32 != tf32)) {
+  const int graph_kind = (tf32 ? 1 : 0) + (arrowv ? 2 : 0);
+  if (h->inner_graph && (!use_graph || h->graph_kind != graph_kind)) {
     cudaGraphExecDestroy(h->inner_graph);
     h->inner_graph = nullptr;
   }
@@ -855,8 +859,9 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // inner residual to ~1e-3 relative)
   // the float64 true residual takes its virtual-index terms from exact digit products on
   // the tensor cores when that is exact for this Nv, else from float64 GEMMs
-  const int lv = split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
-  h->last_precision = tf32 ? ESMP2_MIXED_TF32 : ESMP2_MIXED_BF16;
+  // (the reduced-cost basis forms its float64 virtual-index terms element-wise: no digit levels)
+  const int lv = !arrowv && split_supported(h, split_levels_for(tol)) ? split_levels_for(tol) : 0;
+  h->last_precision = arrowv ? ESMP2_REDUCED_MIXED : tf32 ? ESMP2_MIXED_TF32 : ESMP2_MIXED_BF16;
   h->r_true = false;
   const double eta = 1e-2;
   // An intermediate true residual only has to be accurate relative to itself: its digit
@@ -870,17 +875,21 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     int lv_k = lv;
     if (lv && rho_next > 1e1 * tol) lv_k = std::min(lv, split_levels_for(rho_next));
     const bool cold = outer == 0 && h->x_zero;  // cold start: the first true residual is -b
+    bool approx = false;   // formed with reduced accuracy (relative to itself only)
     if (cold) {
       lv_k = lv;
     } else {
       // far from the tolerance the coupling pass runs in float32 (its ~1e-7 relative error
       // is a small fraction of the residual it feeds), next to reduced digit levels
-      const bool c32 = lv_k < lv && rho_next >= 1e-5;
-      if ((s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k, c32 ? 0 : 1))) return s;
+      const bool c32 = (arrowv || lv_k < lv) && rho_next >= 1e-5;
+      if (arrowv) s = sigma64_arrow(h, x, q, c32 ? 0 : 1);
+      else s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k, c32 ? 0 : 1);
+      if (s) return s;
       if (c32) couple_f32_into(h, x, q);
+      approx = c32 || lv_k < lv;
       ++nsig64;
     }
-    k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->bsemi, cold ? nullptr : q, r, h->red, bb < 0.0 ? 1 : 0);
+    k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(c, bsel, cold ? nullptr : q, r, h->red, bb < 0.0 ? 1 : 0);
     k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 3);
     h->launches += 2;
     if ((s = read_slots(h, sl, 32))) return s;
@@ -889,7 +898,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     relres = bn > 0 ? rn / bn : 0.0;
     if (std::getenv("ESMP2_DEBUG"))
       std::fprintf(stderr, "esmp2 refine: outer %d relres %.3e inner_total %d levels %d\n", outer, relres, inner_total, lv_k);
-    if (relres <= 1e1 * tol && lv_k < lv) { rho_next = 0.0; continue; }  // confirm with every level
+    if (relres <= 1e1 * tol && approx) { rho_next = 0.0; continue; }  // confirm at full accuracy
     if (relres <= tol) { result = ESMP2_OK; h->r_true = true; break; }
     if (inner_total >= maxit) break;
     // three refinement steps in a row without reducing the true residual: stop
@@ -950,7 +959,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
         h->launches = l0;
         if (ok) {
           h->inner_graph_launches = h->inner_graph_launches_pending;
-          h->graph_tf32 = tf32;
+          h->graph_kind = graph_kind;
           if ((s = check_cuda(h, cudaGraphLaunch(h->inner_graph, st), "inner graph"))) return s;
           h->launches += h->inner_graph_launches;
         } else {

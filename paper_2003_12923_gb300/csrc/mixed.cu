@@ -272,7 +272,9 @@ esmp2_status sigma_inner(esmp2_handle *h, const float *p, float *q, bool p_bf16_
 esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y) {
   esmp2_status s = ESMP2_OK;
   if (h->d.No <= 32) {  // the inner solve's packed path (singlet vectors), checked through the same call
-    if ((s = ensure_mixed(h, true)) || (s = packed_setup(h)) || (s = sigma_mixed_packed(h, x, y))) return s;
+    if ((s = ensure_mixed(h, true)) || (h->arrowv && (s = ensure_arrow(h))) || (s = packed_setup(h)) ||
+        (s = sigma_mixed_packed(h, x, y)))
+      return s;
     return check_device_flag(h);
   }
   if ((s = ensure_mixed(h, false))) return s;
@@ -315,7 +317,7 @@ esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
   if (h->d.No <= 32) {
-    if ((s = packed_setup(h)) || (s = profile_packed(h, x, reps, ms))) return s;
+    if ((h->arrowv && (s = ensure_arrow(h))) || (s = packed_setup(h)) || (s = profile_packed(h, x, reps, ms))) return s;
     return check_device_flag(h);
   }
   const int No = h->d.No, Nv = h->d.Nv;

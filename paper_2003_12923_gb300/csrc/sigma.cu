@@ -822,7 +822,7 @@ void couple_f32_into(esmp2_handle *h, const double *x, double *y) {
   const int64_t n = h->d.n;
   k_round_f32<<<1216, 256, 0, h->stream>>>(x, h->p32, n);
   cudaMemsetAsync(h->q32, 0, sizeof(float) * (size_t)n, h->stream);
-  couple32(h, h->F32, h->p32, h->q32);
+  couple32(h, h->arrowv ? h->F32arr : h->F32, h->p32, h->q32);
   k_add_f32_masked<<<1216, 256, 0, h->stream>>>(h->q32, y, h->d.No, h->d.Nv);
   h->launches += 2;
 }

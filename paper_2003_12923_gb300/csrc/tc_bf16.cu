@@ -713,7 +713,7 @@ esmp2_status ensure_split(esmp2_handle *h) {
   const int S = 5 * No * No, P = kSplitMaxLevels - 1;
   cudaError_t e = dmalloc(&h->xdig, sizeof(__nv_bfloat16) * (size_t)P * S * Nv * Nvp, h->stream);
   if (e == cudaSuccess) e = dmalloc(&h->Fdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp, h->stream);
-  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&h->es), sizeof(int) * (size_t)(S + 2), h->stream);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&h->es), sizeof(int) * (size_t)(S + 4), h->stream);
   if (e != cudaSuccess) {
     dfree(h->xdig, h->stream); dfree(h->Fdig, h->stream); dfree(h->es, h->stream);
     h->xdig = h->Fdig = nullptr; h->es = nullptr;
@@ -785,27 +785,30 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
   return check_cuda(h, cudaGetLastError(), "virt_split");
 }
 
-// Y = X W_v (rows x Nv times Nv x Nv, rows a multiple of Nv) in float64 accuracy from exact
-// digit products on the tensor cores (ten levels), the right-factor form of the orbital
-// rotations of the integral transforms.  X is read as rows/Nv slices of Nv x Nv.
-esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y) {
+// Y = X M (rows x Nv times an Nv x Nv matrix M, rows a multiple of Nv) in float64 accuracy from
+// exact digit products on the tensor cores (ten levels): the right-factor form of the orbital
+// rotations (M = W_v for the integral transforms, the virtual rotation of the reduced-cost
+// basis).  X is read as rows/Nv slices of Nv x Nv.  The digit planes of M^T (row b' holds column
+// b' of M, the K-major right operand) are built on first use into *dig with the power-of-two
+// scale in es[eslot] (device) and *eM (host).
+esmp2_status xwm_split(esmp2_handle *h, const double *X, int64_t rows, double *Y, const double *M, void **dig,
+                       int *eM, int eslot) {
   esmp2_status s = ensure_split(h);
   if (s) return s;
   const int No = h->d.No, Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
   const int S = (int)(rows / Nv), P = kSplitMaxLevels - 1, levels = kSplitMaxLevels;
   if (rows % Nv != 0 || S > 5 * No * No || (int64_t)(levels - 1) * Nv * 1024 >= (1LL << 24)) {
-    h->err = "xwv_split: unsupported shape";
+    h->err = "xwm_split: unsupported shape";
     return ESMP2_ERR_UNSUPPORTED;
   }
   const int64_t NvNv = (int64_t)Nv * Nv;
-  if (!h->Rdig) {  // digits of W_v^T: row b' holds column b' of W_v (the K-major right operand)
-    cudaError_t e = dmalloc(&h->Rdig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp, h->stream);
+  if (!*dig) {
+    cudaError_t e = dmalloc(dig, sizeof(__nv_bfloat16) * (size_t)P * Nv * Nvp, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "rotation digits");
-    int *eR = h->es + 5 * No * No + 1;
-    tc::k_slice_exp<<<1, 256, 0, h->stream>>>(h->Wv, Nv, Nv, 1, 0, eR, Nv);
-    tc::k_digits<<<256, 256, 0, h->stream>>>(h->Wv, 1, Nv, Nv, Nvp, 1, 0, eR, P,
-                                             static_cast<__nv_bfloat16 *>(h->Rdig), Nv);
-    e = cudaMemcpyAsync(&h->eR, eR, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    int *ed = h->es + 5 * No * No + eslot;
+    tc::k_slice_exp<<<1, 256, 0, h->stream>>>(M, Nv, Nv, 1, 0, ed, Nv);
+    tc::k_digits<<<256, 256, 0, h->stream>>>(M, 1, Nv, Nv, Nvp, 1, 0, ed, P, static_cast<__nv_bfloat16 *>(*dig), Nv);
+    e = cudaMemcpyAsync(eM, ed, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     h->launches += 2;
     if (e != cudaSuccess) return check_cuda(h, e, "rotation digits");
@@ -829,17 +832,21 @@ esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y
     g.y64 = nullptr;
     g.p64 = Y;
     g.es = h->es;
-    g.eF = h->eR;
+    g.eF = *eM;
     g.first = 1;
     g.err = h->dflag;
     const double fl = 2.0 * (double)rows * Nv * Nv;   // one float64-accurate rotation
-    if (const char *m = launch_virt(h->stream, h->xdig, P, h->Rdig, P, g, fl, g.npairs * fl, ESMP2_KT_DIGITS)) {
+    if (const char *m = launch_virt(h->stream, h->xdig, P, *dig, P, g, fl, g.npairs * fl, ESMP2_KT_DIGITS)) {
       h->err = m;
       return ESMP2_ERR_CUDA;
     }
     h->launches += 1;
   }
-  return check_cuda(h, cudaGetLastError(), "xwv_split");
+  return check_cuda(h, cudaGetLastError(), "xwm_split");
+}
+
+esmp2_status xwv_split(esmp2_handle *h, const double *X, int64_t rows, double *Y) {
+  return xwm_split(h, X, rows, Y, h->Wv, &h->Rdig, &h->eR, 1);
 }
 
 void to_bf16_f64(esmp2_handle *h, const double *src, void *dst, int64_t rows) {

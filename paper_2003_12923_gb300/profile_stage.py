@@ -14,6 +14,7 @@ Stages:
     sigma-mixed   sigma with bf16 virtual-index terms, float64 elsewhere
     sigma-inner   the inner (float32 vector) sigma of the mixed solve, per-stage timed
     solve-mixed   a mixed-precision solve to --tol (create excluded)
+  (--inner bf16 | tf32 | reduced picks the inner sigma of the last two)
 """
 from __future__ import annotations
 
@@ -36,6 +37,8 @@ def main(argv=None):
                              "sigma-inner", "solve-mixed"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner", default="bf16", choices=["bf16", "tf32", "reduced"],
+                    help="sigma-inner / solve-mixed: bf16 or tf32 contraction, or the reduced-cost basis")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,11 +51,12 @@ def main(argv=None):
     x = h.rhs()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    inner = {"bf16": esmp2.MIXED_BF16, "tf32": esmp2.MIXED_TF32, "reduced": esmp2.REDUCED_MIXED}[args.inner]
     if args.stage == "solve-mixed":
-        info = h.solve(tol=args.tol, maxit=3000, precision=esmp2.MIXED_BF16)
+        info = h.solve(tol=args.tol, maxit=3000, precision=inner)
         print("solve", info)
     elif args.stage == "sigma-inner":
-        ms = h.profile_sigma(x, precision=esmp2.MIXED_BF16, reps=args.reps)
+        ms = h.profile_sigma(x, precision=inner, reps=args.reps)
         print("inner sigma stage ms (to bf16, virtual, -, couplings, total):", [round(float(v), 3) for v in ms[:5]])
     else:
         out = torch.empty_like(x)

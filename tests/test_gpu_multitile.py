@@ -52,7 +52,8 @@ def test_energy_multitile_against_stored_oracle(task):
     i = g["instance"]
     inst = synth.make_instance(i["No"], i["Nv"], i["seed"], sigma_off=i["sigma_off"])
     for prec, tol, etol in ((esmp2.FP64, 1e-11, 1e-10), (esmp2.FP64_TC, 1e-11, 1e-10),
-                            (esmp2.MIXED_BF16, 1e-8, 1e-8), (esmp2.MIXED_TF32, 1e-8, 1e-8)):
+                            (esmp2.MIXED_BF16, 1e-8, 1e-8), (esmp2.MIXED_TF32, 1e-8, 1e-8),
+                            (esmp2.REDUCED_MIXED, 1e-8, 1e-8)):
         h = handle_for(inst)
         h.solve(tol=tol, maxit=3000, precision=prec)
         e = h.energy()
