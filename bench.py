@@ -254,6 +254,46 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None, tol=1e-8, co
             "t_sigma_s": t_sigma, "n_sigma": n_sigma, "wall_s": time.time() - t0}
 
 
+def indefinite_line(args, esmp2, dins, names, No, Nv, seed, so, tol, prec_name, message, steps=24):
+    """The JSON line of a workload whose operator is not positive definite: no time-to-solution,
+    the solver's message, and the extreme Ritz values of `steps` Lanczos steps on the operator
+    (the library's float64 sigma, started from the right-hand side)."""
+    import torch
+    h = esmp2.Handle(*(dins[k] for k in names))
+    # A is symmetric in the determinant inner product (block weights of the layout)
+    wt = torch.tensor(h.weights, dtype=torch.float64, device=dins["F"].device).view(5, 1, 1, 1, 1)
+    wnorm = lambda v: float((wt * v * v).sum()) ** 0.5
+    b = h.rhs()
+    q = b / wnorm(b)
+    q_prev = torch.zeros_like(q)
+    alphas, betas, beta = [], [], 0.0
+    for _ in range(steps):
+        w = h.sigma(q, esmp2.FP64)
+        a = float((wt * w * q).sum())
+        w = w - a * q - beta * q_prev
+        alphas.append(a)
+        beta = wnorm(w)
+        if beta < 1e-14:
+            break
+        betas.append(beta)
+        q_prev, q = q, w / beta
+    h.close()
+    k = len(alphas)
+    T = np.diag(alphas)
+    if k > 1:
+        T = T + np.diag(betas[:k - 1], 1) + np.diag(betas[:k - 1], -1)
+    ritz = np.linalg.eigvalsh(T)
+    return {"metric": METRIC, "value": None, "unit": "s", "n_gpus": 1, "steps": 0, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f64" if prec_name != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1)", "tol": tol,
+                       "precision": prec_name},
+            "status": "indefinite", "message": message,
+            "lanczos": {"steps": k, "ritz_min": float(ritz[0]), "ritz_max": float(ritz[-1]),
+                        "ritz_low": [float(v) for v in ritz[:4]]},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": 0, "clocks": None}
+
+
 def max_over_ranks(value, dist, device):
     """Largest per-rank float over the process group: the whole job's time."""
     import torch
@@ -293,22 +333,40 @@ def run_batch(args):
     solved through esmp2_batch_solve (mixed precision, `--concurrency` workers, one stream
     each) from host inputs, in waves of `--wave` instances (the whole batch's OVVV blocks
     total 230 GB, so inputs are generated wave by wave; generation is not timed).
-    value = instances solved per second of batch_solve wall time.  The float64 comparison
-    times sequential plain-FP64 solves (create + solve + energy, host inputs) on every
-    `--fp64-every`-th instance and scales to the whole batch by No^2 Nv^3."""
+    value = instances solved per second of batch_solve wall time (host inputs: the value is
+    also the end-to-end number).  The float64 comparison times sequential plain-FP64 solves
+    (create + solve + energy, host inputs) on every `--fp64-every`-th instance and scales to
+    the whole batch by No^2 Nv^3; the oracle baseline is extrapolated the same way from
+    sampled O2 sigma elements of four instances."""
     import torch
     import synth
     from paper_2003_12923_gb300 import esmp2
     rank = int(os.environ.get("RANK", "0"))
     shapes = synth.batch_shapes(64)
+    prec = {"mixed": esmp2.MIXED_BF16, "tf32": esmp2.MIXED_TF32, "reduced": esmp2.REDUCED_MIXED,
+            "auto": esmp2.MIXED_BF16}.get(args.precision, esmp2.MIXED_BF16)
     t_batch, t_seq64, w_seq64, w_all = 0.0, 0.0, 0.0, 0.0
-    n_done, worst_res, e2_diffs, iters = 0, 0.0, [], []
+    n_done, worst_res, e2_diffs, iters, launches, h2d = 0, 0.0, [], [], 0, 0
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    # warm-up: one small wave (the first two shapes), untimed
+    warm = [synth.make_instance(No, Nv, sd, sigma_off=1e-3) for (No, Nv, sd) in shapes[:2]]
+    esmp2.batch_solve(warm, tol=args.tol, maxit=args.maxit, precision=prec, concurrency=args.concurrency)
+    del warm
+    esmp2.kernel_timing(True)
+    esmp2.kernel_times()
+    clk = ClockSampler(uuid)
+    clk.start()
     for w0 in range(0, len(shapes), args.wave):
         wave = shapes[w0:w0 + args.wave]
         insts = [synth.make_instance(No, Nv, sd, sigma_off=1e-3) for (No, Nv, sd) in wave]
+        h2d += sum(inst[k].nbytes for inst in insts for k in ("F", "ovov", "ooov", "ovvv", "C"))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, res = esmp2.batch_solve(insts, tol=args.tol, maxit=args.maxit, precision=esmp2.MIXED_BF16,
+        st, res = esmp2.batch_solve(insts, tol=args.tol, maxit=args.maxit, precision=prec,
                                     concurrency=args.concurrency)
         torch.cuda.synchronize()
         t_batch += time.perf_counter() - t0
@@ -320,6 +378,8 @@ def run_batch(args):
             n_done += 1
             worst_res = max(worst_res, r["rel_residual"])
             iters.append(r["iterations"])
+            launches += int(r["kernel_launches"])
+        for (No, Nv, sd), inst, r in zip(wave, insts, res):
             if (w0 + wave.index((No, Nv, sd))) % args.fp64_every == 0:
                 t0 = time.perf_counter()
                 h = esmp2.Handle(*(torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")))
@@ -328,17 +388,51 @@ def run_batch(args):
                 h.close()
                 torch.cuda.synchronize()
                 t_seq64 += time.perf_counter() - t0
-                w_seq64 += w
+                w_seq64 += No * No * float(Nv) ** 3
                 e2_diffs.append(abs(r["E2"] - e64))
         del insts
+    clocks = clk.stop()
+    ktimes = esmp2.kernel_times()
+    esmp2.kernel_timing(False)
     est64 = t_seq64 * (w_all / w_seq64) if w_seq64 > 0 else None
+    peaks, peak_src = load_peaks()
+    fp64_peak = measure_fp64_peak(torch.device("cuda", 0))
+    fams = {k: family_roofline(k, v, peaks, peak_src, fp64_peak, 1) for k, v in ktimes.items()}
+    roofline = None
+    if ktimes:
+        dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
+        roofline = dict(fams[dom])
+        roofline["family"] = dom
+        ent, prof = kernel_traffic(dom)
+        roofline["traffic"] = ent["bytes_per_launch"] if ent else None
+        roofline["traffic_source"] = prof
+        roofline["note"] = "kernel families over the whole batch (fp64 comparison solves included)"
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # O2 on four instances of the batch (sampled sigma elements, extrapolated), scaled to all 64
+        t_cpu, w_cpu, parts = 0.0, 0.0, []
+        for (No, Nv, sd) in shapes[::16]:
+            c1 = cpu_baseline(No, Nv, sd, 1e-3, budget_s=max(2.0, args.ref_budget / 4), tol=args.tol)
+            t_cpu += c1["value"]
+            w_cpu += No * No * float(Nv) ** 3
+            parts.append({"No": No, "Nv": Nv, "seed": sd, "seconds": c1["value"]})
+        t_all = t_cpu * (w_all / w_cpu)
+        cb = {"value": n_done / t_all, "unit": "solves/s", "cores": c1["cores"], "cpu_model": c1["cpu_model"],
+              "kind": "oracle", "extrapolated": True,
+              "sample": ("O2 solves of instances 0, 16, 32, 48 of the batch, each extrapolated from sampled sigma "
+                         "elements, summed and scaled to all 64 by No^2 Nv^3"), "instances": parts}
     line = {"metric": "ESMP2 batched solves/s, 64 uneven instances (No 8-32, Nv 8-14 x No), res<1e-8, mixed",
-            "value": n_done / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "value": n_done / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16+f64", "data": "synthetic",
+            "dtype": "bf16+f64" if prec != esmp2.MIXED_TF32 else "tf32+f64", "data": "synthetic",
             "config": {"workload": "c4: synth.batch_shapes(64) seeds 100-163, sigma_off 1e-3", "tol": args.tol,
-                       "concurrency": args.concurrency, "wave": args.wave,
-                       "step": "esmp2_batch_solve per wave (create from host inputs + solve + energy + destroy)"},
+                       "precision": args.precision, "concurrency": args.concurrency, "wave": args.wave,
+                       "step": "esmp2_batch_solve per wave (create from host inputs + solve + energy + destroy)",
+                       "l2": "no flush: instances are solved once each"},
+            "roofline": roofline, "kernel_families": fams, "cpu_baseline": cb,
+            "e2e": {"value": n_done / t_batch, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(n_done * 8 * 4)},
+            "gpu_launches": launches, "clocks": clocks,
             "instances": n_done, "batch_seconds": t_batch, "worst_rel_residual": worst_res,
             "inner_iterations_total": int(sum(iters)),
             "fp64_sequential": {"seconds_measured": t_seq64, "instances_measured": len(e2_diffs),
@@ -394,7 +488,8 @@ def main():
     ap.add_argument("--wave", type=int, default=2, help="c4: instances generated and solved per batch call")
     ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
     ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tf32", "reduced"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the tf32 and reduced-basis forms")
     ap.add_argument("--tol", type=float, default=None, help="default: the workload's (1e-8 mixed, 1e-10 fp64)")
     ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--ref-budget", type=float, default=12.0)
@@ -430,19 +525,32 @@ def main():
     dins = {k: torch.from_numpy(inst[k]).to(dev) for k in names}
     esmp2.load()
     prec_name = prec0 if args.precision == "auto" else args.precision
-    prec = esmp2.MIXED_BF16 if prec_name == "mixed" else esmp2.FP64
+    prec = {"mixed": esmp2.MIXED_BF16, "tf32": esmp2.MIXED_TF32, "reduced": esmp2.REDUCED_MIXED,
+            "fp64": esmp2.FP64}[prec_name]
     stream = torch.cuda.current_stream()
     fp64_peak = measure_fp64_peak(dev)
 
-    def step(inputs):
+    def step(inputs, precision=prec):
         h = esmp2.Handle(*(inputs[k] for k in names))
-        info = h.solve(tol=tol, maxit=args.maxit, precision=prec)
+        info = h.solve(tol=tol, maxit=args.maxit, precision=precision)
         e = h.energy()
         n_l = h.kernel_launches
         h.close()
         return info, e, n_l
 
-    for _ in range(args.warmup):
+    try:
+        step(dins)
+    except esmp2.Esmp2Error as err:
+        if err.status != esmp2.ERR_INDEFINITE:
+            raise
+        # CG does not apply (Sec. III.A uses CG, which needs a positive definite operator):
+        # report that, with the lowest Ritz values of a short Lanczos run as the evidence
+        if rank == 0:
+            print(json.dumps(indefinite_line(args, esmp2, dins, names, No, Nv, seed, so, tol, prec_name, str(err))))
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    for _ in range(args.warmup - 1):
         step(dins)
     torch.cuda.synchronize()
     if world > 1:
@@ -528,6 +636,24 @@ def main():
         fp64_cmp = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": info64["iterations"],
                     "rel_residual": info64["rel_residual"], "E2": en64["E2"]}
 
+    # the other inner forms on the same instance, each timed once after one untimed run (CUDA
+    # events, create + solve + energy like the step): tf32 contraction, and the reduced-cost basis
+    # (no virtual-index contraction at all; reported beside the tensor-core form, not instead)
+    variants = {}
+    if prec != esmp2.FP64 and No <= 32 and not args.no_variants:
+        for name, pv in (("tf32_form", esmp2.MIXED_TF32), ("reduced_basis_form", esmp2.REDUCED_MIXED)):
+            if pv == prec:
+                continue
+            step(dins, pv)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info_v, e_v, _ = step(dins, pv)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"time_to_solution_s": e0.elapsed_time(e1) / 1e3, "iterations": info_v["iterations"],
+                              "outer": info_v["outer"], "rel_residual": info_v["rel_residual"], "E2": e_v["E2"],
+                              "E2_minus_main": e_v["E2"] - infos[-1][1]["E2"]}
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(No, Nv, seed, so, inst=inst, tol=tol, config=args.config)
@@ -549,6 +675,7 @@ def main():
     if g is not None and seed == g["instance"]["seed"]:
         line["E2_error_vs_oracle"] = {k: e[k] - g[k] for k in ("E2", "E2_D", "E2_L", "E2_S")}
         line["E2_error_vs_oracle"]["oracle"] = GOLDEN[args.config]
+    line.update(variants)
     if fp64_cmp is not None:
         fp64_cmp["E2_mixed_minus_fp64"] = e["E2"] - fp64_cmp["E2"]
         fp64_cmp["speedup_mixed_over_fp64"] = fp64_cmp["time_to_solution_s"] / tts

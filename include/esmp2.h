@@ -254,6 +254,9 @@ int64_t esmp2_kernel_launches(const esmp2_handle *h);
  *                         flops of ONE contraction (4 n_unique Nv, or 2 rows Nv^2 for a
  *                         rotation), however many digit pairs emulate it; exec_units = the
  *                         tensor-core flops of every digit pair
+ *   ESMP2_KT_PRECOND      tcgen05 GEMMs of the inner preconditioner (the two-sided rotation of
+ *                         the residual to and from the basis that diagonalises F_vv); units =
+ *                         executed flops (extra work, not part of the method's count)
  * esmp2_kernel_times synchronises the recorded events, fills out[ESMP2_KT_COUNT] with the
  * totals since the last call and clears them ("launches" counts timed scopes: one coupling
  * pass, one E2_S sector).  Enabling adds two event records per scope. */
@@ -263,7 +266,8 @@ typedef enum {
   ESMP2_KT_GEMM64 = 2,
   ESMP2_KT_E2S = 3,
   ESMP2_KT_DIGITS = 4,
-  ESMP2_KT_COUNT = 5
+  ESMP2_KT_PRECOND = 5,
+  ESMP2_KT_COUNT = 6
 } esmp2_kernel_family;
 typedef struct {
   int64_t launches;

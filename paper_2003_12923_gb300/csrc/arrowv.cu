@@ -222,28 +222,27 @@ __global__ void k_varrow64(const double *x, const double *F, const double *rho, 
 
 }  // namespace
 
-esmp2_status ensure_arrow(esmp2_handle *h) {
-  if (h->arrow_ready) return ESMP2_OK;
+// The virtual rotation R~ = diag(1, V) (V: eigenvectors of F_vv without t') and F in the
+// rotated basis (Farr, float copy F32arr); no vector is rotated here.
+esmp2_status ensure_vrot(esmp2_handle *h) {
+  if (h->Rv) return ESMP2_OK;
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, m = Nv - 1;
   if (Nv > 1024) {
-    h->err = "the reduced-cost basis supports Nv <= 1024";
+    h->err = "the virtual rotation supports Nv <= 1024";
     return ESMP2_ERR_UNSUPPORTED;
   }
-  const size_t n = (size_t)h->d.n, S = (size_t)5 * No * No;
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, st);
   };
-  A(reinterpret_cast<void **>(&h->Rv), sizeof(double) * (size_t)Nv * Nv);
-  A(reinterpret_cast<void **>(&h->Rvt), sizeof(double) * (size_t)Nv * Nv);
-  A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
-  A(reinterpret_cast<void **>(&h->barr), sizeof(double) * n);
-  A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
-  A(reinterpret_cast<void **>(&h->rho64), sizeof(double) * S * Nv);
-  A(reinterpret_cast<void **>(&h->kap64), sizeof(double) * S * Nv);
+  double *Rv = nullptr, *Rvt = nullptr;
+  A(reinterpret_cast<void **>(&Rv), sizeof(double) * (size_t)Nv * Nv);
+  A(reinterpret_cast<void **>(&Rvt), sizeof(double) * (size_t)Nv * Nv);
+  if (!h->Farr) A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
+  if (!h->F32arr) A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
   double *A0 = nullptr, *A1 = nullptr, *V0 = nullptr, *V1 = nullptr, *W3 = nullptr, *T1 = nullptr, *nrm = nullptr;
   const size_t mm = (size_t)std::max(1, m * m);
   A(reinterpret_cast<void **>(&A0), sizeof(double) * mm);
@@ -258,7 +257,8 @@ esmp2_status ensure_arrow(esmp2_handle *h) {
   };
   if (e != cudaSuccess) {
     release();
-    return check_cuda(h, e, "reduced-cost basis buffers");
+    dfree(Rv, st); dfree(Rvt, st);
+    return check_cuda(h, e, "virtual rotation buffers");
   }
   // eigenvectors of F_vv without t'
   if (m >= 1) {
@@ -267,10 +267,11 @@ esmp2_status ensure_arrow(esmp2_handle *h) {
     const int rounds = m + (m & 1) - 1;
     const unsigned grid = (unsigned)std::min<int64_t>(cdiv(2LL * m * m, 512), 304);
     double prev = -1.0;
-    // sweeps until the off-diagonal part is at the rounding level: below 1e-15 of the norm,
-    // or no longer shrinking (after quadratic convergence the rotations only move rounding
-    // noise around)
-    for (int sweep = 0; sweep < 20; ++sweep) {
+    // sweeps until the off-diagonal part is at the rounding level: below 1e-15 of the norm, or
+    // below 1e-12 of it and no longer shrinking (after the quadratic phase the rotations only
+    // move rounding noise around).  In the TOP basis F_vv is far from diagonal (W_v mixes the
+    // virtual orbitals), so the first sweeps reduce it only a few-fold each.
+    for (int sweep = 0; sweep < 40; ++sweep) {
       for (int r = 0; r < rounds; ++r) {
         k_jacobi_round<<<grid, 512, 0, st>>>(A0, A1, V0, V1, m, r);
         std::swap(A0, A1);
@@ -283,15 +284,16 @@ esmp2_status ensure_arrow(esmp2_handle *h) {
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) {
         release();
-        return check_cuda(h, e, "reduced-cost basis (Jacobi)");
+        dfree(Rv, st); dfree(Rvt, st);
+        return check_cuda(h, e, "virtual rotation (Jacobi)");
       }
       if (!(hn[0] > 1e-30 * hn[1])) break;
-      if (sweep >= 2 && hn[0] > 0.25 * prev) break;
+      if (hn[0] < 1e-24 * hn[1] && prev > 0.0 && hn[0] > 0.25 * prev) break;
       prev = hn[0];
     }
-    debug_phase(h, "  reduced basis: Jacobi eigenvectors of the virtual block");
+    debug_phase(h, "  virtual rotation: Jacobi eigenvectors of the virtual block");
   }
-  k_build_rv<<<256, 256, 0, st>>>(V0, No, Nv, h->Rv, h->Rvt, W3);
+  k_build_rv<<<256, 256, 0, st>>>(V0, No, Nv, Rv, Rvt, W3);
   // Farr = W3^T Fsemi W3
   Gemm64 g{};
   g.alpha = 1.0; g.beta = 0.0; g.batch = 1; g.M = N; g.N = N; g.K = N;
@@ -302,11 +304,31 @@ esmp2_status ensure_arrow(esmp2_handle *h) {
   k_clean_arrow<<<256, 256, 0, st>>>(h->Farr, No, Nv);
   k_to_f32<<<64, 256, 0, st>>>(h->Farr, h->F32arr, (int64_t)N * N);
   h->launches += 5;
+  release();
+  h->Rv = Rv;
+  h->Rvt = Rvt;
+  return check_cuda(h, cudaGetLastError(), "virtual rotation");
+}
+
+esmp2_status ensure_arrow(esmp2_handle *h) {
+  if (h->arrow_ready) return ESMP2_OK;
+  esmp2_status s = ensure_vrot(h);
+  if (s) return s;
+  const int No = h->d.No, Nv = h->d.Nv;
+  const size_t n = (size_t)h->d.n, S = (size_t)5 * No * No;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, st);
+  };
+  A(reinterpret_cast<void **>(&h->barr), sizeof(double) * n);
+  A(reinterpret_cast<void **>(&h->rho64), sizeof(double) * S * Nv);
+  A(reinterpret_cast<void **>(&h->kap64), sizeof(double) * S * Nv);
+  if (e != cudaSuccess) return check_cuda(h, e, "reduced-cost basis buffers");
   // the right-hand side in the reduced-cost basis (float64-exact digit-split rotations)
   s = rotate_virt(h, h->bsemi, h->barr, h->s64.w ? h->s64.w : h->s64.p, true);
-  release();
   if (s) return s;
-  debug_phase(h, "  reduced basis: F and rhs rotation");
+  debug_phase(h, "  reduced basis: rhs rotation");
   h->arrow_ready = true;
   return check_cuda(h, cudaGetLastError(), "reduced-cost basis");
 }

@@ -110,12 +110,12 @@ struct PV {
   }
 };
 
-struct FF {  // float Fock matrix of the working basis
+struct FF {  // float Fock matrix of the working basis (read-only in every kernel: cached loads)
   const float *F;
   int N, No;
-  __device__ __forceinline__ float o(int k, int l) const { return F[k * N + l]; }
-  __device__ __forceinline__ float v(int a, int b) const { return F[(No + a) * N + No + b]; }
-  __device__ __forceinline__ float ov(int k, int a) const { return F[k * N + No + a]; }
+  __device__ __forceinline__ float o(int k, int l) const { return __ldg(F + k * N + l); }
+  __device__ __forceinline__ float v(int a, int b) const { return __ldg(F + (No + a) * N + No + b); }
+  __device__ __forceinline__ float ov(int k, int a) const { return __ldg(F + k * N + No + a); }
 };
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
     const float s1 = i0 ? 1.f : F.o(0, i), s2 = F.o(0, j);
     const float *t1p = i0 ? c.OC1 + ((int64_t)BLK * No + j) * L.SL : c.x + L.boff[BLK] + (int64_t)pair_ij(No, 0, j) * L.SL;
     const float *t2p = i0 ? nullptr : c.x + L.boff[BLK] + (int64_t)pair_ij(No, 0, i) * L.SL;   // x_i0 = -x_0i
-    const float f00 = F.ov(0, 0);
+    const float f00 = F.ov(0, 0), fi0 = F.ov(i, 0), fj0 = F.ov(j, 0);
     SV A1{}, A2{}, A3{};
     const float *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;
     if (BLK == BT) {
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
           }
         } else if (BLK == BX) {
           const float foa0 = F.ov(0, a), foai = F.ov(i, a), foaj = F.ov(j, a);
-          u += f00 * A1.at(ab) - foa0 * A1.at(b) + fob0 * A1.at(a) - F.ov(i, 0) * A2.at(ab) + F.ov(j, 0) * A3.at(ab) +
+          u += f00 * A1.at(ab) - foa0 * A1.at(b) + fob0 * A1.at(a) - fi0 * A2.at(ab) + fj0 * A3.at(ab) +
                foai * A2.at(b) - foaj * A3.at(b) - fobi * A2.at(a) + fobj * A3.at(a);
         } else {
           u += f00 * A1.at(ab) + fobj * A2.at(a) - fobi * A3.at(a) - F.ov(j, a) * A2.at(b) + F.ov(i, a) * A3.at(b);
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) kp_couple_anti(CP c) {
 // tiles read transposed (P_ji, Z_ji and, for i = 0, OZ_j) of the next item are loaded into
 // registers while the current one is computed.
 template <bool AV>
-__global__ void __launch_bounds__(kThreads) kp_couple_s(CP c) {
+__global__ void __launch_bounds__(kThreads, 4) kp_couple_s(CP c) {
   const Packed &L = c.pv.L;
   __shared__ float Pa[kT][kT + 1], Pb[kT][kT + 1], Zt[kT][kT + 1], Ot[kT][kT + 1], Ys[kT][kT + 1];
   const int nt = (L.Nv + kT - 1) / kT, No = L.No, Nv = L.Nv, Nvp = L.Nvp;
@@ -826,7 +826,7 @@ __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret
 __device__ __forceinline__ float g4(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
 template <bool AV>
-__global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
+__global__ void __launch_bounds__(kThreads, AV ? 3 : 4) kp_couple_z(CP c) {
   const Packed &L = c.pv.L;
   const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, nb4 = Nvp >> 2;
   const FF &F = c.F;
@@ -892,6 +892,206 @@ __global__ void __launch_bounds__(kThreads) kp_couple_z(CP c) {
   if (c.dot) cta_partial((double)dsum, c.dot, c.dot_base + blockIdx.x);
 }
 
+// ---------------------------------------------------------------- rotated Jacobi preconditioner
+// z = R~ D~^-1 R~^T r R~ R~^T slice by slice: R~ = diag(1, V) rotates the virtual orbitals other
+// than t' to the eigenvectors of F_vv (t' fixed, so the masks keep their positions), D~ is the
+// diagonal of A in that basis (the Jacobi preconditioner of the reduced-cost basis).  D and L
+// do not change under that rotation, so M^-1 A has the spectrum the reduced-cost basis solve
+// sees; the rotations run as bf16 tcgen05 GEMMs (vgemm.cu), the result is projected back onto
+// the singlet subspace with the masks (the rotations' rounding is not symmetric).
+
+__device__ __forceinline__ void st_bf4(__nv_bfloat16 *p4, float4 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t *>(&a);
+  u.y = *reinterpret_cast<uint32_t *>(&b);
+  *reinterpret_cast<uint2 *>(p4) = u;
+}
+
+// start of an inner solve: r = r64 on the packed slots, rb = bf16(r), d = 0; partials <r, r>_w
+__global__ void kp_init_rj(PV pv, const double *r64, float *r, __nv_bfloat16 *rb, float *d, double *red) {
+  const Packed &L = pv.L;
+  const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
+  float a1 = 0.f;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+    int blk, i, j;
+    pv.decode(s, blk, i, j);
+    const double *src = r64 + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
+    const int64_t e0 = (int64_t)s * L.SL + (int64_t)a * L.Nvp;
+    const float w = blk_w(blk);
+    for (int b = threadIdx.x; b < L.Nvp; b += blockDim.x) {
+      const float ri = b < L.Nv ? (float)src[b] : 0.f;
+      r[e0 + b] = ri;
+      rb[e0 + b] = __float2bfloat16_rn(ri);
+      d[e0 + b] = 0.f;
+      a1 += w * ri * ri;
+    }
+  }
+  double v[1] = {(double)a1};
+  cta_partials<1>(v, red);
+}
+
+// r -= alpha q, rb = bf16(r); partials <r, r>_w
+__global__ void kp_update_rj(PV pv, const double *slots, float *r, const float *q, __nv_bfloat16 *rb, double *red) {
+  const Packed &L = pv.L;
+  const float alpha = (float)slots[4];
+  const int64_t n4 = L.n >> 2, z4 = L.boff[BZ] >> 2;
+  float4 *r4 = reinterpret_cast<float4 *>(r);
+  const float4 *q4 = reinterpret_cast<const float4 *>(q);
+  float a1 = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    float4 rv = r4[e];
+    const float4 qv = __ldg(q4 + e);
+    rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+    r4[e] = rv;
+    st_bf4(rb + 4 * e, rv);
+    a1 += (e >= z4 ? 2.f : 1.f) * (rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+  }
+  double v[1] = {(double)a1};
+  cta_partials<1>(v, red);
+}
+
+// d += alpha p; p = z + beta p; pb = bf16(p) (if kept)
+__global__ void kp_p_rj(PV pv, const double *slots, const float *z, float *p, float *d, __nv_bfloat16 *pb) {
+  const Packed &L = pv.L;
+  const float alpha = (float)slots[4], beta = (float)slots[5];
+  const int64_t n4 = L.n >> 2;
+  const float4 *z4 = reinterpret_cast<const float4 *>(z);
+  float4 *p4 = reinterpret_cast<float4 *>(p), *d4 = reinterpret_cast<float4 *>(d);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pv4 = p4[e], zv = __ldg(z4 + e);
+    float4 dv = d4[e];
+    dv.x += alpha * pv4.x; dv.y += alpha * pv4.y; dv.z += alpha * pv4.z; dv.w += alpha * pv4.w;
+    d4[e] = dv;
+    const float4 pn = make_float4(zv.x + beta * pv4.x, zv.y + beta * pv4.y, zv.z + beta * pv4.z, zv.w + beta * pv4.w);
+    p4[e] = pn;
+    if (pb) st_bf4(pb + 4 * e, pn);
+  }
+}
+
+// z projected onto the singlet subspace with the masks, in place; partials of <r, z>_w
+// (r has the symmetries exactly).  T, X, Y: tile pairs, w_ab = (z_ab - z_ba) / 2, w_ba = -w_ab.
+template <int BLK>
+__global__ void __launch_bounds__(kThreads) kp_proj_anti(PV pv, float *z, const float *r, double *red, int64_t base) {
+  const Packed &L = pv.L;
+  __shared__ float Za[kT][kT + 1], Zb[kT][kT + 1], Ws[kT][kT + 1];
+  const int nt = (L.Nv + kT - 1) / kT, npairs = nt * (nt + 1) / 2;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int64_t first, last;
+  cta_items((int64_t)L.nh * npairs, first, last);
+  float dsum = 0.f;
+  for (int64_t it = first; it < last; ++it) {
+    const int k = (int)(it / npairs);
+    int tp = (int)(it % npairs), ta = 0;
+    while (tp >= nt - ta) { tp -= nt - ta; ++ta; }
+    const int tb = ta + tp;
+    int i, j;
+    pair_decode(No, k, i, j);
+    const int64_t so = L.boff[BLK] + (int64_t)k * L.SL;
+    float *zs = z + so;
+    const float *rs = r + so;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int q = ty + 8 * rr, a = ta * kT + q, b = tb * kT + tx, a2 = tb * kT + q, b2 = ta * kT + tx;
+      Za[q][tx] = (a < Nv && b < Nv) ? zs[(int64_t)a * Nvp + b] : 0.f;
+      Zb[q][tx] = (a2 < Nv && b2 < Nv) ? zs[(int64_t)a2 * Nvp + b2] : 0.f;
+    }
+    __syncthreads();
+    const int b = tb * kT + tx;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int q = ty + 8 * rr, a = ta * kT + q;
+      float w = 0.f;
+      if (a < Nv && b < Nv && (ta < tb || q < tx) && valid_elem(BLK, i, j, a, b)) {
+        w = 0.5f * (Za[q][tx] - Zb[tx][q]);
+        dsum += 2.f * w * rs[(int64_t)a * Nvp + b];
+      }
+      if (a < Nv && b < Nv && (ta < tb || q <= tx)) zs[(int64_t)a * Nvp + b] = w;
+      Ws[q][tx] = -w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int q = ty + 8 * rr, a = tb * kT + q, bb = ta * kT + tx;
+      if (a < Nv && bb < Nv && (ta < tb || q > tx)) zs[(int64_t)a * Nvp + bb] = Ws[tx][q];
+    }
+    __syncthreads();
+  }
+  cta_partial((double)dsum, red, base + blockIdx.x);
+}
+
+// S: w = (z_ij^ab + z_ji^ba) / 2 on both images
+__global__ void __launch_bounds__(kThreads) kp_proj_s(PV pv, float *z, const float *r, double *red, int64_t base) {
+  const Packed &L = pv.L;
+  __shared__ float Za[kT][kT + 1], Zb[kT][kT + 1], Ws[kT][kT + 1];
+  const int nt = (L.Nv + kT - 1) / kT, No = L.No, Nv = L.Nv, Nvp = L.Nvp;
+  const int npair = No * (No + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int64_t first, last;
+  cta_items((int64_t)npair * nt * nt, first, last);
+  float dsum = 0.f;
+  for (int64_t it = first; it < last; ++it) {
+    int pi = (int)(it / (nt * nt));
+    const int tt = (int)(it % (nt * nt)), ta = tt / nt, tb = tt % nt;
+    int i = 0;
+    while (pi >= No - i) { pi -= No - i; ++i; }
+    const int j = i + pi;
+    if (i == j && ta > tb) continue;
+    float *zij = z + L.boff[BS] + ((int64_t)i * No + j) * L.SL, *zji = z + L.boff[BS] + ((int64_t)j * No + i) * L.SL;
+    const float *rij = r + L.boff[BS] + ((int64_t)i * No + j) * L.SL;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int q = ty + 8 * rr, a = ta * kT + q, b = tb * kT + tx, a2 = tb * kT + q, b2 = ta * kT + tx;
+      Za[q][tx] = (a < Nv && b < Nv) ? zij[(int64_t)a * Nvp + b] : 0.f;
+      Zb[q][tx] = (a2 < Nv && b2 < Nv) ? zji[(int64_t)a2 * Nvp + b2] : 0.f;
+    }
+    __syncthreads();
+    const bool diag = i == j && ta == tb;
+    const int b = tb * kT + tx;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int q = ty + 8 * rr, a = ta * kT + q;
+      float w = 0.f;
+      if (a < Nv && b < Nv && (!diag || q <= tx)) {
+        w = 0.5f * (Za[q][tx] + Zb[tx][q]);
+        dsum += (diag && q == tx ? 1.f : 2.f) * w * rij[(int64_t)a * Nvp + b];
+        zij[(int64_t)a * Nvp + b] = w;
+      }
+      Ws[q][tx] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {   // z_ji[tb*32 + q][ta*32 + tx] = w_ij[ta*32 + tx][tb*32 + q]
+      const int q = ty + 8 * rr, a = tb * kT + q, bb = ta * kT + tx;
+      if (a < Nv && bb < Nv && (!diag || q > tx)) zji[(int64_t)a * Nvp + bb] = Ws[tx][q];
+    }
+    __syncthreads();
+  }
+  cta_partial((double)dsum, red, base + blockIdx.x);
+}
+
+// Z: masks only (no symmetry between Z slices); weight 2
+__global__ void kp_proj_z(PV pv, float *z, const float *r, double *red, int64_t base) {
+  const Packed &L = pv.L;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp;
+  const int64_t units = (int64_t)L.NN * Nv * Nvp;
+  float *zb = z + L.boff[BZ];
+  const float *rb = r + L.boff[BZ];
+  float dsum = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < units; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / L.SL;
+    const int ab = (int)(e - s * L.SL), a = ab / Nvp, b = ab % Nvp;
+    const int i = (int)(s / No), j = (int)(s % No);
+    float v = zb[e];
+    if (b >= Nv || !valid_elem(BZ, i, j, a, b)) v = 0.f;
+    zb[e] = v;
+    dsum += 2.f * v * rb[e];
+  }
+  cta_partial((double)dsum, red, base + blockIdx.x);
+}
+
 // <u, v>_w over a packed vector (per-CTA partials)
 __global__ void kp_wdot(PV pv, const float *u, const float *v, double *red) {
   const Packed &L = pv.L;
@@ -943,7 +1143,7 @@ esmp2_status packed_setup(esmp2_handle *h) {
   if (!h->pr) {
     const Packed L = make_packed(h->d.No, h->d.Nv);
     h->pk = L;
-    const int No = L.No, N = h->d.N;
+    const int No = L.No;
     A(reinterpret_cast<void **>(&h->pr), sizeof(float) * (size_t)L.n);
     A(reinterpret_cast<void **>(&h->pp), sizeof(float) * (size_t)L.n);
     A(reinterpret_cast<void **>(&h->pq), sizeof(float) * (size_t)L.n);
@@ -1008,7 +1208,7 @@ esmp2_status packed_setup(esmp2_handle *h) {
 float *packed_p(esmp2_handle *h) { return h->tf32 && !h->arrowv ? h->pop32 : h->pp; }
 
 esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
-                   float *PT, int ldp, double alg_flops, bool tf32);
+                   float *PT, int ldp, double alg_flops, bool tf32, const VgemmOut *out = nullptr);
 
 // q = A p on the packed layout (bf16 or tf32 virtual-index terms, float32 everything else);
 // pb_ready: the PCG update already wrote the operand (bf16(p), or p itself in the float32
@@ -1125,6 +1325,140 @@ double packed_wdot(esmp2_handle *h, const float *u, const float *v) {
 void packed_accumulate(esmp2_handle *h, double *x64) {
   kp_acc64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x64, h->pd);
   h->launches += 1;
+}
+
+// Set-up of the rotated Jacobi preconditioner (once per handle): the virtual rotation, its bf16
+// right operands (W[b][c] = M[c][b] for X M: M = R~ gives W = R~^T, M = R~^T gives W = R~), the
+// diagonal of F_vv in the rotated basis and the per-slice occupied part of the diagonal of A.
+esmp2_status packed_rj_setup(esmp2_handle *h) {
+  if (h->rj_ready) return ESMP2_OK;
+  esmp2_status s = ensure_vrot(h);
+  if (s) return s;
+  const Packed &L = h->pk;
+  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, N = h->d.N;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, st);
+  };
+  A(&h->pRbf, sizeof(__nv_bfloat16) * (size_t)L.n);
+  A(&h->pT1, sizeof(__nv_bfloat16) * (size_t)L.n);
+  A(reinterpret_cast<void **>(&h->pZ), sizeof(float) * (size_t)L.n);
+  A(&h->pWR, sizeof(__nv_bfloat16) * (size_t)Nv * Nvp);
+  A(&h->pWRt, sizeof(__nv_bfloat16) * (size_t)Nv * Nvp);
+  A(reinterpret_cast<void **>(&h->pLam), sizeof(float) * (size_t)Nv);
+  A(reinterpret_cast<void **>(&h->pOcc), sizeof(float) * (size_t)L.nslices);
+  A(reinterpret_cast<void **>(&h->pCode), sizeof(int) * (size_t)L.nslices);
+  A(reinterpret_cast<void **>(&h->pdot2), sizeof(double) * 5 * (size_t)kCoupleGrid);
+  A(reinterpret_cast<void **>(&h->zero_slots), sizeof(double) * 32);
+  if (e != cudaSuccess) return check_cuda(h, e, "rotated preconditioner buffers");
+  // pad columns of the GEMM operands and of z start (and stay) zero: the transposed epilogue
+  // writes columns < Nv only, and p = z + beta p must keep zero pads (they are K of the sigma GEMM)
+  cudaMemsetAsync(h->pRbf, 0, sizeof(__nv_bfloat16) * (size_t)L.n, st);
+  cudaMemsetAsync(h->pT1, 0, sizeof(__nv_bfloat16) * (size_t)L.n, st);
+  cudaMemsetAsync(h->pZ, 0, sizeof(float) * (size_t)L.n, st);
+  cudaMemsetAsync(h->zero_slots, 0, sizeof(double) * 32, st);
+  std::vector<double> R((size_t)Nv * Nv);
+  std::vector<float> F((size_t)N * N), Fs((size_t)N * N);
+  e = cudaMemcpyAsync(R.data(), h->Rv, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F.data(), h->F32arr, sizeof(float) * F.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Fs.data(), h->F32, sizeof(float) * Fs.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check_cuda(h, e, "rotated preconditioner set-up");
+  std::vector<__nv_bfloat16> WR((size_t)Nv * Nvp, __float2bfloat16_rn(0.f)), WRt = WR;
+  for (int b = 0; b < Nv; ++b)
+    for (int c = 0; c < Nv; ++c) {
+      WR[(size_t)b * Nvp + c] = __float2bfloat16_rn((float)R[(size_t)b * Nv + c]);
+      WRt[(size_t)b * Nvp + c] = __float2bfloat16_rn((float)R[(size_t)c * Nv + b]);
+    }
+  std::vector<float> lam(Nv), occ(L.nslices);
+  std::vector<int> code(L.nslices);
+  for (int a = 0; a < Nv; ++a) lam[a] = F[(size_t)(No + a) * N + No + a];
+  // the occupied part as kp_dinv forms it, in float: F_ii + F_jj + omega - (L block ? F_t't' - F_tt : 0)
+  const float om = (float)h->omega_op, shift = Fs[(size_t)No * N + No] - Fs[0];
+  for (int sl = 0; sl < L.nslices; ++sl) {
+    int blk, i, j, t = sl;
+    if (t < L.nh) { blk = BT; }
+    else if ((t -= L.nh) < L.NN) { blk = BS; }
+    else if ((t -= L.NN) < L.nh) { blk = BX; }
+    else if ((t -= L.nh) < L.nh) { blk = BY; }
+    else { t -= L.nh; blk = BZ; }
+    if (blk == BS || blk == BZ) { i = t / No; j = t % No; }
+    else pair_decode(No, t, i, j);
+    occ[sl] = Fs[(size_t)i * N + i] + Fs[(size_t)j * N + j] + om - (blk >= BX ? shift : 0.f);
+    code[sl] = blk | (i == 0 ? 8 : 0) | (j == 0 ? 16 : 0);
+  }
+  e = cudaMemcpyAsync(h->pWR, WR.data(), sizeof(__nv_bfloat16) * WR.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pWRt, WRt.data(), sizeof(__nv_bfloat16) * WRt.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pLam, lam.data(), sizeof(float) * lam.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pOcc, occ.data(), sizeof(float) * occ.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pCode, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check_cuda(h, e, "rotated preconditioner set-up");
+  h->rj_ready = true;
+  return ESMP2_OK;
+}
+
+// z = M^-1 r from the bf16 copy pRbf (overwritten), then projected; partials of <r, z>_w in
+// pdot2 (5 kCoupleGrid doubles)
+static esmp2_status packed_precond(esmp2_handle *h) {
+  const Packed &L = h->pk;
+  const int64_t rows = (int64_t)L.nslices * L.Nv;
+  const double fl = 2.0 * (double)rows * L.Nv * L.Nv;
+  VgemmOut o{};
+  o.family = ESMP2_KT_PRECOND;
+  esmp2_status s;
+  o.PT16 = h->pT1;                                                  // (r R~)^T
+  if ((s = vgemm(h, h->pRbf, rows, 0, h->pWRt, nullptr, nullptr, L.Nvp, fl, false, &o))) return s;
+  o.PT16 = h->pRbf; o.lam = h->pLam; o.occ = h->pOcc; o.code = h->pCode;   // D~^-1 (R~^T r R~)
+  if ((s = vgemm(h, h->pT1, rows, 0, h->pWRt, nullptr, nullptr, L.Nvp, fl, false, &o))) return s;
+  o.PT16 = h->pT1; o.lam = nullptr; o.occ = nullptr; o.code = nullptr;    // (z~ R~^T)^T
+  if ((s = vgemm(h, h->pRbf, rows, 0, h->pWR, nullptr, nullptr, L.Nvp, fl, false, &o))) return s;
+  o.PT16 = nullptr;                                                 // R~ z~ R~^T (float32)
+  if ((s = vgemm(h, h->pT1, rows, 0, h->pWR, nullptr, h->pZ, L.Nvp, fl, false, &o))) return s;
+  PV pv{L};
+  cudaStream_t st = h->stream;
+  kp_proj_anti<BT><<<kCoupleGrid, kThreads, 0, st>>>(pv, h->pZ, h->pr, h->pdot2, 0);
+  kp_proj_anti<BX><<<kCoupleGrid, kThreads, 0, st>>>(pv, h->pZ, h->pr, h->pdot2, kCoupleGrid);
+  kp_proj_anti<BY><<<kCoupleGrid, kThreads, 0, st>>>(pv, h->pZ, h->pr, h->pdot2, 2 * kCoupleGrid);
+  kp_proj_s<<<kCoupleGrid, kThreads, 0, st>>>(pv, h->pZ, h->pr, h->pdot2, 3 * kCoupleGrid);
+  kp_proj_z<<<kCoupleGrid, 256, 0, st>>>(pv, h->pZ, h->pr, h->pdot2, 4 * kCoupleGrid);
+  h->launches += 5;
+  return check_cuda(h, cudaGetLastError(), "packed_precond");
+}
+
+// start of a preconditioned inner solve: r (packed) from r64, d = 0, z = M^-1 r, p = z; slots:
+// rr (1) and rz (0)
+esmp2_status packed_rj_init(esmp2_handle *h, const double *r64, int grid) {
+  const Packed &L = h->pk;
+  PV pv{L};
+  cudaStream_t st = h->stream;
+  kp_init_rj<<<grid, 128, 0, st>>>(pv, r64, h->pr, static_cast<__nv_bfloat16 *>(h->pRbf), h->pd, h->red);
+  k_finalize_ext(h->red, grid, h->red_out, 5, st);
+  h->launches += 2;
+  if (esmp2_status s = packed_precond(h)) return s;
+  k_finalize_ext(h->pdot2, 5 * kCoupleGrid, h->red_out, 7, st);
+  kp_p_rj<<<grid, 256, 0, st>>>(pv, h->zero_slots, h->pZ, packed_p(h), h->pd,
+                                h->tf32 ? nullptr : static_cast<__nv_bfloat16 *>(h->pop));
+  h->launches += 2;
+  return check_cuda(h, cudaGetLastError(), "packed_rj_init");
+}
+
+// the part of a preconditioned inner iteration after q = A p and alpha: r -= alpha q, z = M^-1 r,
+// beta, d += alpha p, p = z + beta p
+esmp2_status packed_rj_step(esmp2_handle *h, int grid) {
+  const Packed &L = h->pk;
+  PV pv{L};
+  cudaStream_t st = h->stream;
+  kp_update_rj<<<grid, 256, 0, st>>>(pv, h->red_out, h->pr, h->pq, static_cast<__nv_bfloat16 *>(h->pRbf), h->red);
+  k_finalize_ext(h->red, grid, h->red_out, 5, st);
+  h->launches += 2;
+  if (esmp2_status s = packed_precond(h)) return s;
+  k_finalize_ext(h->pdot2, 5 * kCoupleGrid, h->red_out, 6, st);
+  kp_p_rj<<<grid, 256, 0, st>>>(pv, h->red_out, h->pZ, packed_p(h), h->pd,
+                                h->tf32 ? nullptr : static_cast<__nv_bfloat16 *>(h->pop));
+  h->launches += 2;
+  return check_cuda(h, cudaGetLastError(), "packed_rj_step");
 }
 
 // per-stage timing of `reps` packed inner sigma builds of the packed copy of x (CUDA events):

@@ -145,6 +145,17 @@ struct esmp2_handle {
   double *rho64 = nullptr, *kap64 = nullptr;  // [5 No^2][Nv] row / column sums against F_t'c
   float *pRho = nullptr, *pKap = nullptr;     // packed inner: [slices][Nv] row sums, [No^2][Nv] Z column sums
   int pdinv_basis = -1;     // basis the packed preconditioner was built for
+  // rotated Jacobi preconditioner of the packed bf16 / tf32 inner solve: z = R D^-1 R^T r per
+  // slice, R the virtual rotation that diagonalises F_vv, D the diagonal of A in that basis
+  bool rj = false;          // in use for the current solve
+  bool rj_ready = false;
+  void *pRbf = nullptr, *pT1 = nullptr;  // bf16 r and the intermediate products (packed)
+  float *pZ = nullptr;      // z = M^-1 r (packed)
+  void *pWR = nullptr, *pWRt = nullptr;  // bf16 right operands for X R and X R^T
+  float *pLam = nullptr, *pOcc = nullptr;  // diagonal of F_vv in that basis; per-slice occupied part
+  int *pCode = nullptr;     // per-slice block | 8 (i == 0) | 16 (j == 0)
+  double *pdot2 = nullptr;  // partials of <r, z>_w
+  double *zero_slots = nullptr;  // 32 zero doubles (alpha = beta = 0)
   bool x_zero = true;       // s64.x is known to be zero (its sigma is zero, no build needed)
   bool r_true = false;      // s64.r holds the true residual -b - A x of s64.x (same basis)
   // float64-accurate virtual-index terms from exact bf16 digit products (tcgen05)
@@ -214,6 +225,11 @@ esmp2_status packed_setup(esmp2_handle *h);
 esmp2_status sigma_packed(esmp2_handle *h, const float *p, float *q, bool pb_ready, double *dot, int stages = 7);
 esmp2_status profile_packed(esmp2_handle *h, const double *x, int reps, double *ms);
 void packed_init(esmp2_handle *h, const double *r64, int grid);
+esmp2_status packed_rj_setup(esmp2_handle *h);
+void k_finalize_ext(const double *red, int nparts, double *slots, int mode, cudaStream_t st);
+esmp2_status packed_rj_init(esmp2_handle *h, const double *r64, int grid);
+esmp2_status packed_rj_step(esmp2_handle *h, int grid);
+esmp2_status ensure_vrot(esmp2_handle *h);
 float *packed_p(esmp2_handle *h);
 void packed_accumulate(esmp2_handle *h, double *x64);
 double packed_wdot(esmp2_handle *h, const float *u, const float *v);
@@ -260,6 +276,17 @@ cudaError_t smem_limit_once(const void *func, int bytes);
 // fill out of bounds.  False when the driver's encoder is unavailable or rejects the description.
 bool tma_map_2d(CUtensorMap *m, const void *base, bool f32, uint64_t inner, uint64_t outer, uint64_t row_bytes,
                 uint32_t box_inner, uint32_t box_outer, int swizzle_bytes);
+
+// Output options of the virtual-index GEMM (vgemm.cu): transposed rows stored as bf16 into
+// PT16 (instead of float32 into PT), optionally scaled by the reduced-cost-basis inverse
+// diagonal (lam: [Nv] diagonal of F_vv in that basis, occ: [slices] occupied part, code:
+// [slices] block | 8 (i == 0) | 16 (j == 0)); family: kernel-timing family of the launch.
+struct VgemmOut {
+  void *PT16 = nullptr;
+  const float *lam = nullptr, *occ = nullptr;
+  const int *code = nullptr;
+  int family = 0;
+};
 
 // ESMP2_DEBUG=1: synchronise the handle's stream and print the host time since the last
 // phase mark (set-up breakdowns; no effect otherwise).

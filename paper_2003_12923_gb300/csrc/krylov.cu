@@ -78,7 +78,8 @@ __device__ __forceinline__ void block_partials(double (&v)[NQ], double *red) {
 }
 
 // Sum the partials of nq quantities in fixed order; mode selects the scalar bookkeeping.
-// slots: 0 rz, 1 rr, 2 bb, 3 pq, 4 alpha, 5 beta, 8.. generic results
+// slots: 0 rz, 1 rr, 2 bb, 3 pq, 4 alpha, 5 beta, 8.. generic results (slots 4, 5 of a zeroed
+// slot array give alpha = beta = 0)
 __global__ void k_finalize(const double *red, int nparts, int nq, double *slots, int mode) {
   __shared__ double sh[32];
   for (int q = 0; q < nq; ++q) {
@@ -98,6 +99,13 @@ __global__ void k_finalize(const double *red, int nparts, int nq, double *slots,
       } else if (mode == 2) {     // rz_new, rr -> beta
         if (q == 0) { slots[5] = t / slots[0]; slots[0] = t; }
         else slots[1] = t;
+      } else if (mode == 5) {     // rr alone
+        slots[1] = t;
+      } else if (mode == 6) {     // rz_new alone -> beta
+        slots[5] = t / slots[0];
+        slots[0] = t;
+      } else if (mode == 7) {     // rz alone (start)
+        slots[0] = t;
       } else {                    // generic
         slots[8 + q] = t;
       }
@@ -620,6 +628,11 @@ __global__ void k_e2s_gen(SCtx s, double *red) {
 
 void launch_pcg_init(esmp2_handle *h, const double *b, const double *q, double *r, double *p);
 
+// one quantity's partials summed into the slots with the bookkeeping of `mode` (k_finalize)
+void k_finalize_ext(const double *red, int nparts, double *slots, int mode, cudaStream_t st) {
+  k_finalize<<<1, 256, 0, st>>>(red, nparts, 1, slots, mode);
+}
+
 static VCtx vctx(const esmp2_handle *h, const double *F = nullptr) {
   VCtx c;
   c.No = h->d.No; c.Nv = h->d.Nv; c.N = h->d.N; c.B = h->d.B; c.F = F ? F : h->F; c.omega = h->omega_op;
@@ -816,8 +829,13 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   const bool packed = h->d.No <= 32;
   ICtx ic;
   bool fused_bf16 = true;
+  // the contraction forms of the packed solve precondition with the Jacobi diagonal of the
+  // basis that diagonalises F_vv, applied through two-sided rotations (rotated Jacobi); the
+  // reduced-cost basis already is that basis
+  const bool rj = packed && !arrowv;
   if (packed) {
     if ((s = packed_setup(h))) return s;
+    if (rj && (s = packed_rj_setup(h))) return s;
     for (int k = 0; k < 6; ++k) ic.off[k] = h->pk.boff[k];
     const float wp[5] = {1.f, 1.f, 1.f, 1.f, 2.f};
     for (int k = 0; k < 5; ++k) ic.w[k] = wp[k];
@@ -908,10 +926,14 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
     // contracts the slices i < j and mirrors them)
     singlet_project(h, r);
-    if (packed) packed_init(h, r, kRedBlocks);
-    else ki_init<<<kRedBlocks, kRedThreads, 0, st>>>(ic, r, r32, p32, d32, h->red);
-    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 0);
-    h->launches += packed ? 1 : 2;
+    if (rj) {
+      if ((s = packed_rj_init(h, r, kRedBlocks))) return s;
+    } else {
+      if (packed) packed_init(h, r, kRedBlocks);
+      else ki_init<<<kRedBlocks, kRedThreads, 0, st>>>(ic, r, r32, p32, d32, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 0);
+      h->launches += packed ? 1 : 2;
+    }
     if ((s = read_slots(h, sl, 32))) return s;
     const double r0 = std::sqrt(sl[1]);
     const double target = std::max(eta * r0, 0.25 * tol * bn);
@@ -935,10 +957,15 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
       }
       if (packed) k_finalize<<<1, 256, 0, st>>>(h->pdot, h->pdot_n, 1, h->red_out, 1);
       else k_finalize<<<1, 256, 0, st>>>(h->red, (int)couple_dot_parts(h), 1, h->red_out, 1);
-      ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, q32, h->red);
-      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
-      ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32, d32);
-      h->launches += 4;
+      h->launches += 1;
+      if (rj) {   // r -= alpha q, z = M^-1 r (rotated Jacobi), beta, d and p
+        if ((s2 = packed_rj_step(h, kRedBlocks))) return s2;
+      } else {
+        ki_update<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, q32, h->red);
+        k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 2);
+        ki_p<<<kRedBlocks, kRedThreads, 0, st>>>(ic, h->red_out, r32, p32, d32);
+        h->launches += 3;
+      }
       h->inner_graph_launches_pending = h->launches - l0;
       return check_cuda(h, cudaGetLastError(), "inner step");
     };
@@ -993,13 +1020,16 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     if (std::getenv("ESMP2_DEBUG")) std::fprintf(stderr, "esmp2 refine:   inner %d  |r_in|/|r0| %.3e\n", inner, std::sqrt(sl[1]) / r0);
     rho_next = relres * std::max(r0 > 0 ? std::sqrt(sl[1]) / r0 : 0.0, 1e-4);
     if (packed) {
+      // x stays in the singlet subspace exactly: d is exactly antisymmetric in (a, b) and
+      // spin-flip symmetric in S (the packed coupling pass writes both images from one value),
+      // and kp_acc64 adds +d and -d to the two slices (negation commutes with rounding)
       packed_accumulate(h, x);
     } else {
       kt_accumulate<float><<<kRedBlocks, kRedThreads, 0, st>>>(c, x, d32);
       h->launches += 1;
+      singlet_project(h, x);  // the float64 residual pass assumes exactly antisymmetric T, X, Y
     }
     h->x_zero = false;
-    singlet_project(h, x);  // the float64 residual pass assumes exactly antisymmetric T, X, Y
     ++outer;
     if ((s = check_device_flag(h))) return s;
   }

@@ -154,7 +154,24 @@ struct Args {
   float *PT;            // [(rows - rows_normal) / Nv][Nv][ldp]: PT[s][b][c] = result row (s, c), column b
   int ldp;              // row pitch of P and PT (elements, a multiple of 4)
   int *err;             // device error flag
+  // transposed rows stored as bf16 into PT16 instead of PT, optionally scaled element-wise
+  // by the inverse diagonal of the reduced-cost basis (the preconditioner's middle factor):
+  // element (slice s, a, b) of the stored slice times valid ? 1 / ((lam[a] + lam[b]) - occ[s]) : 0
+  __nv_bfloat16 *PT16;
+  const float *lam;     // [Nv] or nullptr (no scaling)
+  const float *occ;     // [slices]
+  const int *code;      // [slices]: block | 8 (i == 0) | 16 (j == 0)
 };
+
+// validity of element (a, b) of a slice with the given code (the masks of the block vector)
+__device__ __forceinline__ bool vg_valid(int code, int a, int b) {
+  const int blk = code & 7;
+  const bool i0 = (code & 8) != 0, j0 = (code & 16) != 0;
+  if ((blk == 0 || blk == 2 || blk == 3) && a == b) return false;
+  if (blk == 2 && (i0 || j0 || a == 0 || b == 0)) return false;
+  if (blk == 4 && (j0 || b == 0 || (i0 && a == 0))) return false;
+  return true;
+}
 
 template <bool TF32>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -256,20 +273,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 256);
       const bool normal = r < g.rows_normal;
       float *dst = nullptr;     // column b (< Nv) of this row
+      __nv_bfloat16 *dst16 = nullptr;
       int64_t tpitch = 1;
+      int rc = 0, rcode = 0;    // transposed rows: row within the slice, slice code
+      float rocc = 0.f, rlam = 0.f;
       if (normal) {
         dst = g.P + r * g.ldp;
       } else if (r < g.rows) {
         const int64_t q = r - g.rows_normal, s = q / g.Nv, c = q % g.Nv;
-        dst = g.PT + s * g.Nv * g.ldp + c;   // column b at dst + b * ldp
+        if (g.PT16) dst16 = g.PT16 + s * g.Nv * g.ldp + c;
+        else dst = g.PT + s * g.Nv * g.ldp + c;   // column b at dst + b * ldp
         tpitch = g.ldp;
+        rc = (int)c;
+        if (g.lam) { rcode = g.code[s]; rocc = g.occ[s]; rlam = g.lam[c]; }
       }
       for (int c = c_begin; c < c_end; c += 16) {
         float v[16];
         tmem_ld16(taddr + (uint32_t)c, v);
         if (r >= g.rows) continue;
         const int bc = b0 + c, mcol = min(16, nvalid - c);
-        if (normal && mcol == 16) {
+        if (dst16) {   // stored element (a = bc + q, b = rc) of the slice
+          if (g.lam) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int a = bc + q;
+              v[q] = (q < mcol && vg_valid(rcode, a, rc)) ? v[q] / ((g.lam[a] + rlam) - rocc) : 0.f;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < mcol) dst16[(int64_t)(bc + q) * tpitch] = __float2bfloat16_rn(v[q]);
+        } else if (normal && mcol == 16) {
           float4 *d4 = reinterpret_cast<float4 *>(dst + bc);
 #pragma unroll
           for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -315,7 +349,7 @@ static bool vgemm_tiling(int ncols, int Kc, int bk, int *nN, int *Nt, int *nk, i
 // P = A W on the tensor cores.  A: rows x Nvp (row pitch Nvp elements), W: Nv x Nvp (row b of
 // W is column b of the right factor), both bf16, or both float32 read as tf32 (tf32 = true).
 esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_normal, const void *W, float *P,
-                   float *PT, int ldp, double alg_flops, bool tf32) {
+                   float *PT, int ldp, double alg_flops, bool tf32, const VgemmOut *out) {
   const int Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
   const int bk = tf32 ? vg::Kind<true>::BK : vg::Kind<false>::BK, esz = tf32 ? 4 : 2;
   int nN = 0, Nt = 0, nk = 0, stages = 0, smem = 0;
@@ -352,11 +386,18 @@ esmp2_status vgemm(esmp2_handle *h, const void *A, int64_t rows, int64_t rows_no
   g.PT = PT;
   g.ldp = ldp;
   g.err = h->dflag;
+  if (out) {
+    g.PT16 = static_cast<__nv_bfloat16 *>(out->PT16);
+    g.lam = out->lam;
+    g.occ = out->occ;
+    g.code = out->code;
+  }
+  const int family = out ? out->family : ESMP2_KT_CONTRACTION;
   const int64_t per_group = std::max<int64_t>(1, std::min<int64_t>(g.m_tiles, sms / nN));
   const int grid = (int)(per_group * nN);
   const double exec = 2.0 * (double)g.m_tiles * vg::BM * (double)Nv * (double)nN * Nt;
   {
-    KScope ks(h->stream, ESMP2_KT_CONTRACTION, alg_flops, exec);
+    KScope ks(h->stream, family, alg_flops, exec);
     if (tf32) vg::k_vgemm<true><<<grid, vg::NTHREADS, smem, h->stream>>>(mA, mW, g);
     else vg::k_vgemm<false><<<grid, vg::NTHREADS, smem, h->stream>>>(mA, mW, g);
   }

@@ -134,7 +134,7 @@ def load(path: str | None = None):
 
 NOALLOC_MAX_BYTES = 64 << 20
 
-KERNEL_FAMILIES = ("contraction", "coupling", "gemm64", "e2s", "digits")
+KERNEL_FAMILIES = ("contraction", "coupling", "gemm64", "e2s", "digits", "precond")
 
 
 def kernel_timing(enable: bool):

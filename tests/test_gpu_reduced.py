@@ -64,3 +64,21 @@ def test_reduced_needs_packed_inner_solve():
     with pytest.raises(esmp2.Esmp2Error) as ei:
         h.solve(tol=1e-8, maxit=10, precision=esmp2.REDUCED_MIXED)
     assert ei.value.status == esmp2.ERR_UNSUPPORTED
+
+
+def test_reduced_matches_contraction_form_at_nv400():
+    """Nv = 400 (as the benchmark): in the TOP basis F_vv is far from diagonal (W_v mixes the
+    virtual orbitals), so the Jacobi eigenvectors take several sweeps; the reduced-cost E2 must
+    equal the tensor-core form's and the float64 form's to the mixed tolerance."""
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(6, 400, 41)
+    e = {}
+    for name, prec, tol in (("fp64", esmp2.FP64, 1e-10), ("bf16", esmp2.MIXED_BF16, 1e-9),
+                            ("reduced", esmp2.REDUCED_MIXED, 1e-9)):
+        h = handle_for(inst)
+        h.solve(tol=tol, maxit=3000, precision=prec)
+        e[name] = h.energy()
+        h.close()
+    for k in ("E2", "E2_D", "E2_L", "E2_S"):
+        assert abs(e["reduced"][k] - e["fp64"][k]) < 1e-8, (k, e["reduced"][k], e["fp64"][k])
+        assert abs(e["bf16"][k] - e["fp64"][k]) < 1e-8, (k, e["bf16"][k], e["fp64"][k])
