@@ -452,18 +452,26 @@ def family_roofline(name, kt, peaks, peak_src, fp64_peak, steps):
            "avg_launch_ms": kt["ms"] / max(1, kt["launches"])}
     if sec <= 0:
         return out
-    if name in ("contraction", "digits"):
+    if name == "precond":
+        out.update({"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops_sustained"],
+                    "achieved": kt["exec_units"] / sec / 1e12, "achieved_executed": kt["exec_units"] / sec / 1e12,
+                    "kernel": "vg::k_vgemm, bf16 rotations of the inner preconditioner (executed flops: extra work "
+                              "beyond the method's count)",
+                    "peak_source": f"bf16 dense sustained, {peak_src} (MEASURED_PEAKS.json)"})
+    elif name in ("contraction", "digits"):
         out.update({"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops_sustained"],
                     "achieved": kt["alg_units"] / sec / 1e12, "achieved_executed": kt["exec_units"] / sec / 1e12,
                     "peak_source": f"bf16 dense sustained, {peak_src} (MEASURED_PEAKS.json)"})
-        out["kernel"] = ("k_virt, bf16 operands (inner sigma): achieved = the method's flops 4 n_unique Nv per build"
+        out["kernel"] = ("vg::k_vgemm, bf16 (or tf32) operands, the packed inner sigma's virtual-index GEMM: achieved = "
+                         "the method's flops 4 n_unique Nv per build"
                          if name == "contraction" else
                          "k_virt, exact bf16 digit products (float64-accurate residual, energy, rotations): "
                          "achieved = the method's flops of each contraction once; achieved_executed = every "
                          "digit pair the tensor cores run")
     elif name == "coupling":
         out.update({"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"], "achieved": kt["alg_units"] / sec / 1e9,
-                    "kernel": "k_couple: element-wise coupling pass (one read of x, one read and write of y)",
+                    "kernel": "kp_couple_anti/s/z (packed float32 inner coupling pass) and k_couple (float64 true "
+                              "residual): algorithmic bytes = one read of x and of the products, one write of y",
                     "peak_source": f"copy bandwidth, {peak_src} (MEASURED_PEAKS.json)"})
     elif name == "gemm64":
         out.update({"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak, "achieved": kt["alg_units"] / sec / 1e12,

@@ -271,13 +271,45 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
     // below 1e-12 of it and no longer shrinking (after the quadratic phase the rotations only
     // move rounding noise around).  In the TOP basis F_vv is far from diagonal (W_v mixes the
     // virtual orbitals), so the first sweeps reduce it only a few-fold each.
-    for (int sweep = 0; sweep < 40; ++sweep) {
-      for (int r = 0; r < rounds; ++r) {
-        k_jacobi_round<<<grid, 512, 0, st>>>(A0, A1, V0, V1, m, r);
-        std::swap(A0, A1);
-        std::swap(V0, V1);
+    // two sweeps (an even number of rounds, so the buffers end where they started) as one
+    // CUDA graph of dependent kernel nodes, replayed: the rounds are short and launch-bound
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
+      cudaGraphNode_t prev_node = nullptr;
+      bool ok = true;
+      double *a0 = A0, *a1 = A1, *v0 = V0, *v1 = V1;
+      for (int k = 0; k < 2 * rounds && ok; ++k) {
+        int rr = k % rounds, mm_ = m;
+        void *args[] = {&a0, &a1, &v0, &v1, &mm_, &rr};
+        cudaKernelNodeParams kp{};
+        kp.func = reinterpret_cast<void *>(k_jacobi_round);
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(512);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t node = nullptr;
+        ok = cudaGraphAddKernelNode(&node, graph, prev_node ? &prev_node : nullptr, prev_node ? 1 : 0, &kp) ==
+             cudaSuccess;
+        prev_node = node;
+        std::swap(a0, a1);
+        std::swap(v0, v1);
       }
-      h->launches += rounds + 1;
+      if (!ok || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+    }
+    for (int sweep = 0; sweep < 40; sweep += 2) {
+      if (gexec) {
+        if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) break;
+      } else {
+        for (int k = 0; k < 2 * rounds; ++k) {
+          k_jacobi_round<<<grid, 512, 0, st>>>(A0, A1, V0, V1, m, k % rounds);
+          std::swap(A0, A1);
+          std::swap(V0, V1);
+        }
+      }
+      h->launches += 2 * rounds + 1;
       k_offnorm<<<1, 1024, 0, st>>>(A0, m, nrm);
       double hn[2] = {0.0, 0.0};
       e = cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st);
@@ -288,8 +320,14 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
         return check_cuda(h, e, "virtual rotation (Jacobi)");
       }
       if (!(hn[0] > 1e-30 * hn[1])) break;
-      if (hn[0] < 1e-24 * hn[1] && prev > 0.0 && hn[0] > 0.25 * prev) break;
+      if (hn[0] < 1e-24 * hn[1] && prev > 0.0 && hn[0] > 0.0625 * prev) break;
       prev = hn[0];
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (e != cudaSuccess) {
+      release();
+      dfree(Rv, st); dfree(Rvt, st);
+      return check_cuda(h, e, "virtual rotation (Jacobi)");
     }
     debug_phase(h, "  virtual rotation: Jacobi eigenvectors of the virtual block");
   }
