@@ -347,6 +347,7 @@ def run_batch(args):
             "auto": esmp2.MIXED_BF16}.get(args.precision, esmp2.MIXED_BF16)
     t_batch, t_seq64, w_seq64, w_all = 0.0, 0.0, 0.0, 0.0
     n_done, worst_res, e2_diffs, iters, launches, h2d = 0, 0.0, [], [], 0, 0
+    e2_by_seed = {}
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
@@ -379,6 +380,7 @@ def run_batch(args):
             worst_res = max(worst_res, r["rel_residual"])
             iters.append(r["iterations"])
             launches += int(r["kernel_launches"])
+            e2_by_seed[sd] = r["E2"]
         for (No, Nv, sd), inst, r in zip(wave, insts, res):
             if (w0 + wave.index((No, Nv, sd))) % args.fp64_every == 0:
                 t0 = time.perf_counter()
@@ -395,6 +397,30 @@ def run_batch(args):
     ktimes = esmp2.kernel_times()
     esmp2.kernel_timing(False)
     est64 = t_seq64 * (w_all / w_seq64) if w_seq64 > 0 else None
+    # the reduced-cost basis form of the same batch (no virtual-index contraction), reported
+    # beside the tensor-core form
+    red = None
+    if not args.no_variants and prec != esmp2.REDUCED_MIXED:
+        t_red, worst_red, d_red = 0.0, 0.0, 0.0
+        e_main = {}
+        for w0 in range(0, len(shapes), args.wave):
+            wave = shapes[w0:w0 + args.wave]
+            insts = [synth.make_instance(No, Nv, sd, sigma_off=1e-3) for (No, Nv, sd) in wave]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, res = esmp2.batch_solve(insts, tol=args.tol, maxit=args.maxit, precision=esmp2.REDUCED_MIXED,
+                                        concurrency=args.concurrency)
+            torch.cuda.synchronize()
+            t_red += time.perf_counter() - t0
+            if st != esmp2.OK:
+                raise RuntimeError("batch_solve (reduced) failed: " + "; ".join(r["message"] for r in res if r["status"]))
+            for (No, Nv, sd), r in zip(wave, res):
+                worst_red = max(worst_red, r["rel_residual"])
+                e_main[sd] = r["E2"]
+            del insts
+        red = {"value": len(shapes) / t_red, "unit": "solves/s", "batch_seconds": t_red, "worst_rel_residual": worst_red}
+    if red is not None:
+        red["max_abs_E2_minus_main"] = max(abs(e_main[sd] - e2_by_seed[sd]) for sd in e_main)
     peaks, peak_src = load_peaks()
     fp64_peak = measure_fp64_peak(torch.device("cuda", 0))
     fams = {k: family_roofline(k, v, peaks, peak_src, fp64_peak, 1) for k, v in ktimes.items()}
@@ -434,7 +460,7 @@ def run_batch(args):
                     "d2h_bytes_per_step": int(n_done * 8 * 4)},
             "gpu_launches": launches, "clocks": clocks,
             "instances": n_done, "batch_seconds": t_batch, "worst_rel_residual": worst_res,
-            "inner_iterations_total": int(sum(iters)),
+            "inner_iterations_total": int(sum(iters)), "reduced_basis_form": red,
             "fp64_sequential": {"seconds_measured": t_seq64, "instances_measured": len(e2_diffs),
                                 "seconds_estimated_all": est64,
                                 "solves_per_s_estimated": (n_done / est64) if est64 else None,

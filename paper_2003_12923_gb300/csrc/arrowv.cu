@@ -13,9 +13,9 @@
 // rotation of the right-hand side (and of the solution, when it is asked for), two float64-
 // exact digit-split products per slice.
 //
-// The eigenvectors of the virtual block come from the cyclic Jacobi method (Golub and Van
-// Loan, Sec. 8.5) with the round-robin ordering of disjoint pairs: one launch per round, all
-// n/2 rotations of a round applied at once as A' = J^T A J, V' = V J.
+// The eigenvectors of the virtual block come from the one-sided (Hestenes) Jacobi method with
+// the round-robin ordering of disjoint pairs: one launch per round, one warp per pair rotating
+// two rows of B and of the accumulated rotation (all accesses along contiguous rows).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -41,89 +41,101 @@ __global__ void k_vblock(const double *F, int N, int No, int m, double *A, doubl
   }
 }
 
-// One round r of the cyclic Jacobi method: rotations of the disjoint pairs (p, q) of the
-// round-robin ordering of n = m (+1 if m is odd) indices, each chosen to zero A_pq
-// (tau = (A_qq - A_pp) / (2 A_pq), t the smaller root of t^2 + 2 tau t - 1 = 0,
-// c = 1 / sqrt(1 + t^2), s = t c; J_pp = J_qq = c, J_pq = s, J_qp = -s); then
-// A2 = J^T A J and V2 = V J.  Column i of J has two entries: J_ii = al[i] and
-// J_{partner(i), i} = be[i].  Every CTA forms the round's table in shared memory.
-__global__ void __launch_bounds__(512) k_jacobi_round(const double *A, double *A2, const double *V, double *V2,
-                                                      int m, int r) {
-  __shared__ int part[1024];
-  __shared__ double al[1024], be[1024];
-  const int n = m + (m & 1);
-  for (int pi = threadIdx.x; pi < n / 2; pi += blockDim.x) {
-    int p, q;
-    if (pi == 0) {
-      p = 0;
-      q = 1 + (r % (n - 1));
-    } else {
-      p = 1 + ((pi + r) % (n - 1));
-      q = 1 + ((n - 1 - pi + r) % (n - 1));
-    }
-    if (p > q) { const int t = p; p = q; q = t; }
-    if (q >= m) {   // p is paired with the padding index
-      part[p] = p; al[p] = 1.0; be[p] = 0.0;
-      continue;
-    }
-    double c = 1.0, s = 0.0;
-    const double apq = A[(int64_t)p * m + q];
-    if (apq != 0.0) {
-      const double tau = (A[(int64_t)q * m + q] - A[(int64_t)p * m + p]) / (2.0 * apq);
-      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-      c = 1.0 / sqrt(1.0 + t * t);
-      s = t * c;
-    }
-    part[p] = q; al[p] = c; be[p] = -s;
-    part[q] = p; al[q] = c; be[q] = s;
+// One round r of the one-sided (Hestenes) Jacobi method on the symmetric positive definite
+// m x m matrix held as the rows of B: the disjoint pairs (p, q) of the round-robin ordering of
+// n = m (+1 if m is odd) indices, one CTA each, rotate rows p and q of B (B <- G^T B) until
+// all rows are mutually orthogonal; the rotations accumulate into the rows of Jt (Jt <- G^T Jt).
+// At convergence B = Jt A with orthogonal rows, so the rows of Jt are eigenvectors of A^2,
+// hence of A (A positive definite).  Rotation of a pair: alpha = |b_p|^2, beta = |b_q|^2,
+// gamma = b_p . b_q, zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 +
+// zeta^2)), c = 1 / sqrt(1 + t^2), s = c t; skipped when |gamma| <= 1e-14 sqrt(alpha beta)
+// (the remaining off-diagonal part of R^T A R is then of the order of 1e-14 of its diagonal).
+// Rows are contiguous, so every access is coalesced.  *rotated is set when a pair rotates.
+constexpr int kJT = 128;                 // threads per pair (one CTA)
+constexpr int kJE = 8;                   // row elements per thread: m <= kJT kJE = 1024
+__global__ void __launch_bounds__(kJT) k_jacobi_os_round(double *B, double *Jt, int m, int r, int *rotated) {
+  __shared__ double red[3][kJT / 32];
+  const int n = m + (m & 1), pi = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int p, q;
+  if (pi == 0) {
+    p = 0;
+    q = 1 + (r % (n - 1));
+  } else {
+    p = 1 + ((pi + r) % (n - 1));
+    q = 1 + ((n - 1 - pi + r) % (n - 1));
   }
-  __syncthreads();
-  const int64_t mm = (int64_t)m * m;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * mm; e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < mm) {
-      const int i = (int)(e / m), j = (int)(e % m), pi = part[i], pj = part[j];
-      const double ri = al[j] * A[(int64_t)i * m + j] + be[j] * A[(int64_t)i * m + pj];
-      const double rp = al[j] * A[(int64_t)pi * m + j] + be[j] * A[(int64_t)pi * m + pj];
-      A2[e] = al[i] * ri + be[i] * rp;
-    } else {
-      const int64_t f = e - mm;
-      const int k = (int)(f / m), j = (int)(f % m), pj = part[j];
-      V2[f] = al[j] * V[(int64_t)k * m + j] + be[j] * V[(int64_t)k * m + pj];
-    }
+  if (p > q) { const int t = p; p = q; q = t; }
+  if (q >= m) return;   // paired with the padding index (uniform over the CTA)
+  double *bp = B + (int64_t)p * m, *bq = B + (int64_t)q * m;
+  double *jp = Jt + (int64_t)p * m, *jq = Jt + (int64_t)q * m;
+  // every load of the two rows (and of the two rows of Jt) issued before it is used
+  double x[kJE], y[kJE], u[kJE], v[kJE];
+#pragma unroll
+  for (int e = 0; e < kJE; ++e) {
+    const int k = tid + e * kJT;
+    const bool in = k < m;
+    x[e] = in ? bp[k] : 0.0;
+    y[e] = in ? bq[k] : 0.0;
+    u[e] = in ? jp[k] : 0.0;
+    v[e] = in ? jq[k] : 0.0;
   }
-}
-
-// out[0] = sum of squares of the off-diagonal elements, out[1] = of all elements (one CTA)
-__global__ void __launch_bounds__(1024) k_offnorm(const double *A, int m, double *out) {
-  __shared__ double s0[32], s1[32];
-  double off = 0.0, tot = 0.0;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    const double v = A[e] * A[e];
-    tot += v;
-    if (e / m != e % m) off += v;
+  double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+  for (int e = 0; e < kJE; ++e) {
+    al += x[e] * x[e];
+    be += y[e] * y[e];
+    ga += x[e] * y[e];
   }
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    off += __shfl_xor_sync(0xffffffffu, off, o);
-    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
   }
-  if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = off; s1[threadIdx.x >> 5] = tot; }
+  if (lane == 0) { red[0][warp] = al; red[1][warp] = be; red[2][warp] = ga; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s0[w]; b += s1[w]; }
-    out[0] = a;
-    out[1] = b;
+  // the rotation from one thread (float64 division and square root are long sequences on
+  // the float64 pipe), broadcast through shared memory
+  __shared__ double cs[2];
+  __shared__ int skip;
+  if (tid == 0) {
+    al = be = ga = 0.0;
+#pragma unroll
+    for (int w = 0; w < kJT / 32; ++w) { al += red[0][w]; be += red[1][w]; ga += red[2][w]; }
+    skip = (al <= 1e-300 || be <= 1e-300 || fabs(ga) <= 1e-14 * sqrt(al * be)) ? 1 : 0;
+    if (!skip) {
+      const double zeta = (be - al) / (2.0 * ga);
+      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      const double c0 = 1.0 / sqrt(1.0 + t * t);
+      cs[0] = c0;
+      cs[1] = c0 * t;
+      *rotated = 1;
+    }
+  }
+  __syncthreads();
+  if (skip) return;   // uniform
+  const double c = cs[0], s = cs[1];
+#pragma unroll
+  for (int e = 0; e < kJE; ++e) {
+    const int k = tid + e * kJT;
+    if (k < m) {
+      bp[k] = c * x[e] - s * y[e];
+      bq[k] = s * x[e] + c * y[e];
+      jp[k] = c * u[e] - s * v[e];
+      jq[k] = s * u[e] + c * v[e];
+    }
   }
 }
 
-// Rv = diag(1, V) (Nv x Nv), Rvt = Rv^T, W3 = diag(I_No, Rv) (N x N)
-__global__ void k_build_rv(const double *V, int No, int Nv, double *Rv, double *Rvt, double *W3) {
+// Rv = diag(1, V) (Nv x Nv; V[i][k] = Vt[k][i], the rows of Vt the eigenvectors), Rvt = Rv^T,
+// W3 = diag(I_No, Rv) (N x N)
+__global__ void k_build_rv(const double *Vt, int No, int Nv, double *Rv, double *Rvt, double *W3) {
   const int N = No + Nv, m = Nv - 1;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / N), q = (int)(e % N);
     double v = p == q ? 1.0 : 0.0;
-    if (p > No && q > No) v = V[(int64_t)(p - No - 1) * m + (q - No - 1)];
+    if (p > No && q > No) v = Vt[(int64_t)(q - No - 1) * m + (p - No - 1)];   // column q of R~: eigenvector q
     else if (p >= No && q >= No && p != q) v = 0.0;
     W3[e] = p < No || q < No ? (p == q ? 1.0 : 0.0) : v;
     if (p >= No && q >= No) {
@@ -243,85 +255,73 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
   A(reinterpret_cast<void **>(&Rvt), sizeof(double) * (size_t)Nv * Nv);
   if (!h->Farr) A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
   if (!h->F32arr) A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
-  double *A0 = nullptr, *A1 = nullptr, *V0 = nullptr, *V1 = nullptr, *W3 = nullptr, *T1 = nullptr, *nrm = nullptr;
+  double *A0 = nullptr, *V0 = nullptr, *W3 = nullptr, *T1 = nullptr, *nrm = nullptr;
   const size_t mm = (size_t)std::max(1, m * m);
   A(reinterpret_cast<void **>(&A0), sizeof(double) * mm);
-  A(reinterpret_cast<void **>(&A1), sizeof(double) * mm);
   A(reinterpret_cast<void **>(&V0), sizeof(double) * mm);
-  A(reinterpret_cast<void **>(&V1), sizeof(double) * mm);
   A(reinterpret_cast<void **>(&W3), sizeof(double) * (size_t)N * N);
   A(reinterpret_cast<void **>(&T1), sizeof(double) * (size_t)N * N);
   A(reinterpret_cast<void **>(&nrm), sizeof(double) * 2);
   auto release = [&]() {
-    dfree(A0, st); dfree(A1, st); dfree(V0, st); dfree(V1, st); dfree(W3, st); dfree(T1, st); dfree(nrm, st);
+    dfree(A0, st); dfree(V0, st); dfree(W3, st); dfree(T1, st); dfree(nrm, st);
   };
   if (e != cudaSuccess) {
     release();
     dfree(Rv, st); dfree(Rvt, st);
     return check_cuda(h, e, "virtual rotation buffers");
   }
-  // eigenvectors of F_vv without t'
+  // eigenvectors of F_vv without t' (one-sided Jacobi on the rows of B = A, Jt = I)
   if (m >= 1) {
     k_vblock<<<256, 256, 0, st>>>(h->Fsemi, N, No, m, A0, V0);
     h->launches += 1;
-    const int rounds = m + (m & 1) - 1;
-    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(2LL * m * m, 512), 304);
-    double prev = -1.0;
-    // sweeps until the off-diagonal part is at the rounding level: below 1e-15 of the norm, or
-    // below 1e-12 of it and no longer shrinking (after the quadratic phase the rotations only
-    // move rounding noise around).  In the TOP basis F_vv is far from diagonal (W_v mixes the
-    // virtual orbitals), so the first sweeps reduce it only a few-fold each.
-    // two sweeps (an even number of rounds, so the buffers end where they started) as one
-    // CUDA graph of dependent kernel nodes, replayed: the rounds are short and launch-bound
+    const int n2 = (m + (m & 1)) / 2, rounds = m + (m & 1) - 1;
+    const unsigned grid = (unsigned)n2;
+    int *rot = reinterpret_cast<int *>(nrm);
+    // two sweeps as one CUDA graph (a reset of the flag, then the rounds as dependent kernel
+    // nodes), replayed until a pass of two sweeps rotates no pair
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
       cudaGraphNode_t prev_node = nullptr;
-      bool ok = true;
-      double *a0 = A0, *a1 = A1, *v0 = V0, *v1 = V1;
+      cudaMemsetParams mp{};
+      mp.dst = rot;
+      mp.value = 0;
+      mp.elementSize = 4;
+      mp.width = 1;
+      mp.height = 1;
+      bool ok = cudaGraphAddMemsetNode(&prev_node, graph, nullptr, 0, &mp) == cudaSuccess;
       for (int k = 0; k < 2 * rounds && ok; ++k) {
         int rr = k % rounds, mm_ = m;
-        void *args[] = {&a0, &a1, &v0, &v1, &mm_, &rr};
+        double *b0 = A0, *j0 = V0;
+        void *args[] = {&b0, &j0, &mm_, &rr, &rot};
         cudaKernelNodeParams kp{};
-        kp.func = reinterpret_cast<void *>(k_jacobi_round);
+        kp.func = reinterpret_cast<void *>(k_jacobi_os_round);
         kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(512);
+        kp.blockDim = dim3(kJT);
         kp.sharedMemBytes = 0;
         kp.kernelParams = args;
         cudaGraphNode_t node = nullptr;
-        ok = cudaGraphAddKernelNode(&node, graph, prev_node ? &prev_node : nullptr, prev_node ? 1 : 0, &kp) ==
-             cudaSuccess;
+        ok = cudaGraphAddKernelNode(&node, graph, &prev_node, 1, &kp) == cudaSuccess;
         prev_node = node;
-        std::swap(a0, a1);
-        std::swap(v0, v1);
       }
       if (!ok || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
       cudaGraphDestroy(graph);
       cudaGetLastError();
     }
-    for (int sweep = 0; sweep < 40; sweep += 2) {
+    bool converged = false;
+    for (int sweep = 0; sweep < 60 && !converged; sweep += 2) {
       if (gexec) {
         if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) break;
       } else {
-        for (int k = 0; k < 2 * rounds; ++k) {
-          k_jacobi_round<<<grid, 512, 0, st>>>(A0, A1, V0, V1, m, k % rounds);
-          std::swap(A0, A1);
-          std::swap(V0, V1);
-        }
+        cudaMemsetAsync(rot, 0, sizeof(int), st);
+        for (int k = 0; k < 2 * rounds; ++k) k_jacobi_os_round<<<grid, kJT, 0, st>>>(A0, V0, m, k % rounds, rot);
       }
-      h->launches += 2 * rounds + 1;
-      k_offnorm<<<1, 1024, 0, st>>>(A0, m, nrm);
-      double hn[2] = {0.0, 0.0};
-      e = cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st);
+      h->launches += 2 * rounds;
+      int hr = 1;
+      e = cudaMemcpyAsync(&hr, rot, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) {
-        release();
-        dfree(Rv, st); dfree(Rvt, st);
-        return check_cuda(h, e, "virtual rotation (Jacobi)");
-      }
-      if (!(hn[0] > 1e-30 * hn[1])) break;
-      if (hn[0] < 1e-24 * hn[1] && prev > 0.0 && hn[0] > 0.0625 * prev) break;
-      prev = hn[0];
+      if (e != cudaSuccess) break;
+      converged = hr == 0;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (e != cudaSuccess) {
