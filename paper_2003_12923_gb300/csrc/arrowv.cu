@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -50,10 +51,27 @@ __global__ void k_vblock(const double *F, int N, int No, int m, double *A, doubl
 // gamma = b_p . b_q, zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 +
 // zeta^2)), c = 1 / sqrt(1 + t^2), s = c t; skipped when |gamma| <= 1e-14 sqrt(alpha beta)
 // (the remaining off-diagonal part of R^T A R is then of the order of 1e-14 of its diagonal).
-// Rows are contiguous, so every access is coalesced.  *rotated is set when a pair rotates.
+// Rows are contiguous, so every access is coalesced.  *maxr2 receives the largest
+// gamma^2 / (alpha beta) of the pairs that rotate (as float bits).
+// Newton-Raphson refinements in float64 of float32 seeds: 1/sqrt(x) by y <- y (3 - x y^2) / 2 and
+// 1/x by y <- y (2 - x y), two steps each (quadratic convergence from the seed's 2^-22 to the
+// float64 rounding level); for x in a range where the float32 seed is a normal number
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y = (double)(1.0f / (float)x);
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+
 constexpr int kJT = 128;                 // threads per pair (one CTA)
 constexpr int kJE = 8;                   // row elements per thread: m <= kJT kJE = 1024
-__global__ void __launch_bounds__(kJT) k_jacobi_os_round(double *B, double *Jt, int m, int r, int *rotated) {
+__global__ void __launch_bounds__(kJT) k_jacobi_os_round(double *B, double *Jt, int m, int r, unsigned *maxr2) {
   __shared__ double red[3][kJT / 32];
   const int n = m + (m & 1), pi = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int p, q;
@@ -102,14 +120,20 @@ __global__ void __launch_bounds__(kJT) k_jacobi_os_round(double *B, double *Jt, 
     al = be = ga = 0.0;
 #pragma unroll
     for (int w = 0; w < kJT / 32; ++w) { al += red[0][w]; be += red[1][w]; ga += red[2][w]; }
-    skip = (al <= 1e-300 || be <= 1e-300 || fabs(ga) <= 1e-14 * sqrt(al * be)) ? 1 : 0;
+    skip = (al <= 1e-300 || be <= 1e-300 || ga * ga <= 1e-28 * al * be) ? 1 : 0;
     if (!skip) {
-      const double zeta = (be - al) / (2.0 * ga);
-      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      const double c0 = 1.0 / sqrt(1.0 + t * t);
+      // largest gamma^2 / (alpha beta) of the pass (non-negative floats order as their bits)
+      atomicMax(maxr2, __float_as_uint((float)(ga * ga * rcp_nr(al * be))));
+      // t = sign(d) g / (|d| + sqrt(d^2 + g^2)) with d = beta - alpha, g = 2 gamma (the smaller
+      // root of t^2 + 2 zeta t - 1 = 0, zeta = d / g), formed on (d, g) scaled to max 1
+      const double d0 = be - al, g0 = 2.0 * ga;
+      const double sc = rcp_nr(fmax(fabs(d0), fabs(g0)));
+      const double d = d0 * sc, g = g0 * sc, q2 = d * d + g * g;   // q2 in [1, 2]
+      const double rt = q2 * rsqrt_nr(q2);
+      const double t = (d >= 0.0 ? g : -g) * rcp_nr(fabs(d) + rt);
+      const double c0 = rsqrt_nr(1.0 + t * t);
       cs[0] = c0;
       cs[1] = c0 * t;
-      *rotated = 1;
     }
   }
   __syncthreads();
@@ -235,9 +259,13 @@ __global__ void k_varrow64(const double *x, const double *F, const double *rho, 
 }  // namespace
 
 // The virtual rotation R~ = diag(1, V) (V: eigenvectors of F_vv without t') and F in the
-// rotated basis (Farr, float copy F32arr); no vector is rotated here.
-esmp2_status ensure_vrot(esmp2_handle *h) {
-  if (h->Rv) return ESMP2_OK;
+// rotated basis (Farr, float copy F32arr); no vector is rotated here.  exact = false stops the
+// Jacobi sweeps once every pair is orthogonal to 1e-6 (enough for a preconditioner); exact =
+// true continues from there to the rounding level (the reduced-cost basis needs F_vv exactly
+// arrow shaped).  The Jacobi state stays on the handle between the two.
+esmp2_status ensure_vrot(esmp2_handle *h, bool exact) {
+  const int want = exact ? 2 : 1;
+  if (h->vrot_level >= want) return ESMP2_OK;
   esmp2_status s = ensure_mixed(h, true);
   if (s) return s;
   const int No = h->d.No, Nv = h->d.Nv, N = h->d.N, m = Nv - 1;
@@ -250,41 +278,43 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
   auto A = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(p, bytes ? bytes : 16, st);
   };
-  double *Rv = nullptr, *Rvt = nullptr;
-  A(reinterpret_cast<void **>(&Rv), sizeof(double) * (size_t)Nv * Nv);
-  A(reinterpret_cast<void **>(&Rvt), sizeof(double) * (size_t)Nv * Nv);
-  if (!h->Farr) A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
-  if (!h->F32arr) A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
-  double *A0 = nullptr, *V0 = nullptr, *W3 = nullptr, *T1 = nullptr, *nrm = nullptr;
   const size_t mm = (size_t)std::max(1, m * m);
-  A(reinterpret_cast<void **>(&A0), sizeof(double) * mm);
-  A(reinterpret_cast<void **>(&V0), sizeof(double) * mm);
+  if (!h->Rv) {
+    A(reinterpret_cast<void **>(&h->Rv), sizeof(double) * (size_t)Nv * Nv);
+    A(reinterpret_cast<void **>(&h->Rvt), sizeof(double) * (size_t)Nv * Nv);
+    A(reinterpret_cast<void **>(&h->Farr), sizeof(double) * (size_t)N * N);
+    A(reinterpret_cast<void **>(&h->F32arr), sizeof(float) * (size_t)N * N);
+    A(reinterpret_cast<void **>(&h->jB), sizeof(double) * mm);
+    A(reinterpret_cast<void **>(&h->jJ), sizeof(double) * mm);
+    A(reinterpret_cast<void **>(&h->jflag), sizeof(unsigned) * 4);
+    if (e != cudaSuccess) return check_cuda(h, e, "virtual rotation buffers");
+    if (m >= 1) {
+      k_vblock<<<256, 256, 0, st>>>(h->Fsemi, N, No, m, h->jB, h->jJ);
+      h->launches += 1;
+    }
+  }
+  double *W3 = nullptr, *T1 = nullptr;
   A(reinterpret_cast<void **>(&W3), sizeof(double) * (size_t)N * N);
   A(reinterpret_cast<void **>(&T1), sizeof(double) * (size_t)N * N);
-  A(reinterpret_cast<void **>(&nrm), sizeof(double) * 2);
-  auto release = [&]() {
-    dfree(A0, st); dfree(V0, st); dfree(W3, st); dfree(T1, st); dfree(nrm, st);
-  };
+  auto release = [&]() { dfree(W3, st); dfree(T1, st); };
   if (e != cudaSuccess) {
     release();
-    dfree(Rv, st); dfree(Rvt, st);
     return check_cuda(h, e, "virtual rotation buffers");
   }
   // eigenvectors of F_vv without t' (one-sided Jacobi on the rows of B = A, Jt = I)
   if (m >= 1) {
-    k_vblock<<<256, 256, 0, st>>>(h->Fsemi, N, No, m, A0, V0);
-    h->launches += 1;
     const int n2 = (m + (m & 1)) / 2, rounds = m + (m & 1) - 1;
     const unsigned grid = (unsigned)n2;
-    int *rot = reinterpret_cast<int *>(nrm);
-    // two sweeps as one CUDA graph (a reset of the flag, then the rounds as dependent kernel
-    // nodes), replayed until a pass of two sweeps rotates no pair
+    unsigned *mr = h->jflag;
+    double *B = h->jB, *J = h->jJ;
+    // two sweeps as one CUDA graph (a reset of the pass maximum, then the rounds as dependent
+    // kernel nodes), replayed until the pass's largest gamma^2 / (alpha beta) is below the target
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
       cudaGraphNode_t prev_node = nullptr;
       cudaMemsetParams mp{};
-      mp.dst = rot;
+      mp.dst = mr;
       mp.value = 0;
       mp.elementSize = 4;
       mp.width = 1;
@@ -292,8 +322,7 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
       bool ok = cudaGraphAddMemsetNode(&prev_node, graph, nullptr, 0, &mp) == cudaSuccess;
       for (int k = 0; k < 2 * rounds && ok; ++k) {
         int rr = k % rounds, mm_ = m;
-        double *b0 = A0, *j0 = V0;
-        void *args[] = {&b0, &j0, &mm_, &rr, &rot};
+        void *args[] = {&B, &J, &mm_, &rr, &mr};
         cudaKernelNodeParams kp{};
         kp.func = reinterpret_cast<void *>(k_jacobi_os_round);
         kp.gridDim = dim3(grid);
@@ -308,30 +337,34 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
       cudaGraphDestroy(graph);
       cudaGetLastError();
     }
-    bool converged = false;
-    for (int sweep = 0; sweep < 60 && !converged; sweep += 2) {
+    // a pass of two sweeps whose rotations were all below the target: 1e-14 (none rotated)
+    // for the exact basis, 1e-6 for the preconditioner
+    const float target = exact ? 0.f : 1e-12f;
+    bool done = false;
+    for (int sweep = 0; sweep < 60 && !done; sweep += 2) {
       if (gexec) {
         if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) break;
       } else {
-        cudaMemsetAsync(rot, 0, sizeof(int), st);
-        for (int k = 0; k < 2 * rounds; ++k) k_jacobi_os_round<<<grid, kJT, 0, st>>>(A0, V0, m, k % rounds, rot);
+        cudaMemsetAsync(mr, 0, sizeof(unsigned), st);
+        for (int k = 0; k < 2 * rounds; ++k) k_jacobi_os_round<<<grid, kJT, 0, st>>>(B, J, m, k % rounds, mr);
       }
       h->launches += 2 * rounds;
-      int hr = 1;
-      e = cudaMemcpyAsync(&hr, rot, sizeof(int), cudaMemcpyDeviceToHost, st);
+      unsigned hr = 0;
+      e = cudaMemcpyAsync(&hr, mr, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) break;
-      converged = hr == 0;
+      float r2;
+      std::memcpy(&r2, &hr, sizeof(r2));
+      done = r2 <= target;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (e != cudaSuccess) {
       release();
-      dfree(Rv, st); dfree(Rvt, st);
       return check_cuda(h, e, "virtual rotation (Jacobi)");
     }
-    debug_phase(h, "  virtual rotation: Jacobi eigenvectors of the virtual block");
+    debug_phase(h, exact ? "  virtual rotation: Jacobi to the rounding level" : "  virtual rotation: Jacobi to 1e-6");
   }
-  k_build_rv<<<256, 256, 0, st>>>(V0, No, Nv, Rv, Rvt, W3);
+  k_build_rv<<<256, 256, 0, st>>>(h->jJ, No, Nv, h->Rv, h->Rvt, W3);
   // Farr = W3^T Fsemi W3
   Gemm64 g{};
   g.alpha = 1.0; g.beta = 0.0; g.batch = 1; g.M = N; g.N = N; g.K = N;
@@ -342,15 +375,18 @@ esmp2_status ensure_vrot(esmp2_handle *h) {
   k_clean_arrow<<<256, 256, 0, st>>>(h->Farr, No, Nv);
   k_to_f32<<<64, 256, 0, st>>>(h->Farr, h->F32arr, (int64_t)N * N);
   h->launches += 5;
+  // digit planes of an earlier (less converged) rotation are stale
+  dfree(h->Rvdig, st);
+  dfree(h->Rvtdig, st);
+  h->Rvdig = h->Rvtdig = nullptr;
   release();
-  h->Rv = Rv;
-  h->Rvt = Rvt;
+  h->vrot_level = want;
   return check_cuda(h, cudaGetLastError(), "virtual rotation");
 }
 
 esmp2_status ensure_arrow(esmp2_handle *h) {
   if (h->arrow_ready) return ESMP2_OK;
-  esmp2_status s = ensure_vrot(h);
+  esmp2_status s = ensure_vrot(h, true);
   if (s) return s;
   const int No = h->d.No, Nv = h->d.Nv;
   const size_t n = (size_t)h->d.n, S = (size_t)5 * No * No;

@@ -1332,7 +1332,7 @@ void packed_accumulate(esmp2_handle *h, double *x64) {
 // diagonal of F_vv in the rotated basis and the per-slice occupied part of the diagonal of A.
 esmp2_status packed_rj_setup(esmp2_handle *h) {
   if (h->rj_ready) return ESMP2_OK;
-  esmp2_status s = ensure_vrot(h);
+  esmp2_status s = ensure_vrot(h, false);
   if (s) return s;
   const Packed &L = h->pk;
   const int No = L.No, Nv = L.Nv, Nvp = L.Nvp, N = h->d.N;

@@ -137,6 +137,9 @@ struct esmp2_handle {
   bool arrow_ready = false;
   bool arrowv = false;      // the current call works in the reduced-cost basis
   double *Rv = nullptr, *Rvt = nullptr;  // Nv x Nv virtual rotation (t' fixed) and its transpose
+  int vrot_level = 0;       // 0 none, 1 to 1e-6 (preconditioner), 2 to the rounding level
+  double *jB = nullptr, *jJ = nullptr;  // Jacobi state (rotated rows, accumulated rotation)
+  unsigned *jflag = nullptr;
   void *Rvdig = nullptr, *Rvtdig = nullptr;  // their digit planes (float64-exact rotations)
   int eRv = 0, eRvt = 0;
   double *Farr = nullptr;   // N x N Fock matrix in that basis
@@ -229,7 +232,7 @@ esmp2_status packed_rj_setup(esmp2_handle *h);
 void k_finalize_ext(const double *red, int nparts, double *slots, int mode, cudaStream_t st);
 esmp2_status packed_rj_init(esmp2_handle *h, const double *r64, int grid);
 esmp2_status packed_rj_step(esmp2_handle *h, int grid);
-esmp2_status ensure_vrot(esmp2_handle *h);
+esmp2_status ensure_vrot(esmp2_handle *h, bool exact);
 float *packed_p(esmp2_handle *h);
 void packed_accumulate(esmp2_handle *h, double *x64);
 double packed_wdot(esmp2_handle *h, const float *u, const float *v);

@@ -46,8 +46,8 @@ template <bool TF32> struct Kind {
 };
 constexpr int NTHREADS = 320;
 // dynamic shared memory per CTA: the 232448-byte opt-in limit less room for the kernel's
-// static shared memory (barriers, TMEM address, flags)
-constexpr int SMEM_MAX = 232448 - 2048;
+// static shared memory (barriers, TMEM address, flags, the epilogue's 10 KB staging tile)
+constexpr int SMEM_MAX = 232448 - 2048 - 10240;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES], acc_full[2], acc_empty[2], pbar;
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
+  // bf16 transposed output: per epilogue warp one 16-column x 32-row chunk, turned so that each
+  // lane stores 16 consecutive rows of one column as two 16-byte vectors
+  __shared__ __align__(16) __nv_bfloat16 stg[8][16][40];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x % g.nN, group = gridDim.x / g.nN, gi = blockIdx.x / g.nN;
   const int b0 = nt * g.Nt, nvalid = min(g.Nt, g.Nv - b0), nmma = (nvalid + 15) & ~15;
@@ -272,6 +275,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t r = m * BM + quarter * 32 + lane;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 256);
       const bool normal = r < g.rows_normal;
+      // the warp's 32 rows form one run of a transposed slice (same slice, consecutive rows
+      // starting on a multiple of 8): the staged 16-byte stores apply
+      bool run = false;
+      if (g.PT16) {
+        const int64_t r0 = m * BM + quarter * 32, q0 = r0 - g.rows_normal;
+        run = r0 >= g.rows_normal && r0 + 31 < g.rows && (q0 % g.Nv) + 31 < g.Nv && (q0 % g.Nv) % 8 == 0;
+      }
       float *dst = nullptr;     // column b (< Nv) of this row
       __nv_bfloat16 *dst16 = nullptr;
       int64_t tpitch = 1;
@@ -300,9 +310,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               v[q] = (q < mcol && vg_valid(rcode, a, rc)) ? v[q] / ((g.lam[a] + rlam) - rocc) : 0.f;
             }
           }
+          if (run) {   // all 32 lanes here (every row of the warp is in range)
+            __nv_bfloat16(*st)[40] = stg[warp - 2];
+            __syncwarp();
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (q < mcol) dst16[(int64_t)(bc + q) * tpitch] = __float2bfloat16_rn(v[q]);
+            for (int q = 0; q < 16; ++q) st[q][lane] = __float2bfloat16_rn(v[q]);
+            __syncwarp();
+            const int j = lane >> 1, hh = (lane & 1) * 16;   // column bc + j, rows hh .. hh + 15 of the run
+            if (j < mcol) {
+              const uint4 *src = reinterpret_cast<const uint4 *>(&st[j][hh]);
+              uint4 *out = reinterpret_cast<uint4 *>(dst16 - lane + (int64_t)(bc + j) * tpitch + hh);
+              out[0] = src[0];
+              out[1] = src[1];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (q < mcol) dst16[(int64_t)(bc + q) * tpitch] = __float2bfloat16_rn(v[q]);
+          }
         } else if (normal && mcol == 16) {
           float4 *d4 = reinterpret_cast<float4 *>(dst + bc);
 #pragma unroll

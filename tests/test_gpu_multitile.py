@@ -71,6 +71,7 @@ def test_c2_rhs_energy_and_rates(record_property):
     import torch
     from paper_2003_12923_gb300 import esmp2
     No, Nv, seed = 20, 200, 1
+    g = _golden("e2_c2")
     inst = synth.make_instance(No, Nv, seed, sigma_off=1e-3)
     prep = top.prepare(inst)
     oc = o2.O2(prep)
@@ -81,7 +82,6 @@ def test_c2_rhs_energy_and_rates(record_property):
     got = b[torch.from_numpy(idx).cuda()].cpu().numpy()
     assert float(np.abs(got - ref).max()) <= 1e-12 * float(np.abs(ref).max())
     e2s_ref, _ = oc.e2_s()
-    g = _golden("e2_c2")
     assert abs(g["E2_S"] - e2s_ref) < 1e-13
     info = h.solve(tol=1e-10, maxit=3000, precision=esmp2.FP64)
     assert info["rel_residual"] <= 1e-10
