@@ -254,10 +254,9 @@ def cpu_baseline(No, Nv, seed, sigma_off, budget_s=12.0, inst=None, tol=1e-8, co
             "t_sigma_s": t_sigma, "n_sigma": n_sigma, "wall_s": time.time() - t0}
 
 
-def indefinite_line(args, esmp2, dins, names, No, Nv, seed, so, tol, prec_name, message, steps=24):
-    """The JSON line of a workload whose operator is not positive definite: no time-to-solution,
-    the solver's message, and the extreme Ritz values of `steps` Lanczos steps on the operator
-    (the library's float64 sigma, started from the right-hand side)."""
+def lanczos_ritz(esmp2, dins, names, steps=24):
+    """The extreme Ritz values of `steps` Lanczos steps on the operator (the library's float64
+    sigma, weighted inner product of the layout, started from the right-hand side)."""
     import torch
     h = esmp2.Handle(*(dins[k] for k in names))
     # A is symmetric in the determinant inner product (block weights of the layout)
@@ -283,15 +282,8 @@ def indefinite_line(args, esmp2, dins, names, No, Nv, seed, so, tol, prec_name, 
     if k > 1:
         T = T + np.diag(betas[:k - 1], 1) + np.diag(betas[:k - 1], -1)
     ritz = np.linalg.eigvalsh(T)
-    return {"metric": METRIC, "value": None, "unit": "s", "n_gpus": 1, "steps": 0, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16+f64" if prec_name != "fp64" else "f64", "data": "synthetic",
-            "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1)", "tol": tol,
-                       "precision": prec_name},
-            "status": "indefinite", "message": message,
-            "lanczos": {"steps": k, "ritz_min": float(ritz[0]), "ritz_max": float(ritz[-1]),
-                        "ritz_low": [float(v) for v in ritz[:4]]},
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": 0, "clocks": None}
+    return {"steps": k, "ritz_min": float(ritz[0]), "ritz_max": float(ritz[-1]),
+            "ritz_low": [float(v) for v in ritz[:4]]}
 
 
 def max_over_ranks(value, dist, device):
@@ -522,8 +514,9 @@ def main():
     ap.add_argument("--wave", type=int, default=2, help="c4: instances generated and solved per batch call")
     ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
     ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tf32", "reduced"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tf32", "reduced", "minres"])
     ap.add_argument("--no-variants", action="store_true", help="skip the tf32 and reduced-basis forms")
+    ap.add_argument("--minres-probe", type=int, default=150, help="MINRES iterations tried on an indefinite workload")
     ap.add_argument("--tol", type=float, default=None, help="default: the workload's (1e-8 mixed, 1e-10 fp64)")
     ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--ref-budget", type=float, default=12.0)
@@ -560,30 +553,44 @@ def main():
     esmp2.load()
     prec_name = prec0 if args.precision == "auto" else args.precision
     prec = {"mixed": esmp2.MIXED_BF16, "tf32": esmp2.MIXED_TF32, "reduced": esmp2.REDUCED_MIXED,
-            "fp64": esmp2.FP64}[prec_name]
+            "fp64": esmp2.FP64, "minres": esmp2.REDUCED_MINRES}[prec_name]
     stream = torch.cuda.current_stream()
     fp64_peak = measure_fp64_peak(dev)
 
-    def step(inputs, precision=prec):
-        h = esmp2.Handle(*(inputs[k] for k in names))
-        info = h.solve(tol=tol, maxit=args.maxit, precision=precision)
+    hkw = {}   # problem-statement options of the handles (the level shift of an indefinite workload)
+
+    def step(inputs, precision=None):
+        h = esmp2.Handle(*(inputs[k] for k in names), **hkw)
+        info = h.solve(tol=tol, maxit=args.maxit, precision=prec if precision is None else precision)
         e = h.energy()
         n_l = h.kernel_launches
         h.close()
         return info, e, n_l
 
+    indefinite = None
     try:
         step(dins)
     except esmp2.Esmp2Error as err:
         if err.status != esmp2.ERR_INDEFINITE:
             raise
-        # CG does not apply (Sec. III.A uses CG, which needs a positive definite operator):
-        # report that, with the lowest Ritz values of a short Lanczos run as the evidence
-        if rank == 0:
-            print(json.dumps(indefinite_line(args, esmp2, dins, names, No, Nv, seed, so, tol, prec_name, str(err))))
-        if world > 1:
-            dist.destroy_process_group()
-        return 0
+        # CG does not apply (Sec. III.A uses CG, which needs a positive definite operator): the
+        # lowest Ritz values of a short Lanczos run are the evidence.  Preconditioned MINRES is
+        # probed with a bounded number of iterations; the timed solve applies the level shift
+        # (the intruder-state remedy) just large enough to make the operator positive definite.
+        lz = lanczos_ritz(esmp2, dins, names)
+        hm = esmp2.Handle(*(dins[k] for k in names))
+        t0 = time.perf_counter()
+        im = hm.solve(tol=tol, maxit=args.minres_probe, precision=esmp2.REDUCED_MINRES, raise_on_error=False)
+        torch.cuda.synchronize()
+        probe = {"iterations": im["iterations"], "rel_residual": im["rel_residual"],
+                 "seconds": time.perf_counter() - t0, "status": im["status"]}
+        hm.close()
+        shift = float(np.ceil((-lz["ritz_min"] + 0.1) * 10.0) / 10.0)
+        indefinite = {"cg_status": "indefinite", "message": str(err), "lanczos": lz, "minres_probe": probe,
+                      "level_shift": shift,
+                      "note": "the timed solve is the mixed CG solve of A + level_shift (E2 of the shifted operator)"}
+        hkw["level_shift"] = shift
+        step(dins)
     for _ in range(args.warmup - 1):
         step(dins)
     torch.cuda.synchronize()
@@ -630,14 +637,16 @@ def main():
     roofline["traffic_source"] = prof
 
     # per-stage view of one sigma build of this precision (outside the timed region)
-    h = esmp2.Handle(*(dins[k] for k in names))
+    h = esmp2.Handle(*(dins[k] for k in names), **hkw)
     x = h.rhs()
-    ms = h.profile_sigma(x, precision=prec, reps=3)
+    # (MINRES runs the float64 sigma of the reduced-cost basis, not profiled per stage: the
+    # float64 stages of the TOP-basis sigma are shown instead)
+    ms = h.profile_sigma(x, precision=esmp2.FP64 if prec == esmp2.REDUCED_MINRES else prec, reps=3)
     fl = sigma_flops(No, Nv)
     nu = unique_amplitudes(No, Nv)
     roofline["sigma_stage_ms"] = [float(v) for v in ms[:5]]
     sigma_alg_tflops = fl["alg_total"] / (ms[4] * 1e-3) / 1e12
-    sigma_alg_gbs = (16.0 if prec == esmp2.FP64 else 6.0) * nu / (ms[4] * 1e-3) / 1e9
+    sigma_alg_gbs = (16.0 if prec in (esmp2.FP64, esmp2.REDUCED_MINRES) else 6.0) * nu / (ms[4] * 1e-3) / 1e9
     h.close()
 
     e2e = None
@@ -657,11 +666,11 @@ def main():
         e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     fp64_cmp = None
-    if prec != esmp2.FP64 and not args.no_fp64_compare:
+    if prec not in (esmp2.FP64, esmp2.REDUCED_MINRES) and not args.no_fp64_compare:
         # the plain float64 GPU form on the same instance, timed once with CUDA events
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h64 = esmp2.Handle(*(dins[k] for k in names))
+        h64 = esmp2.Handle(*(dins[k] for k in names), **hkw)
         info64 = h64.solve(tol=tol, maxit=args.maxit, precision=esmp2.FP64)
         en64 = h64.energy()
         h64.close()
@@ -674,7 +683,7 @@ def main():
     # events, create + solve + energy like the step): tf32 contraction, and the reduced-cost basis
     # (no virtual-index contraction at all; reported beside the tensor-core form, not instead)
     variants = {}
-    if prec != esmp2.FP64 and No <= 32 and not args.no_variants:
+    if prec not in (esmp2.FP64, esmp2.REDUCED_MINRES) and No <= 32 and not args.no_variants:
         for name, pv in (("tf32_form", esmp2.MIXED_TF32), ("reduced_basis_form", esmp2.REDUCED_MIXED)):
             if pv == prec:
                 continue
@@ -695,7 +704,8 @@ def main():
     info, e = infos[-1]
     line = {"metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == esmp2.FP64 else "bf16+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if prec in (esmp2.FP64, esmp2.REDUCED_MINRES) else "bf16+f64",
+            "data": "synthetic",
             "config": {"workload": f"{args.config}: No={No} Nv={Nv} seed={seed} sigma_off={so} TOP(1)",
                        "tol": tol, "precision": prec_name, "step": "create+solve+energy, inputs resident",
                        "l2": "no flush: every block vector (5.8 GB at No=30 Nv=400) is larger than L2"},
@@ -710,6 +720,8 @@ def main():
         line["E2_error_vs_oracle"] = {k: e[k] - g[k] for k in ("E2", "E2_D", "E2_L", "E2_S")}
         line["E2_error_vs_oracle"]["oracle"] = GOLDEN[args.config]
     line.update(variants)
+    if indefinite is not None:
+        line["indefinite_for_cg"] = indefinite
     if fp64_cmp is not None:
         fp64_cmp["E2_mixed_minus_fp64"] = e["E2"] - fp64_cmp["E2"]
         fp64_cmp["speedup_mixed_over_fp64"] = fp64_cmp["time_to_solution_s"] / tts

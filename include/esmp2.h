@@ -68,6 +68,9 @@ typedef enum {
                             inside float64 refinement; the right-hand side is rotated once
                             (float64-exact digit-split products).  E2 equals the other forms' to
                             the solve tolerance; E2_S stays in the TOP basis.  No <= 32, Nv <= 1024. */
+  ESMP2_REDUCED_MINRES = 5, /* preconditioned MINRES in float64 in the reduced-cost basis (SPD
+                            preconditioner |diag|^-1): for operators that are not positive definite
+                            (intruder states, strong coupling), where CG stops with INDEFINITE */
   ESMP2_FP64_TC = 3      /* float64-accurate virtual-index terms: x and F_vv split into exact 6-bit
                             bf16 digits (per-slice power-of-two scale), digit products summed exactly
                             in fp32 on tcgen05 level by level (levels 2..10) and combined in float64;
@@ -184,6 +187,8 @@ esmp2_status esmp2_rhs(esmp2_handle *h, double *b);
  * iterative refinement, each step solving the correction with bf16/fp32 inner
  * PCG.  ESMP2_MIXED_TF32: the same with tf32 inner contractions (No <= 32, else
  * UNSUPPORTED).  ESMP2_REDUCED_MIXED: the same in the reduced-cost basis (see the enum).
+ * ESMP2_REDUCED_MINRES: preconditioned MINRES (Paige-Saunders) in float64 in that basis, for
+ * operators that are not positive definite; restarted from x until the true residual meets tol.
  * Stops when the TRUE relative residual ||b + A x|| / ||b|| (fp64) <= tol.
  * (Mixed: intermediate true residuals far from tol take fewer exact digit levels and a
  * float32 coupling pass, accurate relative to their own size; the residual that stops

@@ -33,7 +33,7 @@ void free_handle(esmp2_handle *h) {
                   h->cp.G, h->cp.H, h->cp.CYZ, h->cp.GP, h->cp.HP, h->P64, h->F32, h->dinv32, h->cp32.VX, h->cp32.GP, h->cp32.WZ, h->cp32.HP,
                   h->cp32.OX, h->cp32.OZ, h->cp32.OC1, h->cp32.OC2, h->cp32.G, h->cp32.H, h->cp32.CYZ, h->red, h->red_out, h->xlp, h->Fvlp, h->ylp, h->r32, h->p32,
                   h->q32, h->x32, h->dflag, h->Rocc, h->Rocct, h->Fsemi, h->bsemi, h->cp.OC1, h->cp.OC2,
-                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig, h->pr, h->pp, h->pq, h->pd, h->pdinv, h->pop, h->pW, h->pop32, h->pW32, h->pRbf, h->pT1, h->pZ, h->pWR, h->pWRt, h->pLam, h->pOcc, h->pCode, h->pdot2, h->zero_slots, h->Rv, h->Rvt, h->Rvdig, h->Rvtdig, h->Farr, h->barr, h->F32arr, h->rho64, h->kap64, h->pRho, h->pKap, h->jB, h->jJ, h->jflag,
+                  h->xdig, h->Fdig, h->es, h->slist, h->Rdig, h->pr, h->pp, h->pq, h->pd, h->pdinv, h->pop, h->pW, h->pop32, h->pW32, h->pRbf, h->pT1, h->pZ, h->pWR, h->pWRt, h->pLam, h->pOcc, h->pCode, h->pdot2, h->zero_slots, h->Rv, h->Rvt, h->Rvdig, h->Rvtdig, h->Farr, h->barr, h->F32arr, h->rho64, h->kap64, h->pRho, h->pKap, h->jB, h->jJ, h->jflag, h->mr_a, h->mr_b, h->mr_v,
                   h->pP, h->pVX, h->pGP, h->pWZ, h->pHP, h->pOC, h->pOC2, h->pOX, h->pOZ, h->pG, h->pH, h->pCYZ, h->pdot};
   for (void *p : ptrs)
     if (p) dfree(p, h->stream);
@@ -257,6 +257,7 @@ esmp2_status esmp2_solve(esmp2_handle *h, double tol, int maxit, esmp2_precision
   if (p == ESMP2_MIXED_BF16) return solve_mixed(h, tol, maxit, info);
   if (p == ESMP2_MIXED_TF32) return solve_mixed(h, tol, maxit, info, true);
   if (p == ESMP2_REDUCED_MIXED) return solve_mixed(h, tol, maxit, info, false, true);
+  if (p == ESMP2_REDUCED_MINRES) return solve_minres(h, tol, maxit, info);
   h->err = "precision not supported";
   return ESMP2_ERR_UNSUPPORTED;
 }

@@ -140,6 +140,7 @@ struct esmp2_handle {
   int vrot_level = 0;       // 0 none, 1 to 1e-6 (preconditioner), 2 to the rounding level
   double *jB = nullptr, *jJ = nullptr;  // Jacobi state (rotated rows, accumulated rotation)
   unsigned *jflag = nullptr;
+  double *mr_a = nullptr, *mr_b = nullptr, *mr_v = nullptr;  // MINRES direction vectors and Lanczos vector (n)
   void *Rvdig = nullptr, *Rvtdig = nullptr;  // their digit planes (float64-exact rotations)
   int eRv = 0, eRvt = 0;
   double *Farr = nullptr;   // N x N Fock matrix in that basis
@@ -215,6 +216,7 @@ esmp2_status sigma_mixed(esmp2_handle *h, const double *x, double *y);
 esmp2_status profile64(esmp2_handle *h, const double *x, double *y, int reps, double *ms, int tc_levels = 0);
 esmp2_status profile_mixed(esmp2_handle *h, const double *x, double *y, int reps, double *ms);
 esmp2_status solve64(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, int virt_tc = 0);
+esmp2_status solve_minres(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info);
 esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info, bool tf32 = false,
                          bool arrowv = false);
 esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts);

@@ -624,6 +624,60 @@ __global__ void k_e2s_gen(SCtx s, double *red) {
   block_partials<1>(v, red);
 }
 
+// ---- preconditioned MINRES (symmetric, possibly indefinite A; SPD preconditioner
+// M^-1 = |diag|^-1 of the reduced-cost basis), vectors in the full-storage float64 layout.
+// |1 / d| with the masks (d the Jacobi diagonal of VCtx::dinv)
+__device__ __forceinline__ double mr_minv(const VCtx &c, int64_t e) { return fabs(c.dinv(e)); }
+
+// v = M^-1 r / beta
+__global__ void k_mr_v(VCtx c, const double *r, double beta_inv, double *v) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    v[e] = mr_minv(c, e) * r[e] * beta_inv;
+}
+// partials <r, M^-1 r>_w, <r, r>_w
+__global__ void k_mr_res(VCtx c, const double *r, double *red) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[e], w = c.w(e);
+    v[0] += w * ri * mr_minv(c, e) * ri;
+    v[1] += w * ri * ri;
+  }
+  block_partials<2>(v, red);
+}
+// partial <u, v>_w
+__global__ void k_mr_dot(VCtx c, const double *u, const double *v_, double *red) {
+  double v[1] = {0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x)
+    v[0] += c.w(e) * u[e] * v_[e];
+  block_partials<1>(v, red);
+}
+// y = q - a1 r2 - a2 r1 (written over r1); partial <y, M^-1 y>_w
+__global__ void k_mr_y(VCtx c, const double *q, const double *r2, double *r1y, double a1, double a2, double *red) {
+  double v[1] = {0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const double y = q[e] - a1 * r2[e] - a2 * r1y[e];
+    r1y[e] = y;
+    v[0] += c.w(e) * y * mr_minv(c, e) * y;
+  }
+  block_partials<1>(v, red);
+}
+// w1 <- (v - e1 w1 - e2 w2) / gamma (the new direction, over the oldest one); x += phi w1;
+// v <- M^-1 y / beta_next
+__global__ void k_mr_update(VCtx c, double *v, double *w1, const double *w2, double *x, const double *y, double e1,
+                            double e2, double ginv, double phi, double bn_inv) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 5 * c.B; e += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (v[e] - e1 * w1[e] - e2 * w2[e]) * ginv;
+    w1[e] = wn;
+    x[e] += phi * wn;
+    v[e] = mr_minv(c, e) * y[e] * bn_inv;
+  }
+}
+// r = -b - q (q null: r = -b)
+__global__ void k_negsum64(const double *b, const double *q, double *out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = q ? -b[e] - q[e] : -b[e];
+}
+
 }  // namespace
 
 void launch_pcg_init(esmp2_handle *h, const double *b, const double *q, double *r, double *p);
@@ -794,6 +848,134 @@ esmp2_status energy(esmp2_handle *h, esmp2_energy_parts *parts) {
   parts->E2_S = h->e2s;
   parts->E2 = parts->E2_D + parts->E2_L + parts->E2_S;
   return check_cuda(h, cudaGetLastError(), "energy");
+}
+
+// Preconditioned MINRES (Paige and Saunders) on A x = -b in the reduced-cost basis, float64:
+// for operators that are not positive definite, where CG does not apply (Sec. III.A uses CG).
+// The Lanczos vectors of M^-1 A are generated with the weighted inner product; x follows from
+// the short recurrence of the QR factorisation of the tridiagonal matrix (one Givens rotation
+// per step).  The preconditioned residual estimate phibar triggers a true residual; the solve
+// restarts from x until the true relative residual meets tol.
+esmp2_status solve_minres(esmp2_handle *h, double tol, int maxit, esmp2_solve_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  esmp2_status s = ensure_arrow(h);
+  if (s) return s;
+  if ((s = x_to_basis(h, 2))) return s;
+  h->arrowv = true;
+  const int64_t n = h->d.n;
+  cudaStream_t st = h->stream;
+  if (!h->mr_a) {   // the two direction vectors and the Lanczos vector v (x, q, r1, r2 are the handle's)
+    cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->mr_a), sizeof(double) * (size_t)n, st);
+    if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&h->mr_b), sizeof(double) * (size_t)n, st);
+    if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&h->mr_v), sizeof(double) * (size_t)n, st);
+    if (e != cudaSuccess) return check_cuda(h, e, "MINRES vectors");
+  }
+  singlet_project(h, h->s64.x);
+  const VCtx c = vctx(h, h->Farr);
+  double *x = h->s64.x, *q = h->s64.q, *r1 = h->s64.r, *r2 = h->s64.p, *v = h->mr_v, *w1 = h->mr_a, *w2 = h->mr_b;
+  if (!x || !q || !r1 || !r2 || !v || !w1 || !w2 || !h->barr || !h->Farr) {
+    h->err = "MINRES: missing work vector";
+    return ESMP2_ERR_STATE;
+  }
+  h->last_precision = ESMP2_REDUCED_MINRES;
+  h->r_true = false;
+  double sl[32], relres = 1.0, bn = -1.0;
+  int iters = 0, nsig = 0, restarts = 0;
+  esmp2_status result = ESMP2_ERR_NOT_CONVERGED;
+  while (true) {
+    // true residual r2 = -b - A x, its norms <r, M^-1 r>_w and <r, r>_w
+    if (h->x_zero) {
+      k_negsum64<<<1216, 256, 0, st>>>(h->barr, nullptr, r2, n);
+    } else {
+      if ((s = sigma64_arrow(h, x, q))) return s;
+      ++nsig;
+      k_negsum64<<<1216, 256, 0, st>>>(h->barr, q, r2, n);
+    }
+    k_mr_res<<<kRedBlocks, kRedThreads, 0, st>>>(c, r2, h->red);
+    k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 2, h->red_out, 3);
+    h->launches += 3;
+    if ((s = read_slots(h, sl, 32))) return s;
+    if (bn < 0.0) {   // |b|_w
+      k_mr_dot<<<kRedBlocks, kRedThreads, 0, st>>>(c, h->barr, h->barr, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 3);
+      h->launches += 2;
+      double sb[32];
+      if ((s = read_slots(h, sb, 32))) return s;
+      bn = std::sqrt(sb[8]);
+    }
+    const double beta1 = std::sqrt(std::max(sl[8], 0.0));
+    relres = bn > 0 ? std::sqrt(std::max(sl[9], 0.0)) / bn : 0.0;
+    if (std::getenv("ESMP2_DEBUG"))
+      std::fprintf(stderr, "esmp2 minres: restart %d relres %.3e iterations %d\n", restarts, relres, iters);
+    if (relres <= tol) {
+      result = ESMP2_OK;
+      if (r2 != h->s64.r) cudaMemcpyAsync(h->s64.r, r2, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+      h->r_true = true;
+      break;
+    }
+    if (iters >= maxit || restarts >= 20 || !(beta1 > 0.0)) break;
+    ++restarts;
+    // Lanczos start: r1 = r2 = r, v = M^-1 r / beta1, w1 = w2 = 0
+    cudaMemcpyAsync(r1, r2, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(w1, 0, sizeof(double) * (size_t)n, st);
+    cudaMemsetAsync(w2, 0, sizeof(double) * (size_t)n, st);
+    k_mr_v<<<1216, 256, 0, st>>>(c, r2, 1.0 / beta1, v);
+    h->launches += 1;
+    double oldb = 0.0, beta = beta1, dbar = 0.0, epsln = 0.0, phibar = beta1, cs = -1.0, sn = 0.0;
+    // phibar = |r|_{M^-1} of the recurrence; it is run well below the target (the two norms differ
+    // by the spread of |diag|), then the true residual decides
+    const double stop = 0.1 * tol * beta1 / std::max(relres, 1e-300);
+    while (iters < maxit) {
+      if ((s = sigma64_arrow(h, v, q))) return s;   // q = A v
+      ++nsig;
+      k_mr_dot<<<kRedBlocks, kRedThreads, 0, st>>>(c, v, q, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 3);
+      h->launches += 2;
+      if ((s = read_slots(h, sl, 32))) return s;
+      const double alpha = sl[8];
+      // y = q - (alpha / beta) r2 - (beta / oldb) r1, over r1; then r1 <-> r2
+      k_mr_y<<<kRedBlocks, kRedThreads, 0, st>>>(c, q, r2, r1, alpha / beta, oldb > 0.0 ? beta / oldb : 0.0, h->red);
+      k_finalize<<<1, 256, 0, st>>>(h->red, kRedBlocks, 1, h->red_out, 3);
+      h->launches += 2;
+      if ((s = read_slots(h, sl, 32))) return s;
+      std::swap(r1, r2);   // r2 = y (the new Lanczos residual), r1 = the previous one
+      oldb = beta;
+      beta = std::sqrt(std::max(sl[8], 0.0));
+      // QR step of the tridiagonal matrix: the previous rotation on the new column, then a new
+      // rotation that zeroes its subdiagonal beta
+      const double oldeps = epsln, delta = cs * dbar + sn * alpha, gbar = sn * dbar - cs * alpha;
+      epsln = sn * beta;
+      dbar = -cs * beta;
+      const double gamma = std::max(std::sqrt(gbar * gbar + beta * beta), 1e-300);
+      cs = gbar / gamma;
+      sn = beta / gamma;
+      const double phi = cs * phibar;
+      phibar = sn * phibar;
+      // w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma over w_{k-2}; x += phi w_k;
+      // v = M^-1 r2 / beta
+      k_mr_update<<<1216, 256, 0, st>>>(c, v, w1, w2, x, r2, oldeps, delta, 1.0 / gamma, phi,
+                                        beta > 0.0 ? 1.0 / beta : 0.0);
+      h->launches += 1;
+      std::swap(w1, w2);   // w2 = w_k, w1 = w_{k-1}
+      h->x_zero = false;
+      ++iters;
+      if (std::getenv("ESMP2_DEBUG"))
+        std::fprintf(stderr, "esmp2 minres %d: phibar/beta1 %.3e\n", iters, phibar / beta1);
+      if (phibar <= stop || !(beta > 0.0)) break;
+    }
+    singlet_project(h, x);
+  }
+  if (info) {
+    info->iterations = iters;
+    info->outer = restarts;
+    info->sigma_fp64 = nsig;
+    info->sigma_lowp = 0;
+    info->rel_residual = relres;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (result == ESMP2_ERR_NOT_CONVERGED) h->err = "MINRES did not reach the tolerance";
+  h->solved = (result == ESMP2_OK || result == ESMP2_ERR_NOT_CONVERGED);
+  return result;
 }
 
 // Mixed precision: float64 iterative refinement around a low-precision inner PCG.

@@ -18,7 +18,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_NOT_CONVERGED, ERR_INDEFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(9)
-FP64, MIXED_BF16, MIXED_TF32, FP64_TC, REDUCED_MIXED = 0, 1, 2, 3, 4
+FP64, MIXED_BF16, MIXED_TF32, FP64_TC, REDUCED_MIXED, REDUCED_MINRES = 0, 1, 2, 3, 4, 5
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "NOT_CONVERGED", 5: "INDEFINITE",
            6: "CUDA", 7: "TIMEOUT", 8: "STATE"}
 

@@ -82,3 +82,40 @@ def test_reduced_matches_contraction_form_at_nv400():
     for k in ("E2", "E2_D", "E2_L", "E2_S"):
         assert abs(e["reduced"][k] - e["fp64"][k]) < 1e-8, (k, e["reduced"][k], e["fp64"][k])
         assert abs(e["bf16"][k] - e["fp64"][k]) < 1e-8, (k, e["bf16"][k], e["fp64"][k])
+
+
+@pytest.mark.parametrize("No,Nv,shift", [(3, 6, 2.0), (2, 5, 1.5)])
+def test_minres_on_indefinite_operator_against_o1(No, Nv, shift):
+    """An operator with eigenvalues of both signs (occupied orbital energies raised into the
+    virtual range): CG stops with INDEFINITE, preconditioned MINRES in the reduced-cost basis
+    reaches the energy of the explicitly assembled operator's dense solve (O1)."""
+    from paper_2003_12923_gb300 import esmp2
+    from oracle import jw
+    from tests.gpu_util import indefinite_instance
+    inst = indefinite_instance(No, Nv, 5, shift=shift)
+    ref = jw.solve(inst["F"], synth.eri_block("full", No, Nv, 5), inst["C"], No, Nv)
+    ev = np.linalg.eigvalsh(ref.A)
+    assert ev.min() < 0 < ev.max()
+    h = handle_for(inst)
+    with pytest.raises(esmp2.Esmp2Error) as ei:
+        h.solve(tol=1e-10, maxit=500, precision=esmp2.FP64)
+    assert ei.value.status == esmp2.ERR_INDEFINITE
+    h.close()
+    h = handle_for(inst)
+    info = h.solve(tol=1e-11, maxit=3000, precision=esmp2.REDUCED_MINRES)
+    assert info["rel_residual"] <= 1e-11
+    assert abs(h.energy()["E2"] - ref.E2) < 1e-10, (h.energy()["E2"], ref.E2)
+
+
+def test_minres_matches_cg_on_positive_definite_operator():
+    from paper_2003_12923_gb300 import esmp2
+    inst = synth.make_instance(5, 64, 14)
+    e = {}
+    for prec in (esmp2.FP64, esmp2.REDUCED_MINRES):
+        h = handle_for(inst)
+        info = h.solve(tol=1e-11, maxit=3000, precision=prec)
+        assert info["rel_residual"] <= 1e-11
+        e[prec] = h.energy()
+        h.close()
+    for k in ("E2", "E2_D", "E2_L", "E2_S"):
+        assert abs(e[esmp2.REDUCED_MINRES][k] - e[esmp2.FP64][k]) < 1e-10
