@@ -40,7 +40,9 @@ E2_TASKS = {
     "e2_3_300": (3, 300, 22, 1e-3, 1e-9),
     "e2_c2": (20, 200, 1, 1e-3, 1e-7),
 }
-C5 = (16, 160, 5, 1e-3, 1e-8)
+# the derivatives are first order in the solution's error (2 x.db + x.dA x at an approximate x),
+# so the C5 solve is taken to 1e-11, well below the 1e-6 relative accuracy they are compared at
+C5 = (16, 160, 5, 1e-3, 1e-11)
 GRAD_F = [(0, 0), (3, 3), (20, 20), (0, 1), (2, 9), (0, 16), (5, 40), (17, 30), (16, 170), (100, 101)]
 GRAD_OVOV = [(0, 0, 0, 0), (0, 0, 1, 1), (2, 5, 7, 9), (1, 0, 1, 0), (3, 17, 0, 2), (15, 159, 14, 158),
              (4, 40, 9, 3), (6, 100, 6, 11), (0, 7, 12, 150), (11, 60, 2, 60), (8, 1, 8, 1), (13, 31, 5, 77)]
@@ -83,7 +85,7 @@ def run_grad_c5(task):
     t0 = time.time()
     inst = synth.make_instance(No, Nv, seed, sigma_off=so)
     prep = top.prepare(inst)
-    res = o2.solve(prep, tol=tol, maxit=1000)
+    res = o2.solve(prep, tol=tol, maxit=3000)
     out = _meta(task, No, Nv, seed, so, tol, t0, res)
     out.update({k: float(res[k]) for k in ("E2", "E2_D", "E2_L", "E2_S")})
     x = res["x"]
