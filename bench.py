@@ -377,21 +377,24 @@ def run_batch(args):
             iters.append(r["iterations"])
             launches += int(r["kernel_launches"])
             e2_by_seed[sd] = r["E2"]
-        for (No, Nv, sd), inst, r in zip(wave, insts, res):
-            if (w0 + wave.index((No, Nv, sd))) % args.fp64_every == 0:
-                t0 = time.perf_counter()
-                h = esmp2.Handle(*(torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")))
-                h.solve(tol=args.tol, maxit=args.maxit, precision=esmp2.FP64)
-                e64 = h.energy()["E2"]
-                h.close()
-                torch.cuda.synchronize()
-                t_seq64 += time.perf_counter() - t0
-                w_seq64 += No * No * float(Nv) ** 3
-                e2_diffs.append(abs(r["E2"] - e64))
         del insts
     clocks = clk.stop()
     ktimes = esmp2.kernel_times()
     esmp2.kernel_timing(False)
+    # sequential plain-FP64 solves of every fp64_every-th instance, outside the kernel-timing window
+    for idx in range(0, len(shapes), args.fp64_every):
+        No, Nv, sd = shapes[idx]
+        inst = synth.make_instance(No, Nv, sd, sigma_off=1e-3)
+        t0 = time.perf_counter()
+        h = esmp2.Handle(*(torch.from_numpy(inst[k]).cuda() for k in ("F", "ovov", "ooov", "ovvv", "C")))
+        h.solve(tol=args.tol, maxit=args.maxit, precision=esmp2.FP64)
+        e64 = h.energy()["E2"]
+        h.close()
+        torch.cuda.synchronize()
+        t_seq64 += time.perf_counter() - t0
+        w_seq64 += No * No * float(Nv) ** 3
+        e2_diffs.append(abs(e2_by_seed[sd] - e64))
+        del inst
     est64 = t_seq64 * (w_all / w_seq64) if w_seq64 > 0 else None
     # the reduced-cost basis form of the same batch (no virtual-index contraction), reported
     # beside the tensor-core form
@@ -425,10 +428,10 @@ def run_batch(args):
         dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
         roofline = dict(fams[dom])
         roofline["family"] = dom
-        ent, prof = kernel_traffic(dom)
-        roofline["traffic"] = ent["bytes_per_launch"] if ent else None
-        roofline["traffic_source"] = prof
-        roofline["note"] = "kernel families over the whole batch (fp64 comparison solves included)"
+        # the stored dram capture is of the No=30 Nv=400 workload, not of these instances
+        roofline["traffic"] = None
+        roofline["traffic_source"] = None
+        roofline["note"] = "kernel families over the batch's timed waves"
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
         # O2 on four instances of the batch (sampled sigma elements, extrapolated), scaled to all 64
@@ -515,7 +518,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS) + ["c4"])
-    ap.add_argument("--wave", type=int, default=2, help="c4: instances generated and solved per batch call")
+    ap.add_argument("--wave", type=int, default=16, help="c4: instances generated and solved per batch call")
     ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
     ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tf32", "reduced", "minres"])

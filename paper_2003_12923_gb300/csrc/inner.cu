@@ -189,22 +189,31 @@ __global__ void kp_init(PV pv, const double *r64, const __half *dinv, float *r, 
   cta_partials<2>(v, red);
 }
 
-// x64 (full storage) += d (packed); T, X, Y slices also update their (j, i) partner with -d
-__global__ void kp_acc64(PV pv, double *x, const float *d) {
+// x64 (full storage) += d (packed); T, X, Y slices also update their (j, i) partner with -d.
+// One warp per packed row (slice, a), four consecutive b per lane.
+__global__ void __launch_bounds__(256) kp_acc64(PV pv, double *x, const float *d) {
   const Packed &L = pv.L;
   const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, q4 = L.Nvp >> 2, Nv = L.Nv;
+  for (int64_t row = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * wpb) {
+    const int s = (int)(row / Nv), a = (int)(row % Nv);
     int blk, i, j;
     pv.decode(s, blk, i, j);
     const float *src = d + (int64_t)s * L.SL + (int64_t)a * L.Nvp;
-    double *x1 = x + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
-    double *x2 = x + blk * B + ((int64_t)j * L.No + i) * NvNv + (int64_t)a * L.Nv;
+    double *x1 = x + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * Nv;
+    double *x2 = x + blk * B + ((int64_t)j * L.No + i) * NvNv + (int64_t)a * Nv;
     const bool anti = !(blk == BS || blk == BZ);
-    for (int b = threadIdx.x; b < L.Nv; b += blockDim.x) {
-      const double v = (double)src[b];
-      x1[b] += v;
-      if (anti) x2[b] -= v;
+    for (int c = lane; c < q4; c += 32) {
+      const int b = 4 * c;
+      const float4 v = *reinterpret_cast<const float4 *>(src + b);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (b + k < Nv) {
+          x1[b + k] += (double)vv[k];
+          if (anti) x2[b + k] -= (double)vv[k];
+        }
+      }
     }
   }
 }
@@ -908,24 +917,32 @@ __device__ __forceinline__ void st_bf4(__nv_bfloat16 *p4, float4 v) {
   *reinterpret_cast<uint2 *>(p4) = u;
 }
 
-// start of an inner solve: r = r64 on the packed slots, rb = bf16(r), d = 0; partials <r, r>_w
-__global__ void kp_init_rj(PV pv, const double *r64, float *r, __nv_bfloat16 *rb, float *d, double *red) {
+// start of an inner solve: r = r64 on the packed slots, rb = bf16(r), d = 0; partials <r, r>_w.
+// One warp per packed row (slice, a), four consecutive b per lane.
+__global__ void __launch_bounds__(256) kp_init_rj(PV pv, const double *r64, float *r, __nv_bfloat16 *rb, float *d,
+                                                  double *red) {
   const Packed &L = pv.L;
   const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, q4 = L.Nvp >> 2, Nv = L.Nv;
   float a1 = 0.f;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int s = (int)(row / L.Nv), a = (int)(row % L.Nv);
+  for (int64_t row = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * wpb) {
+    const int s = (int)(row / Nv), a = (int)(row % Nv);
     int blk, i, j;
     pv.decode(s, blk, i, j);
-    const double *src = r64 + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * L.Nv;
+    const double *src = r64 + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * Nv;
     const int64_t e0 = (int64_t)s * L.SL + (int64_t)a * L.Nvp;
     const float w = blk_w(blk);
-    for (int b = threadIdx.x; b < L.Nvp; b += blockDim.x) {
-      const float ri = b < L.Nv ? (float)src[b] : 0.f;
-      r[e0 + b] = ri;
-      rb[e0 + b] = __float2bfloat16_rn(ri);
-      d[e0 + b] = 0.f;
-      a1 += w * ri * ri;
+    for (int c = lane; c < q4; c += 32) {
+      const int b = 4 * c;
+      float4 v;
+      v.x = b < Nv ? (float)src[b] : 0.f;
+      v.y = b + 1 < Nv ? (float)src[b + 1] : 0.f;
+      v.z = b + 2 < Nv ? (float)src[b + 2] : 0.f;
+      v.w = b + 3 < Nv ? (float)src[b + 3] : 0.f;
+      *reinterpret_cast<float4 *>(r + e0 + b) = v;
+      st_bf4(rb + e0 + b, v);
+      *reinterpret_cast<float4 *>(d + e0 + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+      a1 += w * (v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
     }
   }
   double v[1] = {(double)a1};
@@ -1072,22 +1089,29 @@ __global__ void __launch_bounds__(kThreads) kp_proj_s(PV pv, float *z, const flo
   cta_partial((double)dsum, red, base + blockIdx.x);
 }
 
-// Z: masks only (no symmetry between Z slices); weight 2
+// Z: masks only (no symmetry between Z slices); weight 2.  Four consecutive b per thread (Nvp
+// is a multiple of 8, so a float4 never straddles two rows).
 __global__ void kp_proj_z(PV pv, float *z, const float *r, double *red, int64_t base) {
   const Packed &L = pv.L;
-  const int No = L.No, Nv = L.Nv, Nvp = L.Nvp;
-  const int64_t units = (int64_t)L.NN * Nv * Nvp;
-  float *zb = z + L.boff[BZ];
-  const float *rb = r + L.boff[BZ];
+  const int No = L.No, Nv = L.Nv, q4 = L.Nvp >> 2;
+  const int64_t units = (int64_t)L.NN * Nv * q4;
+  float4 *zb = reinterpret_cast<float4 *>(z + L.boff[BZ]);
+  const float4 *rb = reinterpret_cast<const float4 *>(r + L.boff[BZ]);
   float dsum = 0.f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < units; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = e / L.SL;
-    const int ab = (int)(e - s * L.SL), a = ab / Nvp, b = ab % Nvp;
-    const int i = (int)(s / No), j = (int)(s % No);
-    float v = zb[e];
-    if (b >= Nv || !valid_elem(BZ, i, j, a, b)) v = 0.f;
+    const int64_t row = e / q4;   // Z row (slice s = row / Nv, virtual a = row % Nv)
+    const int b0 = (int)(e - row * q4) * 4;
+    const int s = (int)(row / Nv), a = (int)(row - (int64_t)s * Nv);
+    const int i = s / No, j = s - i * No;
+    const bool rowok = j != 0 && !(i == 0 && a == 0);   // the Z masks of valid_elem
+    float4 v = zb[e];
+    const float4 rv = __ldg(rb + e);
+    v.x = (rowok && b0 != 0 && b0 < Nv) ? v.x : 0.f;
+    v.y = (rowok && b0 + 1 < Nv) ? v.y : 0.f;
+    v.z = (rowok && b0 + 2 < Nv) ? v.z : 0.f;
+    v.w = (rowok && b0 + 3 < Nv) ? v.w : 0.f;
     zb[e] = v;
-    dsum += 2.f * v * rb[e];
+    dsum += 2.f * (v.x * rv.x + v.y * rv.y + v.z * rv.z + v.w * rv.w);
   }
   cta_partial((double)dsum, red, base + blockIdx.x);
 }
@@ -1323,7 +1347,7 @@ double packed_wdot(esmp2_handle *h, const float *u, const float *v) {
 }
 
 void packed_accumulate(esmp2_handle *h, double *x64) {
-  kp_acc64<<<2432, 128, 0, h->stream>>>(PV{h->pk}, x64, h->pd);
+  kp_acc64<<<2432, 256, 0, h->stream>>>(PV{h->pk}, x64, h->pd);
   h->launches += 1;
 }
 
@@ -1433,7 +1457,7 @@ esmp2_status packed_rj_init(esmp2_handle *h, const double *r64, int grid) {
   const Packed &L = h->pk;
   PV pv{L};
   cudaStream_t st = h->stream;
-  kp_init_rj<<<grid, 128, 0, st>>>(pv, r64, h->pr, static_cast<__nv_bfloat16 *>(h->pRbf), h->pd, h->red);
+  kp_init_rj<<<grid, 256, 0, st>>>(pv, r64, h->pr, static_cast<__nv_bfloat16 *>(h->pRbf), h->pd, h->red);
   k_finalize_ext(h->red, grid, h->red_out, 5, st);
   h->launches += 2;
   if (esmp2_status s = packed_precond(h)) return s;
