@@ -1009,10 +1009,13 @@ __global__ void __launch_bounds__(kThreads) kp_proj_anti(PV pv, float *z, const 
     const int64_t so = L.boff[BLK] + (int64_t)k * L.SL;
     float *zs = z + so;
     const float *rs = r + so;
+    float rv[4];   // r on the tile (ta, tb), loaded with the z tiles
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int q = ty + 8 * rr, a = ta * kT + q, b = tb * kT + tx, a2 = tb * kT + q, b2 = ta * kT + tx;
-      Za[q][tx] = (a < Nv && b < Nv) ? zs[(int64_t)a * Nvp + b] : 0.f;
+      const bool in = a < Nv && b < Nv;
+      Za[q][tx] = in ? zs[(int64_t)a * Nvp + b] : 0.f;
+      rv[rr] = in ? __ldg(rs + (int64_t)a * Nvp + b) : 0.f;
       Zb[q][tx] = (a2 < Nv && b2 < Nv) ? zs[(int64_t)a2 * Nvp + b2] : 0.f;
     }
     __syncthreads();
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads) kp_proj_anti(PV pv, float *z, const 
       float w = 0.f;
       if (a < Nv && b < Nv && (ta < tb || q < tx) && valid_elem(BLK, i, j, a, b)) {
         w = 0.5f * (Za[q][tx] - Zb[tx][q]);
-        dsum += 2.f * w * rs[(int64_t)a * Nvp + b];
+        dsum += 2.f * w * rv[rr];
       }
       if (a < Nv && b < Nv && (ta < tb || q <= tx)) zs[(int64_t)a * Nvp + b] = w;
       Ws[q][tx] = -w;
@@ -1058,10 +1061,13 @@ __global__ void __launch_bounds__(kThreads) kp_proj_s(PV pv, float *z, const flo
     if (i == j && ta > tb) continue;
     float *zij = z + L.boff[BS] + ((int64_t)i * No + j) * L.SL, *zji = z + L.boff[BS] + ((int64_t)j * No + i) * L.SL;
     const float *rij = r + L.boff[BS] + ((int64_t)i * No + j) * L.SL;
+    float rv[4];   // r_ij on the tile (ta, tb), loaded with the z tiles
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int q = ty + 8 * rr, a = ta * kT + q, b = tb * kT + tx, a2 = tb * kT + q, b2 = ta * kT + tx;
-      Za[q][tx] = (a < Nv && b < Nv) ? zij[(int64_t)a * Nvp + b] : 0.f;
+      const bool in = a < Nv && b < Nv;
+      Za[q][tx] = in ? zij[(int64_t)a * Nvp + b] : 0.f;
+      rv[rr] = in ? __ldg(rij + (int64_t)a * Nvp + b) : 0.f;
       Zb[q][tx] = (a2 < Nv && b2 < Nv) ? zji[(int64_t)a2 * Nvp + b2] : 0.f;
     }
     __syncthreads();
@@ -1073,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads) kp_proj_s(PV pv, float *z, const flo
       float w = 0.f;
       if (a < Nv && b < Nv && (!diag || q <= tx)) {
         w = 0.5f * (Za[q][tx] + Zb[tx][q]);
-        dsum += (diag && q == tx ? 1.f : 2.f) * w * rij[(int64_t)a * Nvp + b];
+        dsum += (diag && q == tx ? 1.f : 2.f) * w * rv[rr];
         zij[(int64_t)a * Nvp + b] = w;
       }
       Ws[q][tx] = w;

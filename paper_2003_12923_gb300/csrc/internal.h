@@ -201,8 +201,10 @@ namespace esmp2 {
 esmp2_status setup_top_basis(esmp2_handle *h);
 esmp2_status setup_rhs(esmp2_handle *h);
 esmp2_status sigma64(esmp2_handle *h, const double *x, double *y, int tc_levels = 0);
+// s_sym: x has the spin-flip symmetry of S exactly (S_ij^ab = S_ji^ba bit for bit); the
+// digit-level virtual pass then contracts the S slices with F_vv from one side only
 esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels = 0,
-                       int couplings = 1);
+                       int couplings = 1, bool s_sym = false);
 void couple_f32_into(esmp2_handle *h, const double *x, double *y);
 void launch_intermediates64(esmp2_handle *h, const double *F, int arrow, const double *x);
 void launch_couple64(esmp2_handle *h, const double *F, int arrow, const double *x, double *y);
@@ -242,6 +244,7 @@ esmp2_status sigma_mixed_packed(esmp2_handle *h, const double *x, double *y);
 void antisym_project(esmp2_handle *h, double *v);
 void singlet_project(esmp2_handle *h, double *v);
 void combine_sym(esmp2_handle *h, double *y);
+void combine_s(esmp2_handle *h, double *y);
 constexpr int kFp64TcLevels = 10;  // digit levels of the float64-exact tensor-core contraction
 int split_levels_for(double tol);
 bool split_supported(const esmp2_handle *h, int levels);

@@ -1083,7 +1083,9 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
       // is a small fraction of the residual it feeds), next to reduced digit levels
       const bool c32 = (arrowv || lv_k < lv) && rho_next >= 1e-5;
       if (arrowv) s = sigma64_arrow(h, x, q, c32 ? 0 : 1);
-      else s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k, c32 ? 0 : 1);
+      // x holds the singlet symmetries exactly (the packed accumulation keeps them bit for
+      // bit, the full-storage path projects x after each step)
+      else s = sigma64_F(h, h->Fsemi, 1, x, q, lv_k, c32 ? 0 : 1, true);
       if (s) return s;
       if (c32) couple_f32_into(h, x, q);
       approx = c32 || lv_k < lv;

@@ -628,6 +628,34 @@ __global__ void k_combine_sym(int No, int Nv, const double *P, double *y) {
   }
 }
 
+// y_ij = P_ij + P_ji^T for the S block from P (= x F on every S slice) in P64: F x_ij equals
+// (x_ji F)^T when S_ij^ab = S_ji^ba.  One CTA per (slice (i, j), tile pair (ta, tb)).
+__global__ void k_combine_s(int No, int Nv, const double *P, double *y) {
+  __shared__ double t1[32][33], t2[32][33];
+  const int64_t NvNv = (int64_t)Nv * Nv, B = (int64_t)No * No * NvNv;
+  const int tiles = (Nv + 31) / 32;
+  int64_t bid = blockIdx.x;
+  const int tb = (int)(bid % tiles); bid /= tiles;
+  const int ta = (int)(bid % tiles); bid /= tiles;
+  const int j = (int)(bid % No), i = (int)(bid / No);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int a0 = ta * 32, b0 = tb * 32;
+  const double *P1 = P + BS * B + ((int64_t)i * No + j) * NvNv;
+  const double *P2 = P + BS * B + ((int64_t)j * No + i) * NvNv;
+  double *Y = y + BS * B + ((int64_t)i * No + j) * NvNv;
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    t1[r][tx] = (a < Nv && b < Nv) ? P1[(int64_t)a * Nv + b] : 0.0;
+    const int a2 = b0 + r, b2 = a0 + tx;                  // transposed tile of P2
+    t2[r][tx] = (a2 < Nv && b2 < Nv) ? P2[(int64_t)a2 * Nv + b2] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < Nv && b < Nv) Y[(int64_t)a * Nv + b] = t1[r][tx] + t2[tx][r];
+  }
+}
+
 // In-place projection of the T, X, Y blocks onto exactly antisymmetric amplitudes:
 // w = (v_ij^ab - v_ji^ab - v_ij^ba + v_ji^ba) / 4 is computed once per canonical element and
 // written with the exact signs to all four images (i == j or a == b slots become zero).
@@ -788,6 +816,14 @@ void combine_sym(esmp2_handle *h, double *y) {
   h->launches += 1;
 }
 
+// y_ij = P_ij + P_ji^T for the S block (P = x F on every S slice, in P64)
+void combine_s(esmp2_handle *h, double *y) {
+  const int No = h->d.No, Nv = h->d.Nv, tiles = (Nv + 31) / 32;
+  const int64_t nblocks = (int64_t)No * No * tiles * tiles;
+  k_combine_s<<<(unsigned)nblocks, 256, 0, h->stream>>>(No, Nv, h->P64, y);
+  h->launches += 1;
+}
+
 namespace {
 __global__ void k_round_f32(const double *src, float *dst, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -835,15 +871,16 @@ void couple_f32_into(esmp2_handle *h, const double *x, double *y) {
 // couplings = 0 (arrow form only): stop after the index contractions (the caller adds the
 // coupling pass).
 esmp2_status sigma64_F(esmp2_handle *h, const double *F, int arrow, const double *x, double *y, int tc_levels,
-                       int couplings) {
+                       int couplings, bool s_sym) {
   if (!h->P64) {
     cudaError_t e = dmalloc(reinterpret_cast<void **>(&h->P64), sizeof(double) * 4 * (size_t)h->d.B, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "sigma64 workspace");
   }
   if (tc_levels) {
-    esmp2_status s = virt_split(h, x, y, h->P64, 1, tc_levels);
+    esmp2_status s = virt_split(h, x, y, h->P64, s_sym ? 2 : 1, tc_levels);
     if (s) return s;
     combine_sym(h, y);
+    if (s_sym) combine_s(h, y);
   } else {
     virt64_sym(h, F, x, y);
   }

@@ -394,11 +394,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //     Z = sum_{p=1..P} d_p 64^(P-p),  d_p in [-32, 31] for p >= 2, d_1 in [-32, 32]
 // give z = sum_p d_p 64^-p to within 64^-P / 2.  Every d_p is exact in bf16 and every
 // product of two digits is an integer of magnitude <= 2^10.
-// Per-slice exponent: one CTA per slice, element (r, c) of slice s at s*sstride + r*ld + c*cs.
+// Per-slice exponent: one CTA per slice, element (r, c) of slice s at s*sstride + r*ld + c*cs;
+// with a slice list, CTA k takes slice list[k] (the other slices are left alone).
 __global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int64_t sstride, int *es,
-                            int64_t cs = 1) {
+                            int64_t cs = 1, const int *list = nullptr) {
   __shared__ double red[32];
-  const double *X = x + blockIdx.x * sstride;
+  const int sl = list ? list[blockIdx.x] : (int)blockIdx.x;
+  const double *X = x + sl * sstride;
   double m = 0.0;
   for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x)
     m = fmax(m, fabs(X[(e / cols) * ld + (e % cols) * cs]));
@@ -413,7 +415,7 @@ __global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int
     if (threadIdx.x == 0) {
       int e = 0;
       if (m > 0.0) frexp(m, &e);   // m = f 2^e with f in [0.5, 1): 2 max |x| < 2^(e+1)
-      es[blockIdx.x] = m > 0.0 ? e + 1 : 0;
+      es[sl] = m > 0.0 ? e + 1 : 0;
     }
   }
 }
@@ -421,11 +423,16 @@ __global__ void k_slice_exp(const double *x, int rows, int cols, int64_t ld, int
 // digits: out[p][s][r][c] (row pitch Nvp, pad columns zero), plane = S * rows * Nvp.
 // One CTA iteration per row; one float64 multiply and one conversion per element, the rest
 // is integer arithmetic.
+// With a slice list (nlist entries) only the listed slices are split; every slice keeps its
+// place in the digit planes (plane p, slice s at (p S + s) rows Nvp).
 __global__ void k_digits(const double *x, int S, int rows, int cols, int Nvp, int64_t ld, int64_t sstride,
-                         const int *es, int P, __nv_bfloat16 *out, int64_t cs = 1) {
+                         const int *es, int P, __nv_bfloat16 *out, int64_t cs = 1, const int *list = nullptr,
+                         int nlist = 0) {
   const int64_t plane = (int64_t)S * rows * Nvp;
-  for (int64_t row = blockIdx.x; row < (int64_t)S * rows; row += gridDim.x) {
-    const int s = (int)(row / rows), r = (int)(row % rows);
+  const int64_t nrows = (int64_t)(list ? nlist : S) * rows;
+  for (int64_t li = blockIdx.x; li < nrows; li += gridDim.x) {
+    const int s = list ? list[li / rows] : (int)(li / rows), r = (int)(li % rows);
+    const int64_t row = (int64_t)s * rows + r;
     const double scale = ldexp(1.0, 6 * P - es[s]);
     const double *src = x + s * sstride + r * ld;
     __nv_bfloat16 *dst = out + row * Nvp;
@@ -659,6 +666,8 @@ esmp2_status virt_bf16(esmp2_handle *h, const void *xb, const void *Fb, int S, f
 // a relative error of order 2^{-6 (Lmax - 1)} against the largest term of each slice.
 // sym = 1: T, X, Y slices (exactly antisymmetric) take only x F on i < j into p64 and the
 // caller forms y_ij = P_ij - P_ij^T; S and Z slices take x F + F x into y.
+// sym = 2: as sym = 1, and the S slices (S_ij^ab = S_ji^ba exactly) also take only x F into
+// p64: F x_ij = (x_ji F)^T, so the caller forms y_ij = P_ij + P_ji^T.
 // sym = 0: every slice takes both terms into y (any input).
 namespace {
 constexpr int kSplitMaxLevels = 10;
@@ -743,9 +752,12 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
   const int No = h->d.No, Nv = h->d.Nv, Nvp = (Nv + 7) & ~7;
   const int S = 5 * No * No, P = kSplitMaxLevels - 1;
   const int64_t NvNv = (int64_t)Nv * Nv;
-  tc::k_slice_exp<<<S, 256, 0, h->stream>>>(x, Nv, Nv, Nv, NvNv, h->es);
+  // the symmetric forms read only the listed slices (T, X, Y with i < j, all of S and Z)
+  const int *list = sym ? h->slist : nullptr;
+  const int nsl = sym ? h->nslist : S;
+  tc::k_slice_exp<<<nsl, 256, 0, h->stream>>>(x, Nv, Nv, Nv, NvNv, h->es, 1, list);
   tc::k_digits<<<1216, 256, 0, h->stream>>>(x, S, Nv, Nv, Nvp, Nv, NvNv, h->es, levels - 1,
-                                            static_cast<__nv_bfloat16 *>(h->xdig));
+                                            static_cast<__nv_bfloat16 *>(h->xdig), 1, list, nsl);
   h->launches += 2;
   const int half = No * (No - 1) / 2;
   {  // every level 2 .. levels of every tile in one launch
@@ -756,9 +768,9 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
     g.slices = sym ? h->slist : nullptr;
     g.per_block = No * No;
     for (int b = 0; b < 5; ++b) {
-      const bool txy = (b == 0 || b == 2 || b == 3);
-      g.tm[b] = (sym && txy) ? 1 : 2;
-      g.to_p64[b] = sym && txy;
+      const bool one = (b == 0 || b == 2 || b == 3) || (sym == 2 && b == 1);
+      g.tm[b] = (sym && one) ? 1 : 2;
+      g.to_p64[b] = sym && one;
     }
     g.S_plane = S;
     g.lmin = 2;                   // level l pairs digit p of x with digit l - p of F
@@ -774,7 +786,7 @@ esmp2_status virt_split(esmp2_handle *h, const double *x, double *y, double *p64
     // the method's work is one contraction of the block vector, however many digit pairs
     // emulate it; the tensor cores execute every pair on the stored slices
     const double nv3 = (double)Nv * Nv * Nv;
-    const double per_pair = sym ? 3.0 * half * 2.0 * nv3 + 2.0 * No * No * 4.0 * nv3 : 4.0 * nv3 * S;
+    const double per_pair = sym ? 3.0 * half * 2.0 * nv3 + (sym == 2 ? 6.0 : 8.0) * No * No * nv3 : 4.0 * nv3 * S;
     const double alg = sym ? alg_virtual_flops(No, Nv) : per_pair;
     if (const char *m = launch_virt(h->stream, h->xdig, P, h->Fdig, P, g, alg, g.npairs * per_pair, ESMP2_KT_DIGITS)) {
       h->err = m;
