@@ -7,7 +7,8 @@ esmp2_solve to a true relative residual below --tol, esmp2_energy (E2_D + E2_L b
 Hylleraas functional, E2_S by the direct S-space sum), esmp2_destroy.
 value = mean seconds per step (time-to-solution, lower is better).
 e2e   = the same through the public API from pinned HOST buffers (host->device copy
-        of every input and the device->host read of the energy inside the timed region).
+        of every input and the device->host read of the energy inside the timed region),
+        mean of two steps after one untimed one.
 Multi-GPU: instances are independent, so N ranks run N replicas (weak scaling, no
 collective on the data path).
 """
@@ -664,11 +665,13 @@ def main():
             t.numpy()[...] = inst[k]
             pinned[k] = t.numpy()
         h2d = sum(pinned[k].nbytes for k in names)
+        step(pinned)   # untimed: the staging buffers of host inputs are the device pool's first use
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info_e, e_e, _ = step(pinned)
+        for _ in range(2):
+            info_e, e_e, _ = step(pinned)
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
+        t_e2e = (time.perf_counter() - t0) / 2
         d2h = 8 * 32 * (info_e["iterations"] + 4 * info_e["outer"] + 8) + 8 * 32 * 6
         e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 

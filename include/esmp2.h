@@ -299,7 +299,7 @@ esmp2_status esmp2_kernel_times(esmp2_kernel_time *out);
  * rounded up to 256, Nvp = Nv rounded up to 8); larger requests return
  * ESMP2_ERR_UNSUPPORTED without touching the device.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  All calls share the
+ * and caches it.  All calls share the
  * array and it keeps the last call's contents (the error flag is cleared on entry), so
  * calls that overlap on the GPU (different streams or threads) race; serialise them.
  * The call synchronises `stream` (a cudaStream_t, NULL = legacy default) to read the

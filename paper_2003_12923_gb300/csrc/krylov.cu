@@ -1002,7 +1002,7 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
   // the singlet solution lies in the symmetric subspace (antisymmetric T, X, Y; S_ij^ab =
   // S_ji^ba); the packed inner solve acts on that subspace only, so x and every residual
   // handed to it are projected onto it (removing the rounding-level components outside)
-  singlet_project(h, h->s64.x);
+  if (!h->x_zero) singlet_project(h, h->s64.x);
   const VCtx c = vctx(h, arrowv ? h->Farr : h->Fsemi);
   const double *bsel = arrowv ? h->barr : h->bsemi;
   debug_phase(h, "solve: x rotation + projection");
@@ -1108,8 +1108,11 @@ esmp2_status solve_mixed(esmp2_handle *h, double tol, int maxit, esmp2_solve_inf
     else stalled = 0;
     prev_relres = relres;
     // inner PCG on A d = r (r made exactly antisymmetric in T, X, Y: the inner sigma
-    // contracts the slices i < j and mirrors them)
-    singlet_project(h, r);
+    // contracts the slices i < j and mirrors them).  The rotated Jacobi preconditioner
+    // projects z = M^-1 r onto the singlet subspace itself, so every search direction and d
+    // have the symmetries exactly whatever rounding-level asymmetry r carries; r is then
+    // read as it is.
+    if (!rj) singlet_project(h, r);
     if (rj) {
       if ((s = packed_rj_init(h, r, kRedBlocks))) return s;
     } else {

@@ -64,7 +64,7 @@ cudaError_t dmalloc(void **p, size_t bytes, cudaStream_t st) {
     if (!ready[dev]) {
       size_t fr = 0, tot = 0;
       cudaMemGetInfo(&fr, &tot);
-      uint64_t keep = tot / 3;
+      uint64_t keep = tot / 2;   // memory kept cached between handles (freed at most down to this)
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
       ready[dev] = true;
     }

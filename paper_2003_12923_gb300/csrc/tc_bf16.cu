@@ -919,7 +919,7 @@ extern "C" esmp2_status esmp2_virtual_contraction_noalloc(const double *x, const
   if (total > (size_t)ESMP2_NOALLOC_MAX_BYTES) return ESMP2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ESMP2_ERR_CUDA;
-  if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device (must precede any stream capture)
+  if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ESMP2_ERR_CUDA;
     g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
