@@ -43,9 +43,9 @@ GOLDEN = {"c2": "tests/golden/o2_e2_c2.json"}
 # valid only while the kernel's source file is byte-identical to the captured one (sha256
 # prefix), else reported as null
 TRAFFIC = {
-    "digits": {"source": "paper_2003_12923_gb300/csrc/tc_bf16.cu", "sha256_16": "e67fd014fc4faf5a",
+    "digits": {"source": "paper_2003_12923_gb300/csrc/tc_bf16.cu", "sha256_16": "a13c20289dbe36a5",
                "profile": "profiles/k_virt_digit_levels_No30_Nv400.md",
-               "bytes_per_launch": 40.9e9},   # the eight k_virt launches of one step, averaged
+               "bytes_per_launch": 24.7e9},   # the eight k_virt launches of one step, averaged
 }
 
 

@@ -190,11 +190,12 @@ __global__ void kp_init(PV pv, const double *r64, const __half *dinv, float *r, 
 }
 
 // x64 (full storage) += d (packed); T, X, Y slices also update their (j, i) partner with -d.
-// One warp per packed row (slice, a), four consecutive b per lane.
+// One warp per packed row (slice, a); consecutive lanes take consecutive b, so every load and
+// every read-modify-write of the float64 rows is one contiguous segment per warp.
 __global__ void __launch_bounds__(256) kp_acc64(PV pv, double *x, const float *d) {
   const Packed &L = pv.L;
   const int64_t rows = (int64_t)L.nslices * L.Nv, NvNv = (int64_t)L.Nv * L.Nv, B = (int64_t)L.NN * NvNv;
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, q4 = L.Nvp >> 2, Nv = L.Nv;
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, Nv = L.Nv;
   for (int64_t row = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * wpb) {
     const int s = (int)(row / Nv), a = (int)(row % Nv);
     int blk, i, j;
@@ -203,17 +204,10 @@ __global__ void __launch_bounds__(256) kp_acc64(PV pv, double *x, const float *d
     double *x1 = x + blk * B + ((int64_t)i * L.No + j) * NvNv + (int64_t)a * Nv;
     double *x2 = x + blk * B + ((int64_t)j * L.No + i) * NvNv + (int64_t)a * Nv;
     const bool anti = !(blk == BS || blk == BZ);
-    for (int c = lane; c < q4; c += 32) {
-      const int b = 4 * c;
-      const float4 v = *reinterpret_cast<const float4 *>(src + b);
-      const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (b + k < Nv) {
-          x1[b + k] += (double)vv[k];
-          if (anti) x2[b + k] -= (double)vv[k];
-        }
-      }
+    for (int b = lane; b < Nv; b += 32) {
+      const double v = (double)src[b];
+      x1[b] += v;
+      if (anti) x2[b] -= v;
     }
   }
 }
