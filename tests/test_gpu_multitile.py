@@ -82,11 +82,14 @@ def test_c2_rhs_energy_and_rates(record_property):
     got = b[torch.from_numpy(idx).cuda()].cpu().numpy()
     assert float(np.abs(got - ref).max()) <= 1e-12 * float(np.abs(ref).max())
     e2s_ref, _ = oc.e2_s()
-    assert abs(g["E2_S"] - e2s_ref) < 1e-13
+    # E2_S is a float64 sum over 8.4e8 S-space triples; the stored value and this one are the
+    # same sum taken in another order (another host, another thread count), equal to rounding
+    e2s_tol = 1e-12 * abs(e2s_ref)
+    assert abs(g["E2_S"] - e2s_ref) < e2s_tol
     info = h.solve(tol=1e-10, maxit=3000, precision=esmp2.FP64)
     assert info["rel_residual"] <= 1e-10
     e = h.energy()
-    assert abs(e["E2_S"] - e2s_ref) < 1e-12
+    assert abs(e["E2_S"] - e2s_ref) < e2s_tol
     for k in ("E2", "E2_D", "E2_L"):
         assert abs(e[k] - g[k]) < 1e-10, (k, e[k], g[k])
     ms = h.profile_sigma(b.reshape(h.shape), precision=esmp2.FP64, reps=3)
