@@ -134,9 +134,26 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   cudaMemcpyAsync(h->F, d->F, sizeof(double) * nF, kind, h->stream);
   cudaMemcpyAsync(h->C, d->C, sizeof(double) * nC, kind, h->stream);
   cudaMemcpyAsync(ooov_in, d->ooov, sizeof(double) * nOOOV, kind, h->stream);
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_alloc = nullptr;
   if (!dev) {
     cudaMemcpyAsync(ovov_in, d->ovov, sizeof(double) * nOVOV, kind, h->stream);
-    cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
+    // the OVVV block, the largest input, comes in on a side stream while the TOP basis and the
+    // OVOV and OOOV transforms run; the handle's stream waits for it before the OVVV pass
+    bool side_ok = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&h->ovvv_ready, cudaEventDisableTiming) == cudaSuccess;
+    if (side_ok) {
+      cudaEventRecord(ev_alloc, h->stream);   // the staging buffer is allocated in this stream's order
+      cudaStreamWaitEvent(side, ev_alloc, 0);
+      cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, side);
+      cudaEventRecord(h->ovvv_ready, side);
+    } else {
+      cudaGetLastError();
+      if (h->ovvv_ready) cudaEventDestroy(h->ovvv_ready);
+      h->ovvv_ready = nullptr;
+      cudaMemcpyAsync(ovvv_in, d->ovvv, sizeof(double) * nOVVV, kind, h->stream);
+    }
   }
   const double *ovov_src = dev ? d->ovov : ovov_in, *ovvv_src = dev ? d->ovvv : ovvv_in;
   ce = cudaGetLastError();
@@ -155,6 +172,13 @@ esmp2_status esmp2::create_impl(esmp2_handle **out, const esmp2_desc *d, cudaStr
   h->omega_op = h->omega - h->level_shift;
   debug_phase(h, "create: TOP basis");
   if (!s) s = setup_rhs_from(h, ovov_src, ovov_in, ooov_in, ovvv_src, ovvv_in, scratch);
+  if (h->ovvv_ready) {   // whatever happened above, the handle's stream is ordered after the copy
+    cudaStreamWaitEvent(h->stream, h->ovvv_ready, 0);
+    cudaEventDestroy(h->ovvv_ready);
+    h->ovvv_ready = nullptr;
+  }
+  if (side) cudaStreamDestroy(side);
+  if (ev_alloc) cudaEventDestroy(ev_alloc);
   debug_phase(h, "create: transforms + rhs");
   if (!s) {
     cudaMemsetAsync(h->s64.x, 0, sizeof(double) * h->d.n, h->stream);

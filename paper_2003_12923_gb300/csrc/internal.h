@@ -160,6 +160,7 @@ struct esmp2_handle {
   int *pCode = nullptr;     // per-slice block | 8 (i == 0) | 16 (j == 0)
   double *pdot2 = nullptr;  // partials of <r, z>_w
   double *zero_slots = nullptr;  // 32 zero doubles (alpha = beta = 0)
+  cudaEvent_t ovvv_ready = nullptr;  // create: the OVVV input copy (side stream) has landed
   bool x_zero = true;       // s64.x is known to be zero (its sigma is zero, no build needed)
   bool r_true = false;      // s64.r holds the true residual -b - A x of s64.x (same basis)
   // float64-accurate virtual-index terms from exact bf16 digit products (tcgen05)

@@ -644,6 +644,7 @@ esmp2_status setup_rhs_from(esmp2_handle *h, const double *ovov_src, double *ovo
   }
   {
     debug_phase(h, "  ooov transform");
+    if (h->ovvv_ready) cudaStreamWaitEvent(st, h->ovvv_ready, 0);   // host OVVV copied on a side stream
     int dims[4] = {No, Nv, Nv, Nv};
     const size_t smem = xr_df_smem(Nv);
     if (No <= kXrN && smem <= 220 * 1024) {  // c -> u' (first No columns of Wv)

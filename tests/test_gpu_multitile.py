@@ -90,8 +90,12 @@ def test_c2_rhs_energy_and_rates(record_property):
     assert info["rel_residual"] <= 1e-10
     e = h.energy()
     assert abs(e["E2_S"] - e2s_ref) < e2s_tol
-    for k in ("E2", "E2_D", "E2_L"):
-        assert abs(e[k] - g[k]) < 1e-10, (k, e[k], g[k])
+    assert abs(e["E2"] - g["E2"]) < 1e-10, (e["E2"], g["E2"])
+    # the stored solve stops at a relative residual of 8.5e-8: the total E2_D + E2_L (the
+    # Hylleraas functional) is stationary, its error second order in that residual, but E2_D
+    # and E2_L alone are not, and theirs is first order
+    for k in ("E2_D", "E2_L"):
+        assert abs(e[k] - g[k]) < 1e-8, (k, e[k], g[k])
     ms = h.profile_sigma(b.reshape(h.shape), precision=esmp2.FP64, reps=3)
     n_u = (No * (No - 1) / 2) * (Nv * (Nv - 1) / 2) + No * No * Nv * Nv / 2 \
         + ((No - 1) * (No - 2) / 2) * ((Nv - 1) * (Nv - 2) / 2) + (No * (No - 1) / 2) * (Nv * (Nv - 1) / 2) \
