@@ -520,7 +520,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS) + ["c4"])
     ap.add_argument("--wave", type=int, default=16, help="c4: instances generated and solved per batch call")
-    ap.add_argument("--concurrency", type=int, default=2, help="c4: host workers (streams) of the batch")
+    ap.add_argument("--concurrency", type=int, default=3, help="c4: host workers (streams) of the batch")
     ap.add_argument("--fp64-every", type=int, default=8, help="c4: time plain FP64 on every k-th instance")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tf32", "reduced", "minres"])
     ap.add_argument("--no-variants", action="store_true", help="skip the tf32 and reduced-basis forms")
