@@ -282,7 +282,8 @@ cudaError_t smem_limit_once(const void *func, int bytes);
 
 // 2-D tensor map of bf16 (f32 = false) or float32 elements (inner dimension first; rows of
 // row_bytes), box box_inner x box_outer, shared-memory swizzle of 128, 64, 32 or 0 bytes, zero
-// fill out of bounds.  False when the driver's encoder is unavailable or rejects the description.
+// fill out of bounds.  False when the CUDA driver's tensor-map encoder is unavailable or
+// rejects the description.
 bool tma_map_2d(CUtensorMap *m, const void *base, bool f32, uint64_t inner, uint64_t outer, uint64_t row_bytes,
                 uint32_t box_inner, uint32_t box_outer, int swizzle_bytes);
 
