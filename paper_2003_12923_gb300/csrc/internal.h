@@ -137,7 +137,7 @@ struct esmp2_handle {
   bool arrow_ready = false;
   bool arrowv = false;      // the current call works in the reduced-cost basis
   double *Rv = nullptr, *Rvt = nullptr;  // Nv x Nv virtual rotation (t' fixed) and its transpose
-  int vrot_level = 0;       // 0 none, 1 to 1e-6 (preconditioner), 2 to the rounding level
+  int vrot_level = 0;       // 0 none, 1 to 1e-2 (preconditioner), 2 to the rounding level
   double *jB = nullptr, *jJ = nullptr;  // Jacobi state (rotated rows, accumulated rotation)
   unsigned *jflag = nullptr;
   double *mr_a = nullptr, *mr_b = nullptr, *mr_v = nullptr;  // MINRES direction vectors and Lanczos vector (n)
