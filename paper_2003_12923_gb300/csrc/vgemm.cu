@@ -303,11 +303,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (r >= g.rows) continue;
         const int bc = b0 + c, mcol = min(16, nvalid - c);
         if (dst16) {   // stored element (a = bc + q, b = rc) of the slice
-          if (g.lam) {
+          if (g.lam) {   // the fast division (2 ulp) serves the preconditioner: the denominator of
+                         // (a, b) and of its image (b, a) is the same float, so M stays symmetric
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const int a = bc + q;
-              v[q] = (q < mcol && vg_valid(rcode, a, rc)) ? v[q] / ((g.lam[a] + rlam) - rocc) : 0.f;
+              v[q] = (q < mcol && vg_valid(rcode, a, rc)) ? __fdividef(v[q], (g.lam[a] + rlam) - rocc) : 0.f;
             }
           }
           if (run) {   // all 32 lanes here (every row of the warp is in range)
